@@ -1,0 +1,516 @@
+#!/usr/bin/env python
+"""Benchmark of bulk construction + bulk lookup of the sectorized blocked
+Bloom filter on GB300, measured against the random-access bound.
+
+One step = construction of the whole insert set + lookup of the whole query
+set (every row of the hot path: key load, XXH64, block selection, pattern,
+atomic OR / wide-load test, result store).  The default workload is the
+HBM-resident filter of the "filter at scale" configuration:
+
+    4 GiB filter: 2^27 blocks x 256 bits, S = 32-bit words, K = 8, seed 0;
+    insert 3,435,973,836 keys (10 bits/key; SplitMix64 stream 1);
+    look up 10^9 keys, 10% members (counter-based query stream).
+
+Inputs are generated on the device before timing (inputs larger than L2, so
+no flush is needed).  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload 4GiB|32MiB|1MiB] [--sweep] [--no-e2e] [--no-cpu-baseline]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "4GiB": dict(nbytes=4 << 30, block_bits=256, word_bits=32, k=8, n_lookup=10**9, member_den=10,
+                 desc="4 GiB HBM-resident SBF, 2^27 x 256-bit blocks, S=32, K=8; insert 10 bits/key "
+                      "(3,435,973,836 keys), look up 1e9 keys at 10% members"),
+    "32MiB": dict(nbytes=32 << 20, block_bits=256, word_bits=32, k=8, n_lookup=10**9, member_den=10,
+                  desc="32 MiB L2-resident SBF, 2^20 x 256-bit blocks, S=32, K=8; insert 10 bits/key "
+                       "(26,843,545 keys), look up 1e9 keys at 10% members"),
+    "1MiB": dict(nbytes=1 << 20, block_bits=256, word_bits=32, k=8, n_insert=10**6, n_lookup=10**6,
+                 member_den=2,
+                 desc="1 MiB SBF, 2^15 x 256-bit blocks, S=32, K=8; insert 1e6 keys, look up 1e6 keys"),
+}
+METRIC = "G lookups/s & G inserts/s vs measured random-access bound; FPR at bits/key"
+
+
+def wl_sizes(w):
+    b = w["nbytes"] * 8 // w["block_bits"]
+    n_ins = w.get("n_insert", w["nbytes"] * 8 // 10)
+    return b, n_ins, w["n_lookup"]
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas, no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (a timing reduction, not data)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int, uuid: str | None):
+        self.sel = str(device_index)
+        if uuid:
+            try:
+                listing = subprocess.run(["nvidia-smi", "-L"], capture_output=True, text=True, timeout=10).stdout
+                if uuid in listing:
+                    self.sel = uuid
+            except Exception:
+                pass
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.sel, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = max(smax, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        loaded = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample; rank 0 only)
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(w, budget_s: float):
+    """Oracle insert+lookup throughput on a bounded sample of the workload.
+
+    Inserts the first keys of the insert stream into a full-size host filter
+    and looks up the first queries of the query stream, in chunks, until the
+    budget is spent (about half the budget per operation).
+    """
+    import numpy as np
+    import oracle
+    import synthkeys
+    b, n_ins, n_q = wl_sizes(w)
+    geom = oracle.Geometry(num_blocks=b, block_bits=w["block_bits"], word_bits=w["word_bits"], k=w["k"], seed=0)
+    f = oracle.SBF(geom)
+    chunk = 1 << 20
+    done_i, t_i = 0, 0.0
+    while t_i < budget_s / 2 and done_i < n_ins:
+        c = min(chunk, n_ins - done_i)
+        keys = synthkeys.splitmix64(synthkeys.SEED_INSERT, done_i, c)
+        t0 = time.perf_counter()
+        f.add(keys)
+        t_i += time.perf_counter() - t0
+        done_i += c
+    done_q, t_q = 0, 0.0
+    mixed = synthkeys.mixed_queries(n_ins, n_q // 2, n_q - n_q // 2)[0] if w["member_den"] == 2 else None
+    while t_q < budget_s / 2 and done_q < n_q:
+        c = min(chunk, n_q - done_q)
+        if mixed is not None:
+            q = mixed[done_q:done_q + c]
+        else:
+            q, _ = synthkeys.stream_queries(done_q, c, n_ins, w["member_den"])
+        t0 = time.perf_counter()
+        f.contains(q)
+        t_q += time.perf_counter() - t0
+        done_q += c
+    return {"insert_keys": done_i, "insert_s": t_i, "lookup_keys": done_q, "lookup_s": t_q,
+            "gkeys_s": (done_i + done_q) / (t_i + t_q) / 1e9,
+            "insert_gkeys_s": done_i / t_i / 1e9, "lookup_gkeys_s": done_q / t_q / 1e9}
+
+
+def run_reference(args, w, wname):
+    """The reference arm: the CPU oracle as it stands, on the host cores."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    per_step = max(1.0, min(20.0, 150.0 / max(1, steps + warm)))
+    for _ in range(warm):
+        cpu_oracle_rate(w, per_step * 0.25)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        vals.append(cpu_oracle_rate(w, per_step))
+    wall = time.perf_counter() - t0
+    v = statistics.median(x["gkeys_s"] for x in vals)
+    r = vals[len(vals) // 2]
+    sample = (f"per step: first {r['insert_keys']:,} insert keys into the full-size host filter, then first "
+              f"{r['lookup_keys']:,} queries of the query stream (~{per_step:.0f} s of single-thread CPU work)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "G keys/s", "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": wall / steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64/u32 integer", "data": "synthetic",
+        "config": {"workload": wname, "desc": w["desc"]},
+        "cpu_baseline": {"value": v, "unit": "G keys/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "insert_gkeys_s": r["insert_gkeys_s"], "lookup_gkeys_s": r["lookup_gkeys_s"]},
+        "e2e": {"value": v, "unit": "G keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("sbf_kernels.cuh", "sbf_device.cuh", "salts.cuh"):
+        with open(os.path.join(ROOT, "paper_2512_15595_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, wname: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f)
+    e = t.get(f"{kernel}/{wname}")
+    if not e or e.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def gen_inputs(torch, w, device):
+    import synthkeys
+    b, n_ins, n_q = wl_sizes(w)
+    ins = torch.empty(n_ins, dtype=torch.int64, device=device)
+    synthkeys.splitmix64_torch(synthkeys.SEED_INSERT, 0, n_ins, device, out=ins)
+    flags = torch.empty(n_q, dtype=torch.uint8, device=device)
+    if w["member_den"] == 2:
+        import numpy as np
+        q, fl = synthkeys.mixed_queries(n_ins, n_q // 2, n_q - n_q // 2)
+        qd = torch.from_numpy(q.view(np.int64)).to(device)
+        flags.copy_(torch.from_numpy(fl))
+    else:
+        qd = torch.empty(n_q, dtype=torch.int64, device=device)
+        synthkeys.stream_queries_torch(n_q, n_ins, device, ratio_den=w["member_den"], out=qd, member_flags=flags)
+    torch.cuda.synchronize()
+    return ins, qd, flags
+
+
+def gups_bounds(torch, w, ins, q, device, reps=3):
+    """Random-access bound on the filter's footprint with the same key streams."""
+    from paper_2512_15595_gb300 import BF_GUPS_LOAD, BF_GUPS_RED_OR, _lib, bf_layout
+    unit = max(32, w["block_bits"] // 8)
+    table = torch.zeros(w["nbytes"], dtype=torch.uint8, device=device)
+    gout = torch.empty(q.numel(), dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream()
+    best = {}
+    for mode, name, keys in ((BF_GUPS_LOAD, "load", q), (BF_GUPS_RED_OR, "red_or", ins)):
+        for kpt in (1, 2, 4):
+            lay = bf_layout(0, 0, kpt, 256, 0, 0)
+            ts = []
+            for i in range(reps + 1):
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record(stream)
+                _lib.bf_gups(mode, table.data_ptr(), table.numel(), unit, keys.data_ptr(), keys.numel(),
+                             gout.data_ptr() if mode == BF_GUPS_LOAD else None, lay, stream)
+                e.record(stream)
+                e.synchronize()
+                if i:
+                    ts.append(s.elapsed_time(e))
+            g = keys.numel() / (min(ts) * 1e-3) / 1e9
+            if name not in best or g > best[name]["gkeys_s"]:
+                best[name] = {"gkeys_s": g, "kpt": kpt, "unit_bytes": unit}
+    del table, gout
+    torch.cuda.empty_cache()
+    return best
+
+
+def popcount_fpr(torch, words, w):
+    """E[FPR | this bit array] for ideal query hashing: mean over blocks of
+    prod_w (popcount_w / S)^k' (computed on the device from the array)."""
+    lut = torch.tensor([bin(i).count("1") for i in range(256)], dtype=torch.float32, device=words.device)
+    s = w["block_bits"] // w["word_bits"]
+    kp = w["k"] // s
+    bpw = w["word_bits"] // 8
+    block_bytes = w["block_bits"] // 8
+    nblocks = words.numel() // block_bytes
+    total = 0.0
+    step = 1 << 22
+    for lo in range(0, nblocks, step):
+        hi = min(nblocks, lo + step)
+        blk = words[lo * block_bytes:hi * block_bytes].view(hi - lo, s, bpw).long()
+        pc = lut[blk].sum(-1)
+        total += float(torch.prod((pc / w["word_bits"]) ** kp, dim=-1).double().sum().item())
+    return total / nblocks
+
+
+def run_ours(args, w, wname):
+    import torch
+    world, rank, local = dist_env()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    from paper_2512_15595_gb300 import Filter, _lib, autotune
+    b, n_ins, n_q = wl_sizes(w)
+    props = torch.cuda.get_device_properties(device)
+    regime = autotune.regime_of(w["nbytes"], props.L2_cache_size)
+
+    ins, qd, flags = gen_inputs(torch, w, device)
+    f = Filter(b, w["block_bits"], w["word_bits"], w["k"], 0, device=device)
+    layouts = autotune.apply_tuned(f, regime)
+    out = torch.empty(n_q, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream()
+
+    bounds = gups_bounds(torch, w, ins, qd, device) if not args.no_gups else None
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        f.add(ins)
+        if ev:
+            ev[1].record(stream)
+        f.contains(qd, out=out)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(local, getattr(props, "uuid", None) and f"GPU-{props.uuid}")
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    local_ms = t_start.elapsed_time(t_end)
+    total_ms = max_over_ranks(local_ms, world, device)
+    add_ms = statistics.median(e[0].elapsed_time(e[1]) for e in evs)
+    con_ms = statistics.median(e[1].elapsed_time(e[2]) for e in evs)
+    keys_per_step = n_ins + n_q
+    value = world * keys_per_step * args.steps / (total_ms * 1e-3) / 1e9
+    ins_g = n_ins / (add_ms * 1e-3) / 1e9
+    look_g = n_q / (con_ms * 1e-3) / 1e9
+
+    # accuracy of this build: FPR of the fresh queries at 10 bits/key
+    fresh = flags == 0
+    n_fresh = int(fresh.sum().item())
+    measured_fpr = float(out[fresh].float().sum().item()) / max(1, n_fresh)
+    missed = int((out[flags == 1] == 0).sum().item())
+    realized_fpr = popcount_fpr(torch, f.words, w)
+
+    # roofline of the dominant kernel (construction: one random sector RMW per key)
+    sectors = max(1, w["block_bits"] // 256)
+    bytes_add = 8 + 2 * 32 * sectors
+    bytes_con = 8 + 32 * sectors + 1
+    dominant = "add" if add_ms >= con_ms else "contains"
+    per_key = bytes_add if dominant == "add" else bytes_con
+    dur = add_ms if dominant == "add" else con_ms
+    n_dom = n_ins if dominant == "add" else n_q
+    achieved = per_key * n_dom / (dur * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": measured_traffic(f"sbf_{dominant}_kernel", wname), "kernel": f"sbf_{dominant}_kernel",
+            "peak_source": f"{peak_kind} HBM copy bandwidth", "algorithmic_bytes_per_key": per_key}
+    ra = None
+    if bounds:
+        ra = {"lookup_bound_gkeys_s": bounds["load"]["gkeys_s"], "insert_bound_gkeys_s": bounds["red_or"]["gkeys_s"],
+              "lookup_frac": look_g / bounds["load"]["gkeys_s"], "insert_frac": ins_g / bounds["red_or"]["gkeys_s"],
+              "unit_bytes": bounds["load"]["unit_bytes"], "how": "bf_gups: same key streams, same footprint, "
+              "random unit loads (lookup) / red.or (insert), best kpt"}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(torch, f, ins, qd, args, world, device)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle: a forked process pool is never used, and the oracle
+        # runs in this process only after all GPU work above is done
+        r = cpu_oracle_rate(w, args.cpu_budget)
+        cpu = {"value": r["gkeys_s"], "unit": "G keys/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {r['insert_keys']:,} inserts into the full-size host filter and first "
+                         f"{r['lookup_keys']:,} queries ({r['insert_s'] + r['lookup_s']:.1f} s single-thread)",
+               "insert_gkeys_s": r["insert_gkeys_s"], "lookup_gkeys_s": r["lookup_gkeys_s"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "G keys/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 words (integer)",
+            "data": "synthetic (SplitMix64 key streams generated on the device)",
+            "config": {"workload": wname, "desc": w["desc"], "num_blocks": b, "block_bits": w["block_bits"],
+                       "word_bits": w["word_bits"], "k": w["k"], "n_insert": n_ins, "n_lookup": n_q,
+                       "regime": regime, "layouts": layouts, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (no flush)" if n_ins * 8 > props.L2_cache_size
+                             else "warm L2 (cache-resident regime)"},
+            "insert_gkeys_s": ins_g, "lookup_gkeys_s": look_g, "insert_ms": add_ms, "lookup_ms": con_ms,
+            "random_access_bound": ra,
+            "fpr": {"bits_per_key": w["nbytes"] * 8 / n_ins, "measured": measured_fpr,
+                    "realized_filter": realized_fpr, "fresh_queries": n_fresh, "false_negatives": missed},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 2 * args.steps, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    f.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(torch, f, ins, qd, args, world, device):
+    """Same step through the host-buffer entry points: keys start in pinned
+    host memory, results end there; the copies are inside the timed region."""
+    h_ins = torch.empty(ins.numel(), dtype=torch.int64, pin_memory=True)
+    h_q = torch.empty(qd.numel(), dtype=torch.int64, pin_memory=True)
+    h_out = torch.empty(qd.numel(), dtype=torch.uint8, pin_memory=True)
+    h_ins.copy_(ins)
+    h_q.copy_(qd)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a_ins, a_q, a_out = h_ins.numpy(), h_q.numpy(), h_out.numpy()
+
+    def step():
+        f.add_host(a_ins)
+        f.contains_host(a_q, a_out)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(args.steps):
+        step()
+    e.record(stream)
+    e.synchronize()
+    ms = max_over_ranks(s.elapsed_time(e), world, device)
+    n = ins.numel() + qd.numel()
+    del h_ins, h_q, h_out
+    return {"value": world * n * args.steps / (ms * 1e-3) / 1e9, "unit": "G keys/s",
+            "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": qd.numel(), "ms_per_step": ms / args.steps,
+            "api": "bf_add_host + bf_contains_host (pinned host buffers)"}
+
+
+def run_sweep(args, w, wname):
+    """Autotune every layout of this workload's geometry and store the best."""
+    import torch
+    from paper_2512_15595_gb300 import Filter, autotune
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    props = torch.cuda.get_device_properties(device)
+    b, n_ins, n_q = wl_sizes(w)
+    regime = autotune.regime_of(w["nbytes"], props.L2_cache_size)
+    ins, qd, flags = gen_inputs(torch, w, device)
+    n_add = min(n_ins, args.sweep_keys)
+    n_con = min(n_q, args.sweep_keys)
+    f = Filter(b, w["block_bits"], w["word_bits"], w["k"], 0, device=device)
+    f.add(ins)  # occupancy of the real workload
+    out = torch.empty(n_con, dtype=torch.uint8, device=device)
+    res = autotune.sweep(torch, f, ins[:n_add], qd[:n_con], out, regime,
+                         log=lambda r: print(json.dumps(r), file=sys.stderr, flush=True))
+    table = autotune.load_tuned()
+    table[res["key"]] = res["entry"]
+    autotune.save_tuned(table)
+    print(json.dumps({"sweep": wname, "key": res["key"], "best": res["entry"]}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="4GiB", choices=sorted(WORKLOADS))
+    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--sweep-keys", type=int, default=1 << 28)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-gups", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w, args.workload)
+    elif args.sweep:
+        run_sweep(args, w, args.workload)
+    else:
+        run_ours(args, w, args.workload)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * bloomgb -- sectorized blocked Bloom filter on one GB300 GPU (sm_103a).
+ *
+ * C ABI of the library built from paper_2512_15595_gb300/csrc.  The filter
+ * and the operations follow "Optimizing Bloom Filters on Modern GPUs"
+ * (arXiv 2512.15595):
+ *
+ *   - Sec. II-A: a Bloom filter approximates a set of n keys with a bit array
+ *     of m bits; construction sets the k pattern bits of every key, lookup
+ *     reports a key present iff all of its k bits are set (false positives
+ *     possible, false negatives never).  The blocked form splits the array
+ *     into b blocks of B bits and sends all k bits of a key into one block;
+ *     the sectorized form splits a block into s = B/S words of S bits and
+ *     puts k' = k/s bits into every word (k >= s, s | k).
+ *   - Sec. IV-B: one 64-bit base hash per key (XXH64); the bit positions are
+ *     the high bits of the base hash times odd constants (salts).
+ *   - Sec. IV-A / IV-C: a key is processed by a cooperative group of Theta
+ *     threads, each loading Phi contiguous words per step (1 <= Theta*Phi <= s,
+ *     both powers of two); the group shares the key's hash by shuffles.
+ *
+ * Conventions (all entry points):
+ *   - Pointers named d_* are device pointers owned by the caller; h_* are host
+ *     pointers owned by the caller.  The library never frees caller memory.
+ *   - Operations are asynchronous on the given stream (NULL = legacy default
+ *     stream) and never synchronize the host, except where stated.
+ *   - Argument errors are detected on the host before any launch and return
+ *     BF_EINVAL / BF_EUNSUPPORTED; nothing is enqueued in that case.
+ *   - A CUDA error reported at launch returns BF_ECUDA; bf_last_error() gives
+ *     the message.  n = 0 is a no-op returning BF_OK.
+ *   - Bit layout of the filter: block j occupies words j*s .. j*s+s-1; a word
+ *     is S bits little-endian, bit p is the value 1 << p.
+ *   - Hash readings the paper leaves open (fixed by this library):
+ *       h     = XXH64 of the key's 8 little-endian bytes with params.seed;
+ *       j     = ((h >> 32) * b) >> 32 if b <= 2^32, else high64(h * b);
+ *       h_lo  = h mod 2^32;
+ *       bit t of word w (t < k', w < s) uses salt i = w + s*t and is
+ *         ((h_lo * salt32[i]) mod 2^32) >> 27          for S = 32,
+ *         ((h_lo * salt64[i]) mod 2^64) >> 58          for S = 64,
+ *       salt64[i] = (i-th output of SplitMix64 seeded 0x5A175EED) | 1,
+ *       salt32[i] = (salt64[i] >> 32) | 1.
+ *   - Thread safety: distinct filters may be used from distinct host threads.
+ *     Calls on one filter from several host threads must be serialized by the
+ *     caller.
+ */
+#ifndef BLOOMGB_H
+#define BLOOMGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st* bf_stream_t;
+
+typedef struct bf_filter bf_filter;
+
+typedef enum {
+    BF_OK = 0,
+    BF_EINVAL = 1,         /* bad argument: null pointer, misalignment, bad geometry */
+    BF_ENOMEM = 2,         /* device or pinned-host allocation failed */
+    BF_ECUDA = 3,          /* a CUDA call failed; see bf_last_error() */
+    BF_EUNSUPPORTED = 4    /* valid by the definition, but not compiled into this build */
+} bf_status;
+
+/* Filter geometry (Sec. II-A).  num_blocks = b >= 1; block_bits = B in
+   {64,128,256,512,1024}; word_bits = S in {32,64}; k = pattern bits with
+   s = B/S words per block, k >= s, s | k, k <= 64; seed = XXH64 seed.
+   Builds compile k in {4,8,16}; other admissible k return BF_EUNSUPPORTED. */
+typedef struct {
+    uint64_t num_blocks;
+    uint32_t block_bits;
+    uint32_t word_bits;
+    uint32_t k;
+    uint32_t reserved;      /* must be 0 */
+    uint64_t seed;
+} bf_params;
+
+typedef enum { BF_OP_ADD = 0, BF_OP_CONTAINS = 1 } bf_op;
+
+/* Cache-policy hints (bit flags of bf_layout.flags). */
+enum {
+    BF_HINT_FILTER_EVICT_LAST = 1u << 0,   /* filter accesses carry an L2 evict_last policy */
+    BF_HINT_KEYS_EVICT_NORMAL = 1u << 1    /* keys load with evict_normal instead of evict_first */
+};
+
+/* Execution layout of one operation (Sec. IV-A, IV-C).
+   cg = Theta threads per key (power of two, 1..s); phi = Phi words per thread
+   per step (power of two, cg*phi <= s); kpt = keys each thread hashes per
+   tile (1, 2 or 4); block_threads = CTA size (multiple of 32, <= 1024);
+   grid_ctas = number of CTAs (0 = SM count x resident CTAs per SM).
+   A zero in cg/phi/kpt/block_threads selects the library default. */
+typedef struct {
+    uint32_t cg;
+    uint32_t phi;
+    uint32_t kpt;
+    uint32_t block_threads;
+    uint32_t grid_ctas;
+    uint32_t flags;
+} bf_layout;
+
+/* Validate a geometry on the host.  BF_OK, BF_EINVAL (not an SBF by
+   Sec. II-A) or BF_EUNSUPPORTED (admissible but not compiled). */
+bf_status bf_params_check(const bf_params* params);
+
+/* Validate a layout for a geometry and operation on the host (Sec. IV-A:
+   1 <= cg*phi <= s, powers of two); zeros are resolved to defaults first. */
+bf_status bf_layout_check(const bf_params* params, int op, const bf_layout* layout);
+
+/* Create a filter on the current CUDA device.  If d_words is NULL the library
+   allocates b*B/8 bytes (owned, freed by bf_destroy) and zeroes them with a
+   blocking memset.  Otherwise it adopts the caller's buffer, which must hold
+   b*B/8 bytes, be aligned to max(32, B/8) bytes and stay valid until
+   bf_destroy; an adopted buffer is neither cleared nor freed. */
+bf_status bf_create(const bf_params* params, void* d_words, bf_filter** out);
+
+/* Release the filter (and the bit array if the library allocated it).  The
+   caller must ensure no work on the filter is still in flight. */
+bf_status bf_destroy(bf_filter* f);
+
+/* Zero the bit array, asynchronously on stream. */
+bf_status bf_clear(bf_filter* f, bf_stream_t stream);
+
+/* Construction (Sec. II-A, Sec. IV): set the pattern of each of the n keys
+   d_keys[0..n) (8-byte aligned device array).  Bitwise OR is commutative and
+   idempotent, so the result does not depend on layout, order or duplicates. */
+bf_status bf_add(bf_filter* f, const uint64_t* d_keys, uint64_t n, bf_stream_t stream);
+
+/* Lookup (Sec. II-A, Sec. IV): d_out[i] = 1 if every pattern bit of d_keys[i]
+   is set, else 0; d_out is a device array of n bytes (compatible with
+   torch.bool).  Reads the filter only. */
+bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, uint8_t* d_out,
+                      bf_stream_t stream);
+
+/* End-to-end variants over HOST buffers: keys are copied to the device in
+   chunks on internal streams, overlapping the copies with the kernels; the
+   contains variant copies the results back into h_out.  The work is ordered
+   after prior work on `stream` and all of it is complete when `stream` is.
+   h_keys / h_out must stay valid until then; page-locked (pinned) memory is
+   needed for overlap.  The first call allocates the device staging buffers
+   (2 x chunk_keys x 9 bytes, see bf_set_staging) and keeps them until
+   bf_destroy. */
+bf_status bf_add_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, bf_stream_t stream);
+bf_status bf_contains_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
+                           bf_stream_t stream);
+
+/* Keys per staging chunk of the host variants (default 1<<24).  Frees the
+   current staging buffers; must not be called while host-variant work on
+   this filter is in flight. */
+bf_status bf_set_staging(bf_filter* f, uint64_t chunk_keys);
+
+/* Raw bit array: device pointer and size in bytes. */
+bf_status bf_words(const bf_filter* f, void** d_ptr, uint64_t* nbytes);
+
+/* Geometry of an existing filter. */
+bf_status bf_get_params(const bf_filter* f, bf_params* out);
+
+/* Select the layout of one operation (op = BF_OP_ADD or BF_OP_CONTAINS). */
+bf_status bf_set_layout(bf_filter* f, int op, const bf_layout* layout);
+bf_status bf_get_layout(const bf_filter* f, int op, bf_layout* out);
+
+/* L2 persistence window over the bit array for `stream` (cache-resident
+   filters, e.g. 32 MiB): sets the context's persisting-L2 limit to
+   min(bytes, device maximum) and the stream's access-policy window with the
+   given hit ratio.  hit_ratio <= 0 removes the window, resets persisting
+   lines and sets the limit back to 0. */
+bf_status bf_set_l2_persist(bf_filter* f, bf_stream_t stream, float hit_ratio);
+
+/* Random-access microbenchmark that bounds the filter kernels (Sec. V-B
+   measures the bound with random 64-bit accesses, GUPS).  For each i in
+   [0, n): u = unit index taken from d_keys[i] by the same multiply-shift
+   rule as the block index, over table_bytes / unit_bytes units;
+     mode BF_GUPS_LOAD:   load the unit_bytes at u (32-byte vector loads; 8-byte
+                          load when unit_bytes = 8), fold them to one byte and
+                          store it to d_out[i];
+     mode BF_GUPS_RED_OR: one red.global.or of a 32-bit value derived from
+                          d_keys[i] into each 32-byte sector of unit u.
+   unit_bytes in {8, 32, 64, 128}; d_table aligned to unit_bytes; layout uses
+   kpt, block_threads and grid_ctas (cg/phi ignored). */
+typedef enum { BF_GUPS_LOAD = 0, BF_GUPS_RED_OR = 1 } bf_gups_mode;
+bf_status bf_gups(int mode, void* d_table, uint64_t table_bytes, uint32_t unit_bytes,
+                  const uint64_t* d_keys, uint64_t n, uint8_t* d_out, const bf_layout* layout,
+                  bf_stream_t stream);
+
+/* Number of kernel launches one bf_add / bf_contains / bf_gups call makes:
+   always 1 (the host variants make one per chunk). */
+uint32_t bf_launches_per_call(void);
+
+const char* bf_status_str(bf_status s);
+
+/* Message of the last error on the calling host thread ("" if none). */
+const char* bf_last_error(void);
+
+/* Library version string. */
+const char* bf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLOOMGB_H */

@@ -1,0 +1,118 @@
+"""Sectorized blocked Bloom filter on one GB300 (sm_103a).
+
+The compute path is the CUDA library ``_build/libbloomgb.so`` (C ABI in
+``include/bloomgb.h``); this package is its thin Python binding.  PyTorch
+supplies device memory and streams.  :class:`Filter` is a convenience
+wrapper over the ``bf_*`` functions for torch tensors.
+"""
+from __future__ import annotations
+
+from . import _lib
+from ._lib import (BF_GUPS_LOAD, BF_GUPS_RED_OR, BF_HINT_FILTER_EVICT_LAST, BF_HINT_KEYS_EVICT_NORMAL,
+                   BF_OP_ADD, BF_OP_CONTAINS, BloomError, bf_layout, bf_params)
+
+__all__ = ["Filter", "BloomError", "bf_params", "bf_layout", "BF_OP_ADD", "BF_OP_CONTAINS",
+           "BF_HINT_FILTER_EVICT_LAST", "BF_HINT_KEYS_EVICT_NORMAL", "BF_GUPS_LOAD", "BF_GUPS_RED_OR",
+           "valid_layouts", "device_tensor"]
+
+
+def valid_layouts(block_bits: int, word_bits: int):
+    """All (cg, phi) pairs of Sec. IV-A: powers of two with 1 <= cg*phi <= s."""
+    s = block_bits // word_bits
+    out = []
+    cg = 1
+    while cg <= s:
+        phi = 1
+        while cg * phi <= s:
+            out.append((cg, phi))
+            phi *= 2
+        cg *= 2
+    return out
+
+
+class _DevBuf:
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def device_tensor(ptr: int, nbytes: int, device):
+    """A torch uint8 view of device memory the library owns (no copy)."""
+    import torch
+    return torch.as_tensor(_DevBuf(ptr, nbytes), device=device)
+
+
+def _key_ptr(keys):
+    import torch
+    if not keys.is_cuda:
+        raise ValueError("keys must be a CUDA tensor")
+    if keys.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        raise ValueError("keys must be int64 or uint64 (the 64-bit key bit pattern)")
+    if not keys.is_contiguous():
+        raise ValueError("keys must be contiguous")
+    return keys.data_ptr(), keys.numel()
+
+
+class Filter:
+    """A filter whose bit array is a torch tensor (adopted by the library)."""
+
+    def __init__(self, num_blocks: int, block_bits: int = 256, word_bits: int = 32, k: int = 8,
+                 seed: int = 0, device=None, words=None):
+        import torch
+        self.params = bf_params(num_blocks, block_bits, word_bits, k, 0, seed)
+        self.nbytes = num_blocks * block_bits // 8
+        if words is None:
+            device = torch.device(device or "cuda")
+            words = torch.zeros(self.nbytes, dtype=torch.uint8, device=device)
+        if not words.is_cuda or words.numel() * words.element_size() != self.nbytes or not words.is_contiguous():
+            raise ValueError("words must be a contiguous CUDA tensor of num_blocks*block_bits/8 bytes")
+        self.words = words
+        self.device = words.device
+        with torch.cuda.device(self.device):
+            self.handle = _lib.bf_create(self.params, words.data_ptr())
+
+    # -- operations ------------------------------------------------------
+    def add(self, keys, stream=None) -> None:
+        ptr, n = _key_ptr(keys)
+        _lib.bf_add(self.handle, ptr, n, stream)
+
+    def contains(self, keys, out=None, stream=None):
+        import torch
+        ptr, n = _key_ptr(keys)
+        if out is None:
+            out = torch.empty(n, dtype=torch.bool, device=keys.device)
+        if out.numel() != n or out.element_size() != 1 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous 1-byte tensor with one element per key")
+        _lib.bf_contains(self.handle, ptr, n, out.data_ptr(), stream)
+        return out
+
+    def add_host(self, keys_np, stream=None) -> None:
+        """Construction from a host numpy uint64/int64 array (copied in chunks)."""
+        _lib.bf_add_host(self.handle, keys_np.ctypes.data, keys_np.size, stream)
+
+    def contains_host(self, keys_np, out_np, stream=None) -> None:
+        _lib.bf_contains_host(self.handle, keys_np.ctypes.data, keys_np.size, out_np.ctypes.data, stream)
+
+    def clear(self, stream=None) -> None:
+        _lib.bf_clear(self.handle, stream)
+
+    def set_layout(self, op: int, cg: int = 0, phi: int = 0, kpt: int = 0, block_threads: int = 0,
+                   grid_ctas: int = 0, flags: int = 0) -> None:
+        _lib.bf_set_layout(self.handle, op, bf_layout(cg, phi, kpt, block_threads, grid_ctas, flags))
+
+    def layout(self, op: int) -> dict:
+        return _lib.bf_get_layout(self.handle, op).as_dict()
+
+    def set_l2_persist(self, hit_ratio: float, stream=None) -> None:
+        _lib.bf_set_l2_persist(self.handle, hit_ratio, stream)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            _lib.bf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

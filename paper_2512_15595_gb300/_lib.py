@@ -1,0 +1,202 @@
+"""ctypes binding of libbloomgb.so (include/bloomgb.h).
+
+Argument marshalling only: every step of construction and lookup runs in the
+library's CUDA kernels.  The functions keep the C names; a non-OK status
+raises :class:`BloomError`.  If the library is missing this module raises on
+first use: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libbloomgb.so")
+
+BF_OK, BF_EINVAL, BF_ENOMEM, BF_ECUDA, BF_EUNSUPPORTED = range(5)
+BF_OP_ADD, BF_OP_CONTAINS = 0, 1
+BF_HINT_FILTER_EVICT_LAST = 1 << 0
+BF_HINT_KEYS_EVICT_NORMAL = 1 << 1
+BF_GUPS_LOAD, BF_GUPS_RED_OR = 0, 1
+
+# every symbol include/bloomgb.h declares
+EXPORTED = (
+    "bf_params_check", "bf_layout_check", "bf_create", "bf_destroy", "bf_clear", "bf_add",
+    "bf_contains", "bf_add_host", "bf_contains_host", "bf_set_staging", "bf_words",
+    "bf_get_params", "bf_set_layout", "bf_get_layout", "bf_set_l2_persist", "bf_gups",
+    "bf_launches_per_call", "bf_status_str", "bf_last_error", "bf_version",
+)
+
+
+class BloomError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS = {0: "BF_OK", 1: "BF_EINVAL", 2: "BF_ENOMEM", 3: "BF_ECUDA", 4: "BF_EUNSUPPORTED"}
+
+
+class bf_params(ctypes.Structure):
+    _fields_ = [("num_blocks", ctypes.c_uint64), ("block_bits", ctypes.c_uint32),
+                ("word_bits", ctypes.c_uint32), ("k", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class bf_layout(ctypes.Structure):
+    _fields_ = [("cg", ctypes.c_uint32), ("phi", ctypes.c_uint32), ("kpt", ctypes.c_uint32),
+                ("block_threads", ctypes.c_uint32), ("grid_ctas", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load the library (built by ``paper_2512_15595_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libbloomgb.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    u64, u32, vp, i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int
+    P, LY = ctypes.POINTER(bf_params), ctypes.POINTER(bf_layout)
+    sigs = {
+        "bf_params_check": (i32, [P]),
+        "bf_layout_check": (i32, [P, i32, LY]),
+        "bf_create": (i32, [P, vp, ctypes.POINTER(vp)]),
+        "bf_destroy": (i32, [vp]),
+        "bf_clear": (i32, [vp, vp]),
+        "bf_add": (i32, [vp, vp, u64, vp]),
+        "bf_contains": (i32, [vp, vp, u64, vp, vp]),
+        "bf_add_host": (i32, [vp, vp, u64, vp]),
+        "bf_contains_host": (i32, [vp, vp, u64, vp, vp]),
+        "bf_set_staging": (i32, [vp, u64]),
+        "bf_words": (i32, [vp, ctypes.POINTER(vp), ctypes.POINTER(u64)]),
+        "bf_get_params": (i32, [vp, P]),
+        "bf_set_layout": (i32, [vp, i32, LY]),
+        "bf_get_layout": (i32, [vp, i32, LY]),
+        "bf_set_l2_persist": (i32, [vp, vp, ctypes.c_float]),
+        "bf_gups": (i32, [i32, vp, u64, u32, vp, u64, vp, LY, vp]),
+        "bf_launches_per_call": (u32, []),
+        "bf_status_str": (ctypes.c_char_p, [i32]),
+        "bf_last_error": (ctypes.c_char_p, []),
+        "bf_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != BF_OK:
+        raise BloomError(status, where, lib().bf_last_error().decode())
+
+
+def _stream(stream) -> int | None:
+    """A torch.cuda.Stream, a raw handle (int) or None (torch's current stream)."""
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# C entry points, same names
+# ---------------------------------------------------------------------------
+def bf_params_check(p: bf_params) -> int:
+    return lib().bf_params_check(ctypes.byref(p))
+
+
+def bf_layout_check(p: bf_params, op: int, layout: bf_layout | None) -> int:
+    return lib().bf_layout_check(ctypes.byref(p), op, ctypes.byref(layout) if layout else None)
+
+
+def bf_create(p: bf_params, d_words: int | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().bf_create(ctypes.byref(p), d_words, ctypes.byref(h)), "bf_create")
+    return h.value
+
+
+def bf_destroy(f: int) -> None:
+    _check(lib().bf_destroy(f), "bf_destroy")
+
+
+def bf_clear(f: int, stream=None) -> None:
+    _check(lib().bf_clear(f, _stream(stream)), "bf_clear")
+
+
+def bf_add(f: int, d_keys: int, n: int, stream=None) -> None:
+    _check(lib().bf_add(f, d_keys, n, _stream(stream)), "bf_add")
+
+
+def bf_contains(f: int, d_keys: int, n: int, d_out: int, stream=None) -> None:
+    _check(lib().bf_contains(f, d_keys, n, d_out, _stream(stream)), "bf_contains")
+
+
+def bf_add_host(f: int, h_keys: int, n: int, stream=None) -> None:
+    _check(lib().bf_add_host(f, h_keys, n, _stream(stream)), "bf_add_host")
+
+
+def bf_contains_host(f: int, h_keys: int, n: int, h_out: int, stream=None) -> None:
+    _check(lib().bf_contains_host(f, h_keys, n, h_out, _stream(stream)), "bf_contains_host")
+
+
+def bf_set_staging(f: int, chunk_keys: int) -> None:
+    _check(lib().bf_set_staging(f, chunk_keys), "bf_set_staging")
+
+
+def bf_words(f: int) -> tuple[int, int]:
+    p, n = ctypes.c_void_p(), ctypes.c_uint64()
+    _check(lib().bf_words(f, ctypes.byref(p), ctypes.byref(n)), "bf_words")
+    return p.value, n.value
+
+
+def bf_get_params(f: int) -> bf_params:
+    p = bf_params()
+    _check(lib().bf_get_params(f, ctypes.byref(p)), "bf_get_params")
+    return p
+
+
+def bf_set_layout(f: int, op: int, layout: bf_layout) -> None:
+    _check(lib().bf_set_layout(f, op, ctypes.byref(layout)), "bf_set_layout")
+
+
+def bf_get_layout(f: int, op: int) -> bf_layout:
+    out = bf_layout()
+    _check(lib().bf_get_layout(f, op, ctypes.byref(out)), "bf_get_layout")
+    return out
+
+
+def bf_set_l2_persist(f: int, hit_ratio: float, stream=None) -> None:
+    _check(lib().bf_set_l2_persist(f, _stream(stream), hit_ratio), "bf_set_l2_persist")
+
+
+def bf_gups(mode: int, d_table: int, table_bytes: int, unit_bytes: int, d_keys: int, n: int,
+            d_out: int | None, layout: bf_layout | None = None, stream=None) -> None:
+    _check(lib().bf_gups(mode, d_table, table_bytes, unit_bytes, d_keys, n, d_out,
+                         ctypes.byref(layout) if layout else None, _stream(stream)), "bf_gups")
+
+
+def bf_launches_per_call() -> int:
+    return lib().bf_launches_per_call()
+
+
+def bf_status_str(s: int) -> str:
+    return lib().bf_status_str(s).decode()
+
+
+def bf_last_error() -> str:
+    return lib().bf_last_error().decode()
+
+
+def bf_version() -> str:
+    return lib().bf_version().decode()

@@ -1,0 +1,106 @@
+"""Autotuner for the execution layout of construction and lookup.
+
+The paper tunes the layout offline per block size, memory regime and GPU
+(Sec. V-A: best over all valid (Theta, Phi); Sec. V-D: the optimum differs
+across architectures).  This module times every compiled layout (Theta, Phi,
+keys per thread) of one geometry through the C ABI with CUDA events, keeps
+the fastest per operation, and stores the choice in ``tuned_layouts.json``
+next to this file, keyed by geometry and residency regime.  Filters built
+through :func:`apply_tuned` start from that choice.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import BF_OP_ADD, BF_OP_CONTAINS, Filter, valid_layouts
+
+TUNED_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_layouts.json")
+
+
+def regime_of(nbytes: int, l2_bytes: int) -> str:
+    """'l2' if the bit array fits in half the L2, else 'hbm'."""
+    return "l2" if nbytes * 2 <= l2_bytes else "hbm"
+
+
+def key_of(block_bits: int, word_bits: int, k: int, regime: str) -> str:
+    return f"B{block_bits}_S{word_bits}_K{k}_{regime}"
+
+
+def load_tuned() -> dict:
+    if os.path.exists(TUNED_PATH):
+        with open(TUNED_PATH) as f:
+            return json.load(f)
+    return {}
+
+
+def save_tuned(table: dict) -> None:
+    tmp = TUNED_PATH + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, TUNED_PATH)
+
+
+def tuned_layout(block_bits: int, word_bits: int, k: int, regime: str, op: int) -> dict | None:
+    entry = load_tuned().get(key_of(block_bits, word_bits, k, regime))
+    if not entry:
+        return None
+    return entry.get("add" if op == BF_OP_ADD else "contains", {}).get("layout")
+
+
+def apply_tuned(f: Filter, regime: str) -> dict:
+    """Set the filter's layouts from the tuned table (if it has an entry)."""
+    p = f.params
+    used = {}
+    for op, name in ((BF_OP_ADD, "add"), (BF_OP_CONTAINS, "contains")):
+        lay = tuned_layout(p.block_bits, p.word_bits, p.k, regime, op)
+        if lay:
+            f.set_layout(op, **lay)
+        used[name] = f.layout(op)
+    return used
+
+
+def time_op(torch, f: Filter, op: int, keys, out, reps: int = 5, warmup: int = 2, flush=None) -> float:
+    """Median device time (ms) of one bulk call with the filter's current layout."""
+    stream = torch.cuda.current_stream()
+    times = []
+    for i in range(warmup + reps):
+        if flush is not None:
+            flush()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        if op == BF_OP_ADD:
+            f.add(keys)
+        else:
+            f.contains(keys, out=out)
+        e.record(stream)
+        e.synchronize()
+        if i >= warmup:
+            times.append(s.elapsed_time(e))
+    times.sort()
+    return times[len(times) // 2]
+
+
+def sweep(torch, f: Filter, keys_add, keys_q, out, regime: str, kpts=(1, 2, 4), block_threads=(256,),
+          flags=0, reps: int = 5, flush=None, log=None) -> dict:
+    """Time every layout of both operations; returns the table entry (and rows)."""
+    p = f.params
+    rows = []
+    best = {}
+    for op, name, keys in ((BF_OP_ADD, "add", keys_add), (BF_OP_CONTAINS, "contains", keys_q)):
+        for cg, phi in valid_layouts(p.block_bits, p.word_bits):
+            for kpt in kpts:
+                for bt in block_threads:
+                    lay = dict(cg=cg, phi=phi, kpt=kpt, block_threads=bt, flags=flags)
+                    f.set_layout(op, **lay)
+                    ms = time_op(torch, f, op, keys, out, reps=reps, flush=flush)
+                    g = keys.numel() / (ms * 1e-3) / 1e9
+                    row = dict(op=name, gkeys_s=g, ms=ms, **lay)
+                    rows.append(row)
+                    if log:
+                        log(row)
+                    if name not in best or g > best[name]["gkeys_s"]:
+                        best[name] = dict(gkeys_s=g, layout=lay)
+    entry = {"add": best["add"], "contains": best["contains"],
+             "n_add": keys_add.numel(), "n_contains": keys_q.numel(), "filter_bytes": f.nbytes}
+    return {"key": key_of(p.block_bits, p.word_bits, p.k, regime), "entry": entry, "rows": rows}

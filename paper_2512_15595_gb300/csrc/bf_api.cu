@@ -1,0 +1,545 @@
+// Host side of the C ABI declared in include/bloomgb.h: argument checks,
+// layout resolution, kernel dispatch, L2 persistence and the host-buffer
+// pipeline.  Every compute step runs in the kernels of sbf_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "bloomgb.h"
+#include "registry.h"
+
+namespace bloomgb {
+constexpr int kMaxBlockThreadsHost = 512;  // matches kMaxBlockThreads of the kernels
+}
+
+using namespace bloomgb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bf_status fail(bf_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+bf_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return BF_ECUDA;
+}
+
+bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+struct Registry {
+  std::vector<KernelEntry> sbf;
+  std::vector<GupsEntry> gups;
+};
+
+const Registry& registry() {
+  static const Registry r = [] {
+    Registry reg;
+#define BLOOMGB_REGISTER(B, S) register_B##B##_S##S(reg.sbf);
+    BLOOMGB_GEOMETRIES(BLOOMGB_REGISTER)
+#undef BLOOMGB_REGISTER
+    register_gups(reg.gups);
+    return reg;
+  }();
+  return r;
+}
+
+const KernelEntry* find_sbf(int op, const bf_params& p, const bf_layout& l) {
+  for (const auto& e : registry().sbf) {
+    if (e.op == op && e.B == static_cast<int>(p.block_bits) && e.S == static_cast<int>(p.word_bits) &&
+        e.K == static_cast<int>(p.k) && e.theta == static_cast<int>(l.cg) &&
+        e.phi == static_cast<int>(l.phi) && e.kpt == static_cast<int>(l.kpt))
+      return &e;
+  }
+  return nullptr;
+}
+
+const GupsEntry* find_gups(int mode, uint32_t unit, uint32_t kpt) {
+  for (const auto& e : registry().gups)
+    if (e.mode == mode && e.unit_bytes == static_cast<int>(unit) && e.kpt == static_cast<int>(kpt)) return &e;
+  return nullptr;
+}
+
+// Resident CTAs per SM for a kernel at a CTA size (cached per device).
+std::mutex g_occ_mu;
+std::unordered_map<std::string, int> g_occ;
+
+bf_status resident_ctas(const void* fn, int threads, int device, int* out) {
+  char key[96];
+  std::snprintf(key, sizeof key, "%p/%d/%d", fn, threads, device);
+  {
+    std::lock_guard<std::mutex> g(g_occ_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) {
+      *out = it->second;
+      return BF_OK;
+    }
+  }
+  int n = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (n < 1) return fail(BF_EINVAL, "kernel cannot run at this CTA size");
+  std::lock_guard<std::mutex> g(g_occ_mu);
+  g_occ[key] = n;
+  *out = n;
+  return BF_OK;
+}
+
+bf_status sm_count(int device, int* out) {
+  cudaError_t e = cudaDeviceGetAttribute(out, cudaDevAttrMultiProcessorCount, device);
+  return e == cudaSuccess ? BF_OK : cuda_fail(e, "cudaDeviceGetAttribute(SM count)");
+}
+
+// grid: at most the resident capacity (a persistent, grid-stride launch),
+// and no more CTAs than there are tiles of work.
+bf_status resolve_grid(const void* fn, int device, uint32_t threads, uint32_t grid_req, uint64_t n,
+                       uint32_t kpt, uint32_t* grid_out) {
+  uint64_t tiles = (n + 32ull * kpt - 1) / (32ull * kpt);
+  uint64_t ctas_needed = (tiles + threads / 32 - 1) / (threads / 32);
+  uint64_t g = grid_req;
+  if (g == 0) {
+    int sms = 0, per_sm = 0;
+    bf_status s = sm_count(device, &sms);
+    if (s != BF_OK) return s;
+    s = resident_ctas(fn, static_cast<int>(threads), device, &per_sm);
+    if (s != BF_OK) return s;
+    g = static_cast<uint64_t>(sms) * per_sm;
+  }
+  g = std::min<uint64_t>(g, std::max<uint64_t>(ctas_needed, 1));
+  g = std::min<uint64_t>(g, 0x7FFFFFFFull);
+  *grid_out = static_cast<uint32_t>(g);
+  return BF_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+constexpr int kPipelineDepth = 3;
+
+}  // namespace
+
+struct bf_filter {
+  bf_params p{};
+  void* words = nullptr;
+  uint64_t nbytes = 0;
+  bool owned = false;
+  int device = 0;
+  bf_layout layout[2]{};
+  const KernelEntry* entry[2]{};
+  // host-buffer pipeline
+  uint64_t chunk_keys = 1ull << 24;
+  void* staging = nullptr;  // kPipelineDepth x (chunk_keys*8 + chunk_keys) bytes
+  cudaStream_t pipe[kPipelineDepth]{};
+  cudaEvent_t ev_start = nullptr;
+  cudaEvent_t ev_done[kPipelineDepth]{};
+  bool l2_window = false;
+};
+
+namespace {
+
+bf_status check_params(const bf_params* p) {
+  if (!p) return fail(BF_EINVAL, "params is NULL");
+  if (p->reserved != 0) return fail(BF_EINVAL, "params.reserved must be 0");
+  if (p->num_blocks == 0) return fail(BF_EINVAL, "num_blocks must be >= 1");
+  if (p->word_bits != 32 && p->word_bits != 64) return fail(BF_EINVAL, "word_bits must be 32 or 64");
+  if (!is_pow2(p->block_bits) || p->block_bits < p->word_bits || p->block_bits > 1024)
+    return fail(BF_EINVAL, "block_bits must be a power of two in [word_bits, 1024]");
+  const uint32_t s = p->block_bits / p->word_bits;
+  if (p->k < s || p->k % s != 0 || p->k > 64)
+    return fail(BF_EINVAL, "k must be a multiple of s = block_bits/word_bits, s <= k <= 64");
+  if (p->num_blocks > (~0ull) / 128) return fail(BF_EINVAL, "num_blocks too large");
+  return BF_OK;
+}
+
+bf_layout default_layout(const bf_params& p, int op) {
+  const uint32_t s = p.block_bits / p.word_bits;
+  bf_layout l{};
+  if (op == BF_OP_ADD) {
+    // Sec. V-B: a fully horizontal layout (Theta = s) coalesces the atomics
+    l.cg = s;
+    l.phi = 1;
+    l.kpt = 1;
+  } else {
+    // Sec. V-B: lookup favours one thread per 32-byte sector
+    uint32_t cg = std::max<uint32_t>(1, p.block_bits / 256);
+    l.cg = std::min(cg, s);
+    l.phi = s / l.cg;
+    l.kpt = 2;
+  }
+  l.block_threads = 256;
+  l.grid_ctas = 0;
+  l.flags = 0;
+  return l;
+}
+
+bf_status resolve_layout(const bf_params& p, int op, const bf_layout* in, bf_layout* out,
+                         const KernelEntry** entry) {
+  if (op != BF_OP_ADD && op != BF_OP_CONTAINS) return fail(BF_EINVAL, "op must be BF_OP_ADD or BF_OP_CONTAINS");
+  const uint32_t s = p.block_bits / p.word_bits;
+  bf_layout d = default_layout(p, op);
+  bf_layout l = in ? *in : d;
+  if (l.cg == 0) l.cg = d.cg;
+  if (l.phi == 0) l.phi = std::max<uint32_t>(1, s / l.cg);
+  if (l.kpt == 0) l.kpt = d.kpt;
+  if (l.block_threads == 0) l.block_threads = d.block_threads;
+  if (!is_pow2(l.cg) || !is_pow2(l.phi) || static_cast<uint64_t>(l.cg) * l.phi > s)
+    return fail(BF_EINVAL, "layout needs powers of two with 1 <= cg*phi <= s");
+  if (l.kpt != 1 && l.kpt != 2 && l.kpt != 4) return fail(BF_EINVAL, "kpt must be 1, 2 or 4");
+  if (l.block_threads % 32 != 0 || l.block_threads > static_cast<uint32_t>(kMaxBlockThreadsHost))
+    return fail(BF_EINVAL, "block_threads must be a multiple of 32 and <= 512");
+  if (l.flags & ~(BF_HINT_FILTER_EVICT_LAST | BF_HINT_KEYS_EVICT_NORMAL))
+    return fail(BF_EINVAL, "unknown layout flag");
+  const KernelEntry* e = find_sbf(op, p, l);
+  if (!e) return fail(BF_EUNSUPPORTED, "no compiled kernel for this geometry and layout");
+  *out = l;
+  if (entry) *entry = e;
+  return BF_OK;
+}
+
+bf_status launch_sbf(const bf_filter* f, int op, const uint64_t* keys, uint64_t n, uint8_t* out,
+                     cudaStream_t stream) {
+  const bf_layout& l = f->layout[op];
+  const KernelEntry* e = f->entry[op];
+  uint32_t grid = 0;
+  bf_status s = resolve_grid(e->fn, f->device, l.block_threads, l.grid_ctas, n, l.kpt, &grid);
+  if (s != BF_OK) return s;
+  SbfArgs a{f->words, f->p.num_blocks, keys, n, out, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, l.flags,
+            f->p.num_blocks < (1ull << 32) ? 0 : (f->p.num_blocks == (1ull << 32) ? 1 : 2)};
+  void* args[] = {&a};
+  cudaError_t err = cudaLaunchKernel(e->fn, dim3(grid), dim3(l.block_threads), args, 0, stream);
+  if (err != cudaSuccess) return cuda_fail(err, op == BF_OP_ADD ? "launch add kernel" : "launch contains kernel");
+  return BF_OK;
+}
+
+bf_status ensure_pipeline(bf_filter* f) {
+  if (f->staging) return BF_OK;
+  const uint64_t per = f->chunk_keys * 9;
+  cudaError_t e = cudaMalloc(&f->staging, per * kPipelineDepth);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    f->staging = nullptr;
+    return fail(BF_ENOMEM, "staging allocation failed");
+  }
+  for (int i = 0; i < kPipelineDepth; ++i) {
+    if (!f->pipe[i] && (e = cudaStreamCreateWithFlags(&f->pipe[i], cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamCreate");
+    if (!f->ev_done[i] && (e = cudaEventCreateWithFlags(&f->ev_done[i], cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreate");
+  }
+  if (!f->ev_start && (e = cudaEventCreateWithFlags(&f->ev_start, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventCreate");
+  return BF_OK;
+}
+
+void release_pipeline(bf_filter* f) {
+  if (f->staging) cudaFree(f->staging);
+  f->staging = nullptr;
+  for (int i = 0; i < kPipelineDepth; ++i) {
+    if (f->pipe[i]) cudaStreamDestroy(f->pipe[i]);
+    if (f->ev_done[i]) cudaEventDestroy(f->ev_done[i]);
+    f->pipe[i] = nullptr;
+    f->ev_done[i] = nullptr;
+  }
+  if (f->ev_start) cudaEventDestroy(f->ev_start);
+  f->ev_start = nullptr;
+}
+
+// Chunked host->device pipeline: chunk c runs entirely on stream c % depth
+// (copy in, kernel, copy out), so its staging slot is reused in order; the
+// depth-many streams overlap one chunk's copies with another's kernel.
+bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
+                        cudaStream_t stream) {
+  bf_status s = ensure_pipeline(f);
+  if (s != BF_OK) return s;
+  cudaError_t e = cudaEventRecord(f->ev_start, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  for (int i = 0; i < kPipelineDepth; ++i)
+    if ((e = cudaStreamWaitEvent(f->pipe[i], f->ev_start, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+  const uint64_t per = f->chunk_keys * 9;
+  uint64_t c = 0;
+  for (uint64_t lo = 0; lo < n; lo += f->chunk_keys, ++c) {
+    const uint64_t cnt = std::min(f->chunk_keys, n - lo);
+    const int slot = static_cast<int>(c % kPipelineDepth);
+    cudaStream_t st = f->pipe[slot];
+    uint64_t* d_keys = reinterpret_cast<uint64_t*>(static_cast<char*>(f->staging) + slot * per);
+    uint8_t* d_out = reinterpret_cast<uint8_t*>(d_keys + f->chunk_keys);
+    if ((e = cudaMemcpyAsync(d_keys, h_keys + lo, cnt * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync H2D");
+    if ((s = launch_sbf(f, op, d_keys, cnt, d_out, st)) != BF_OK) return s;
+    if (op == BF_OP_CONTAINS &&
+        (e = cudaMemcpyAsync(h_out + lo, d_out, cnt, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync D2H");
+  }
+  for (int i = 0; i < kPipelineDepth; ++i) {
+    if ((e = cudaEventRecord(f->ev_done[i], f->pipe[i])) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(stream, f->ev_done[i], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+  }
+  return BF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_params_check(const bf_params* params) {
+  bf_status s = check_params(params);
+  if (s != BF_OK) return s;
+  bf_layout l{};
+  for (int op = 0; op < 2; ++op) {
+    s = resolve_layout(*params, op, nullptr, &l, nullptr);
+    if (s != BF_OK) return s;
+  }
+  return BF_OK;
+}
+
+bf_status bf_layout_check(const bf_params* params, int op, const bf_layout* layout) {
+  bf_status s = check_params(params);
+  if (s != BF_OK) return s;
+  bf_layout l{};
+  return resolve_layout(*params, op, layout, &l, nullptr);
+}
+
+bf_status bf_create(const bf_params* params, void* d_words, bf_filter** out) {
+  if (!out) return fail(BF_EINVAL, "out is NULL");
+  *out = nullptr;
+  bf_status s = bf_params_check(params);
+  if (s != BF_OK) return s;
+  bf_filter* f = new (std::nothrow) bf_filter();
+  if (!f) return fail(BF_ENOMEM, "host allocation failed");
+  f->p = *params;
+  f->nbytes = params->num_blocks * (params->block_bits / 8);
+  cudaError_t e = cudaGetDevice(&f->device);
+  if (e != cudaSuccess) {
+    delete f;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  for (int op = 0; op < 2; ++op) resolve_layout(f->p, op, nullptr, &f->layout[op], &f->entry[op]);
+  if (d_words) {
+    const uint64_t align = std::max<uint64_t>(32, params->block_bits / 8);
+    if (reinterpret_cast<uintptr_t>(d_words) % align != 0) {
+      delete f;
+      return fail(BF_EINVAL, "adopted buffer must be aligned to max(32, block_bits/8) bytes");
+    }
+    f->words = d_words;
+    f->owned = false;
+  } else {
+    e = cudaMalloc(&f->words, f->nbytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete f;
+      return fail(BF_ENOMEM, "cudaMalloc of the bit array failed");
+    }
+    f->owned = true;
+    e = cudaMemset(f->words, 0, f->nbytes);
+    if (e != cudaSuccess) {
+      cudaFree(f->words);
+      delete f;
+      return cuda_fail(e, "cudaMemset");
+    }
+  }
+  *out = f;
+  return BF_OK;
+}
+
+bf_status bf_destroy(bf_filter* f) {
+  if (!f) return fail(BF_EINVAL, "filter is NULL");
+  DeviceGuard g(f->device);
+  release_pipeline(f);
+  if (f->owned && f->words) cudaFree(f->words);
+  delete f;
+  return BF_OK;
+}
+
+bf_status bf_clear(bf_filter* f, bf_stream_t stream) {
+  if (!f) return fail(BF_EINVAL, "filter is NULL");
+  DeviceGuard g(f->device);
+  cudaError_t e = cudaMemsetAsync(f->words, 0, f->nbytes, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? BF_OK : cuda_fail(e, "cudaMemsetAsync");
+}
+
+bf_status bf_add(bf_filter* f, const uint64_t* d_keys, uint64_t n, bf_stream_t stream) {
+  if (!f) return fail(BF_EINVAL, "filter is NULL");
+  if (n == 0) return BF_OK;
+  if (!d_keys) return fail(BF_EINVAL, "keys is NULL");
+  if (reinterpret_cast<uintptr_t>(d_keys) % 8) return fail(BF_EINVAL, "keys must be 8-byte aligned");
+  DeviceGuard g(f->device);
+  return launch_sbf(f, BF_OP_ADD, d_keys, n, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, uint8_t* d_out,
+                      bf_stream_t stream) {
+  if (!f) return fail(BF_EINVAL, "filter is NULL");
+  if (n == 0) return BF_OK;
+  if (!d_keys || !d_out) return fail(BF_EINVAL, "keys or out is NULL");
+  if (reinterpret_cast<uintptr_t>(d_keys) % 8) return fail(BF_EINVAL, "keys must be 8-byte aligned");
+  DeviceGuard g(f->device);
+  return launch_sbf(f, BF_OP_CONTAINS, d_keys, n, d_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+bf_status bf_add_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, bf_stream_t stream) {
+  if (!f) return fail(BF_EINVAL, "filter is NULL");
+  if (n == 0) return BF_OK;
+  if (!h_keys) return fail(BF_EINVAL, "keys is NULL");
+  DeviceGuard g(f->device);
+  return host_pipeline(f, BF_OP_ADD, h_keys, n, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+bf_status bf_contains_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
+                           bf_stream_t stream) {
+  if (!f) return fail(BF_EINVAL, "filter is NULL");
+  if (n == 0) return BF_OK;
+  if (!h_keys || !h_out) return fail(BF_EINVAL, "keys or out is NULL");
+  DeviceGuard g(f->device);
+  return host_pipeline(f, BF_OP_CONTAINS, h_keys, n, h_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+bf_status bf_set_staging(bf_filter* f, uint64_t chunk_keys) {
+  if (!f) return fail(BF_EINVAL, "filter is NULL");
+  if (chunk_keys < 1024 || chunk_keys > (1ull << 32))
+    return fail(BF_EINVAL, "chunk_keys must be in [1024, 2^32]");
+  DeviceGuard g(f->device);
+  release_pipeline(f);
+  f->chunk_keys = chunk_keys;
+  return BF_OK;
+}
+
+bf_status bf_words(const bf_filter* f, void** d_ptr, uint64_t* nbytes) {
+  if (!f || !d_ptr || !nbytes) return fail(BF_EINVAL, "NULL argument");
+  *d_ptr = f->words;
+  *nbytes = f->nbytes;
+  return BF_OK;
+}
+
+bf_status bf_get_params(const bf_filter* f, bf_params* out) {
+  if (!f || !out) return fail(BF_EINVAL, "NULL argument");
+  *out = f->p;
+  return BF_OK;
+}
+
+bf_status bf_set_layout(bf_filter* f, int op, const bf_layout* layout) {
+  if (!f) return fail(BF_EINVAL, "filter is NULL");
+  bf_layout l{};
+  const KernelEntry* e = nullptr;
+  bf_status s = resolve_layout(f->p, op, layout, &l, &e);
+  if (s != BF_OK) return s;
+  f->layout[op] = l;
+  f->entry[op] = e;
+  return BF_OK;
+}
+
+bf_status bf_get_layout(const bf_filter* f, int op, bf_layout* out) {
+  if (!f || !out) return fail(BF_EINVAL, "NULL argument");
+  if (op != BF_OP_ADD && op != BF_OP_CONTAINS) return fail(BF_EINVAL, "bad op");
+  *out = f->layout[op];
+  return BF_OK;
+}
+
+bf_status bf_set_l2_persist(bf_filter* f, bf_stream_t stream, float hit_ratio) {
+  if (!f) return fail(BF_EINVAL, "filter is NULL");
+  DeviceGuard g(f->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaStreamAttrValue attr{};
+  cudaError_t e;
+  if (hit_ratio <= 0.f) {
+    attr.accessPolicyWindow.base_ptr = nullptr;
+    attr.accessPolicyWindow.num_bytes = 0;
+    attr.accessPolicyWindow.hitRatio = 0.f;
+    attr.accessPolicyWindow.hitProp = cudaAccessPropertyNormal;
+    attr.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
+    if ((e = cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &attr)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamSetAttribute");
+    if ((e = cudaCtxResetPersistingL2Cache()) != cudaSuccess) return cuda_fail(e, "cudaCtxResetPersistingL2Cache");
+    if ((e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaDeviceSetLimit");
+    f->l2_window = false;
+    return BF_OK;
+  }
+  if (hit_ratio > 1.f) hit_ratio = 1.f;
+  int max_persist = 0, max_window = 0;
+  cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, f->device);
+  cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, f->device);
+  if (max_persist <= 0 || max_window <= 0) return fail(BF_EUNSUPPORTED, "device has no L2 persistence");
+  const size_t limit = std::min<uint64_t>(f->nbytes, static_cast<uint64_t>(max_persist));
+  if ((e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, limit)) != cudaSuccess)
+    return cuda_fail(e, "cudaDeviceSetLimit");
+  attr.accessPolicyWindow.base_ptr = f->words;
+  attr.accessPolicyWindow.num_bytes = std::min<uint64_t>(f->nbytes, static_cast<uint64_t>(max_window));
+  attr.accessPolicyWindow.hitRatio = hit_ratio;
+  attr.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+  attr.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+  if ((e = cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &attr)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamSetAttribute");
+  f->l2_window = true;
+  return BF_OK;
+}
+
+bf_status bf_gups(int mode, void* d_table, uint64_t table_bytes, uint32_t unit_bytes, const uint64_t* d_keys,
+                  uint64_t n, uint8_t* d_out, const bf_layout* layout, bf_stream_t stream) {
+  if (mode != BF_GUPS_LOAD && mode != BF_GUPS_RED_OR) return fail(BF_EINVAL, "bad mode");
+  if (unit_bytes != 8 && unit_bytes != 32 && unit_bytes != 64 && unit_bytes != 128)
+    return fail(BF_EINVAL, "unit_bytes must be 8, 32, 64 or 128");
+  if (!d_table || table_bytes < unit_bytes) return fail(BF_EINVAL, "table too small");
+  if (reinterpret_cast<uintptr_t>(d_table) % std::max<uint32_t>(unit_bytes, 32) != 0)
+    return fail(BF_EINVAL, "table must be aligned to max(32, unit_bytes)");
+  if (n == 0) return BF_OK;
+  if (!d_keys || (mode == BF_GUPS_LOAD && !d_out)) return fail(BF_EINVAL, "keys or out is NULL");
+  if (reinterpret_cast<uintptr_t>(d_keys) % 8) return fail(BF_EINVAL, "keys must be 8-byte aligned");
+  const uint32_t kpt = (layout && layout->kpt) ? layout->kpt : 2;
+  const uint32_t threads = (layout && layout->block_threads) ? layout->block_threads : 256;
+  const uint32_t grid_req = layout ? layout->grid_ctas : 0;
+  if (threads % 32 || threads > static_cast<uint32_t>(kMaxBlockThreadsHost)) return fail(BF_EINVAL, "block_threads");
+  const GupsEntry* e = find_gups(mode, unit_bytes, kpt);
+  if (!e) return fail(BF_EINVAL, "kpt must be 1, 2 or 4");
+  int device = 0;
+  cudaError_t err = cudaGetDevice(&device);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
+  uint32_t grid = 0;
+  bf_status s = resolve_grid(e->fn, device, threads, grid_req, n, kpt, &grid);
+  if (s != BF_OK) return s;
+  const uint64_t nunits = table_bytes / unit_bytes;
+  GupsArgs a{d_table, nunits, d_keys, n, d_out, nunits < (1ull << 32) ? 0 : (nunits == (1ull << 32) ? 1 : 2)};
+  void* args[] = {&a};
+  err = cudaLaunchKernel(e->fn, dim3(grid), dim3(threads), args, 0, reinterpret_cast<cudaStream_t>(stream));
+  return err == cudaSuccess ? BF_OK : cuda_fail(err, "launch gups kernel");
+}
+
+uint32_t bf_launches_per_call(void) { return 1; }
+
+const char* bf_status_str(bf_status s) {
+  switch (s) {
+    case BF_OK: return "BF_OK";
+    case BF_EINVAL: return "BF_EINVAL";
+    case BF_ENOMEM: return "BF_ENOMEM";
+    case BF_ECUDA: return "BF_ECUDA";
+    case BF_EUNSUPPORTED: return "BF_EUNSUPPORTED";
+  }
+  return "unknown status";
+}
+
+const char* bf_last_error(void) { return g_last_error.c_str(); }
+
+const char* bf_version(void) { return "bloomgb 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,272 @@
+// Bulk construction and lookup kernels of the sectorized blocked Bloom filter.
+//
+// One template per operation, specialised at compile time on the geometry
+// (B block bits, S word bits, K pattern bits) and on the execution layout
+// (THETA threads per key, PHI words per thread per step, KPT keys per thread),
+// as Sec. IV-A/IV-B prescribe (salts and word offsets become literals).
+//
+// Work mapping (Sec. IV-C, work-efficient cooperation): a warp takes a tile of
+// 32*KPT consecutive keys, lane L owning keys [L*KPT, L*KPT+KPT).  Every lane
+// hashes its own keys once; each cooperative group (CG) of THETA lanes then
+// walks over its members' keys, receiving hash and block index by register
+// shuffles, and touches the key's block together: lane r of the CG handles
+// words q*THETA*PHI + r*PHI + [0, PHI) in step q.  Lookup results stay in the
+// owning lane and are written back as one packed store per lane.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "registry.h"
+#include "sbf_device.cuh"
+
+namespace bloomgb {
+
+enum : uint32_t { kHintFilterEvictLast = 1u << 0, kHintKeysEvictNormal = 1u << 1 };
+
+template <int B_, int S_, int K_, int THETA_, int PHI_, int KPT_>
+struct Cfg {
+  static constexpr int B = B_, S = S_, K = K_, THETA = THETA_, PHI = PHI_, KPT = KPT_;
+  using word_t = typename WordOf<S>::type;
+  static constexpr int s = B / S;            // words per block
+  static constexpr int kp = K / s;           // pattern bits per word
+  static constexpr int chunk = THETA * PHI;  // words the CG covers per step
+  static constexpr int steps = s / chunk;    // steps per block
+  static_assert(s >= 1 && B % S == 0, "geometry");
+  static_assert(K % s == 0 && K >= s && K <= kMaxSalts, "SBF needs s | K");
+  static_assert(THETA >= 1 && THETA <= 32 && (THETA & (THETA - 1)) == 0, "THETA");
+  static_assert(PHI >= 1 && (PHI & (PHI - 1)) == 0 && chunk <= s, "PHI");
+  static_assert(KPT == 1 || KPT == 2 || KPT == 4, "KPT");
+};
+
+constexpr unsigned kFullMask = 0xFFFFFFFFu;
+// CTA size bound the kernels are compiled for (leaves up to 128 registers per thread)
+constexpr int kMaxBlockThreads = 512;
+
+// Per-lane multipliers: salt index of (step q, word p, bit t) for CG rank r is
+// q*chunk + r*PHI + p + s*t.  For THETA == 1 these fold to literals.
+template <class C>
+struct LaneSalts {
+  typename C::word_t v[C::steps][C::PHI][C::kp];
+  __device__ __forceinline__ explicit LaneSalts(uint32_t r) {
+    static_for<C::steps>([&](auto q) {
+      static_for<C::PHI>([&](auto p) {
+        static_for<C::kp>([&](auto t) {
+          constexpr int Q = decltype(q)::value, P = decltype(p)::value, T = decltype(t)::value;
+          v[Q][P][T] = salt_select<C::S, Q * C::chunk + P + C::s * T, C::PHI, C::THETA>(r);
+        });
+      });
+    });
+  }
+  __device__ __forceinline__ typename C::word_t pattern(uint32_t hlo, int q, int p) const {
+    typename C::word_t pat = 0;
+#pragma unroll
+    for (int t = 0; t < C::kp; ++t) pat |= pattern_bit(hlo, v[q][p][t]);
+    return pat;
+  }
+};
+
+// Load the lane's KPT keys; returns the validity mask.
+template <int KPT>
+__device__ __forceinline__ uint32_t load_keys(const uint64_t* keys, uint64_t n, uint64_t base,
+                                              bool vec_ok, uint64_t pol, uint64_t (&key)[KPT]) {
+  if (vec_ok && base + KPT <= n) {
+    if constexpr (KPT == 1) key[0] = ld_key1(keys + base, pol);
+    else if constexpr (KPT == 2) ld_key2(keys + base, pol, key);
+    else ld_key4(keys + base, pol, key);
+    return (1u << KPT) - 1u;
+  }
+  uint32_t valid = 0;
+#pragma unroll
+  for (int u = 0; u < KPT; ++u) {
+    key[u] = 0;
+    if (base + u < n) {
+      key[u] = ld_key1(keys + base + u, pol);
+      valid |= 1u << u;
+    }
+  }
+  return valid;
+}
+
+template <class C>
+__global__ void __launch_bounds__(kMaxBlockThreads) sbf_contains_kernel(const SbfArgs a) {
+  using W = typename C::word_t;
+  constexpr int KPT = C::KPT, THETA = C::THETA, PHI = C::PHI, STEPS = C::steps;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t r = lane & (THETA - 1);
+  const uint32_t g0 = lane - r;
+  const LaneSalts<C> salts(r);
+  const uint64_t pol_keys = (a.flags & kHintKeysEvictNormal) ? policy_evict_normal() : policy_evict_first();
+  const uint64_t pol_filter = (a.flags & kHintFilterEvictLast) ? policy_evict_last() : policy_evict_normal();
+  const W* __restrict__ filter = static_cast<const W*>(a.filter);
+  constexpr uint64_t kTile = 32u * KPT;
+  const uint64_t ntiles = (a.n + kTile - 1) / kTile;
+  const uint64_t warps_per_cta = blockDim.x >> 5;
+  const uint64_t nwarps = static_cast<uint64_t>(gridDim.x) * warps_per_cta;
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(a.keys) % (8u * KPT) == 0) &&
+                      (reinterpret_cast<uintptr_t>(a.out) % KPT == 0);
+
+  for (uint64_t tile = blockIdx.x * warps_per_cta + (threadIdx.x >> 5); tile < ntiles; tile += nwarps) {
+    const uint64_t base = tile * kTile + static_cast<uint64_t>(lane) * KPT;
+    uint64_t key[KPT];
+    const uint32_t valid = load_keys<KPT>(a.keys, a.n, base, vec_ok, pol_keys, key);
+    uint32_t hlo[KPT];
+    uint64_t blk[KPT];
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+      const uint64_t h = xxh64_key(key[u], a.acc0);
+      hlo[u] = static_cast<uint32_t>(h);
+      // invalid (tail) keys read block 0, which always exists; their result is dropped
+      blk[u] = ((valid >> u) & 1u) ? block_of(h, a.nblocks, a.block_mode) : 0;
+    }
+    // phase 1: issue every load of the tile before any test (memory-level parallelism)
+    W data[KPT][THETA][STEPS][PHI];
+    uint32_t hk[KPT][THETA];
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+#pragma unroll
+      for (int m = 0; m < THETA; ++m) {
+        uint64_t bm = blk[u];
+        uint32_t hm = hlo[u];
+        if constexpr (THETA > 1) {
+          bm = __shfl_sync(kFullMask, bm, m, THETA);
+          hm = __shfl_sync(kFullMask, hm, m, THETA);
+        }
+        hk[u][m] = hm;
+        const W* bp = filter + bm * C::s + r * PHI;
+#pragma unroll
+        for (int q = 0; q < STEPS; ++q) ld_words<PHI>(bp + q * C::chunk, pol_filter, data[u][m][q]);
+      }
+    }
+    // phase 2: test every word against its pattern; AND across the CG
+    uint32_t res = 0;
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+#pragma unroll
+      for (int m = 0; m < THETA; ++m) {
+        W miss = 0;
+#pragma unroll
+        for (int q = 0; q < STEPS; ++q) {
+#pragma unroll
+          for (int p = 0; p < PHI; ++p) {
+            const W pat = salts.pattern(hk[u][m], q, p);
+            miss |= pat & ~data[u][m][q][p];
+          }
+        }
+        bool ok = (miss == 0);
+        if constexpr (THETA > 1) {
+          const uint32_t seg = (__ballot_sync(kFullMask, ok) >> g0) & ((1u << THETA) - 1u);
+          ok = (seg == (1u << THETA) - 1u);
+          ok = ok && (r == static_cast<uint32_t>(m));
+        }
+        res |= static_cast<uint32_t>(ok) << u;
+      }
+    }
+    // coalesced write-back of the lane's own results
+    if (vec_ok && valid == (1u << KPT) - 1u) {
+      if constexpr (KPT == 1) st_out1(a.out + base, res);
+      else if constexpr (KPT == 2) st_out2(a.out + base, (res & 1u) | ((res & 2u) << 7));
+      else st_out4(a.out + base, (res & 1u) | ((res & 2u) << 7) | ((res & 4u) << 14) | ((res & 8u) << 21));
+    } else {
+#pragma unroll
+      for (int u = 0; u < KPT; ++u)
+        if ((valid >> u) & 1u) st_out1(a.out + base + u, (res >> u) & 1u);
+    }
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(kMaxBlockThreads) sbf_add_kernel(const SbfArgs a) {
+  using W = typename C::word_t;
+  constexpr int KPT = C::KPT, THETA = C::THETA, PHI = C::PHI, STEPS = C::steps;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t r = lane & (THETA - 1);
+  const LaneSalts<C> salts(r);
+  const uint64_t pol_keys = (a.flags & kHintKeysEvictNormal) ? policy_evict_normal() : policy_evict_first();
+  const uint64_t pol_filter = (a.flags & kHintFilterEvictLast) ? policy_evict_last() : policy_evict_normal();
+  W* __restrict__ filter = static_cast<W*>(a.filter);
+  constexpr uint64_t kTile = 32u * KPT;
+  const uint64_t ntiles = (a.n + kTile - 1) / kTile;
+  const uint64_t warps_per_cta = blockDim.x >> 5;
+  const uint64_t nwarps = static_cast<uint64_t>(gridDim.x) * warps_per_cta;
+  const bool vec_ok = reinterpret_cast<uintptr_t>(a.keys) % (8u * KPT) == 0;
+
+  for (uint64_t tile = blockIdx.x * warps_per_cta + (threadIdx.x >> 5); tile < ntiles; tile += nwarps) {
+    const uint64_t base = tile * kTile + static_cast<uint64_t>(lane) * KPT;
+    uint64_t key[KPT];
+    const uint32_t valid = load_keys<KPT>(a.keys, a.n, base, vec_ok, pol_keys, key);
+    uint32_t hlo[KPT];
+    uint64_t blk[KPT];
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+      const uint64_t h = xxh64_key(key[u], a.acc0);
+      hlo[u] = static_cast<uint32_t>(h);
+      blk[u] = block_of(h, a.nblocks, a.block_mode);
+    }
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+#pragma unroll
+      for (int m = 0; m < THETA; ++m) {
+        uint64_t bm = blk[u];
+        uint32_t hm = hlo[u];
+        uint32_t vm = valid;
+        if constexpr (THETA > 1) {
+          bm = __shfl_sync(kFullMask, bm, m, THETA);
+          hm = __shfl_sync(kFullMask, hm, m, THETA);
+          vm = __shfl_sync(kFullMask, vm, m, THETA);
+        }
+        if ((vm >> u) & 1u) {
+          // the CG's lanes update neighbouring words of one block in the same
+          // instruction, so L1 merges them into one request per sector
+          W* bp = filter + bm * C::s + r * PHI;
+#pragma unroll
+          for (int q = 0; q < STEPS; ++q) {
+#pragma unroll
+            for (int p = 0; p < PHI; ++p) red_or(bp + q * C::chunk + p, salts.pattern(hm, q, p), pol_filter);
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// kernel registry
+// ---------------------------------------------------------------------------
+template <class F, int... I>
+__host__ void host_static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__host__ void host_static_for(F&& f) {
+  host_static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+template <int B, int S, int K>
+void register_k(std::vector<KernelEntry>& v) {
+  constexpr int s = B / S;
+  host_static_for<ilog2(s) + 1>([&](auto lt) {
+    constexpr int T = 1 << decltype(lt)::value;
+    host_static_for<ilog2(s / T) + 1>([&](auto lp) {
+      constexpr int P = 1 << decltype(lp)::value;
+      host_static_for<3>([&](auto lk) {
+        constexpr int KPT = 1 << decltype(lk)::value;
+        using C = Cfg<B, S, K, T, P, KPT>;
+        v.push_back({0, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_add_kernel<C>)});
+        v.push_back({1, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_contains_kernel<C>)});
+      });
+    });
+  });
+}
+
+template <int B, int S>
+void register_geometry(std::vector<KernelEntry>& v) {
+  constexpr int s = B / S;
+  if constexpr (4 % s == 0) register_k<B, S, 4>(v);
+  if constexpr (s <= 8) register_k<B, S, 8>(v);
+  if constexpr (s <= 16) register_k<B, S, 16>(v);
+}
+
+}  // namespace bloomgb

@@ -1,0 +1,319 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact on the filter's bit array and on every per-query result, for every
+compiled geometry and every valid (Theta, Phi) layout with every keys-per-
+thread value, on seeded synthetic keys, including ragged tails, single-block
+filters, misaligned pointers and both residency regimes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthkeys
+from conftest import gpu_available
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+GEOMETRIES = [(64, 32), (128, 32), (256, 32), (512, 32), (64, 64), (128, 64), (256, 64), (512, 64), (1024, 64)]
+
+
+def compiled_geometries():
+    for B, S in GEOMETRIES:
+        s = B // S
+        for k in (4, 8, 16):
+            if k >= s and k % s == 0:
+                yield B, S, k
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    from paper_2512_15595_gb300 import build
+    build.build()
+    return t
+
+
+def dev_keys(torch, keys_u64):
+    return torch.from_numpy(np.ascontiguousarray(keys_u64).view(np.int64)).cuda()
+
+
+def gpu_filter(geom, torch):
+    from paper_2512_15595_gb300 import Filter
+    return Filter(geom.num_blocks, geom.block_bits, geom.word_bits, geom.k, geom.seed)
+
+
+def words_np(f):
+    return f.words.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# the 1 MiB workload: 2^15 x 256-bit blocks, S = 32, k = 8, 10^6 keys
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cfg1():
+    geom = oracle.Geometry(num_blocks=1 << 15, block_bits=256, word_bits=32, k=8, seed=0)
+    ins = synthkeys.insert_keys(10**6)
+    q, is_mem = synthkeys.mixed_queries(10**6, 500_000, 500_000)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    return geom, ins, q, is_mem, ref, ref.contains(q)
+
+
+@pytest.mark.parametrize("kpt", [1, 2, 4])
+def test_cfg1_every_layout_bit_exact(torch, cfg1, kpt):
+    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS, valid_layouts
+    geom, ins, q, is_mem, ref, ref_out = cfg1
+    dk, dq = dev_keys(torch, ins), dev_keys(torch, q)
+    for cg, phi in valid_layouts(256, 32):
+        f = gpu_filter(geom, torch)
+        f.set_layout(BF_OP_ADD, cg=cg, phi=phi, kpt=kpt)
+        f.set_layout(BF_OP_CONTAINS, cg=cg, phi=phi, kpt=kpt)
+        f.add(dk)
+        out = f.contains(dq)
+        torch.cuda.synchronize()
+        assert np.array_equal(words_np(f), ref.as_bytes()), (cg, phi, kpt)
+        got = out.cpu().numpy().astype(np.uint8)
+        assert np.array_equal(got, ref_out), (cg, phi, kpt)
+        assert got[is_mem == 1].all()  # no false negatives
+        f.close()
+
+
+def test_cfg1_fpr_in_band(torch, cfg1):
+    geom, ins, q, is_mem, ref, ref_out = cfg1
+    f = gpu_filter(geom, torch)
+    f.add(dev_keys(torch, ins))
+    out = f.contains(dev_keys(torch, q)).cpu().numpy()
+    fresh = is_mem == 0
+    measured = out[fresh].mean()
+    realized = oracle.fpr_given_filter(ref.words, geom)
+    assert abs(measured - realized) <= oracle.binomial_3sigma(realized, int(fresh.sum()))
+
+
+# ---------------------------------------------------------------------------
+# every compiled geometry x layout x keys-per-thread, ragged sizes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("B,S,k", list(compiled_geometries()))
+def test_every_geometry_layout_bit_exact(torch, B, S, k):
+    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS, valid_layouts
+    geom = oracle.Geometry(num_blocks=1009, block_bits=B, word_bits=S, k=k, seed=0xABCDEF)
+    n_ins = 1009 * B // 12 + 17
+    ins = synthkeys.insert_keys(n_ins, seed=11)
+    q, _ = synthkeys.mixed_queries(n_ins, 1500, 2505, seed_insert=11)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    ref_out = ref.contains(q)
+    dk, dq = dev_keys(torch, ins), dev_keys(torch, q)
+    for cg, phi in valid_layouts(B, S):
+        for kpt in (1, 2, 4):
+            f = gpu_filter(geom, torch)
+            f.set_layout(BF_OP_ADD, cg=cg, phi=phi, kpt=kpt, block_threads=128)
+            f.set_layout(BF_OP_CONTAINS, cg=cg, phi=phi, kpt=kpt, block_threads=128)
+            f.add(dk)
+            out = f.contains(dq)
+            assert np.array_equal(words_np(f), ref.as_bytes()), (cg, phi, kpt)
+            assert np.array_equal(out.cpu().numpy().astype(np.uint8), ref_out), (cg, phi, kpt)
+            f.close()
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 127, 129, 1000])
+@pytest.mark.parametrize("b", [1, 7])
+def test_small_and_ragged(torch, n, b):
+    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS
+    geom = oracle.Geometry(num_blocks=b, block_bits=256, word_bits=32, k=8, seed=5)
+    ins = synthkeys.insert_keys(n, seed=21)
+    q = synthkeys.splitmix64(22, 0, n + 3)
+    q[: n // 2] = ins[: n // 2]
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    for cg, kpt in [(1, 4), (8, 1), (2, 2)]:
+        f = gpu_filter(geom, torch)
+        f.set_layout(BF_OP_ADD, cg=cg, kpt=kpt)
+        f.set_layout(BF_OP_CONTAINS, cg=cg, kpt=kpt)
+        if n:
+            f.add(dev_keys(torch, ins))
+        else:
+            f.add(torch.empty(0, dtype=torch.int64, device="cuda"))
+        out = f.contains(dev_keys(torch, q))
+        assert np.array_equal(words_np(f), ref.as_bytes())
+        assert np.array_equal(out.cpu().numpy().astype(np.uint8), ref.contains(q))
+        f.close()
+
+
+def test_misaligned_pointers_and_launch_shapes(torch):
+    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS
+    geom = oracle.Geometry(num_blocks=4099, block_bits=512, word_bits=64, k=16, seed=9)
+    ins = synthkeys.insert_keys(40_001, seed=31)
+    q, _ = synthkeys.mixed_queries(40_001, 7000, 9001, seed_insert=31)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    ref_out = ref.contains(q)
+    # keys at an 8-byte (not 32-byte) offset, results at an odd byte offset
+    dk = torch.empty(ins.size + 1, dtype=torch.int64, device="cuda")
+    dk[1:] = dev_keys(torch, ins)
+    dq = torch.empty(q.size + 1, dtype=torch.int64, device="cuda")
+    dq[1:] = dev_keys(torch, q)
+    out_buf = torch.zeros(q.size + 1, dtype=torch.uint8, device="cuda")
+    for threads, grid in [(32, 1), (64, 3), (512, 0), (256, 1000)]:
+        f = gpu_filter(geom, torch)
+        f.set_layout(BF_OP_ADD, cg=8, phi=1, kpt=4, block_threads=threads, grid_ctas=grid)
+        f.set_layout(BF_OP_CONTAINS, cg=2, phi=4, kpt=4, block_threads=threads, grid_ctas=grid)
+        f.add(dk[1:])
+        f.contains(dq[1:], out=out_buf[1:])
+        assert np.array_equal(words_np(f), ref.as_bytes()), (threads, grid)
+        assert np.array_equal(out_buf[1:].cpu().numpy(), ref_out), (threads, grid)
+        f.close()
+
+
+def test_duplicates_and_idempotence(torch):
+    geom = oracle.Geometry(num_blocks=333, block_bits=128, word_bits=32, k=8, seed=1)
+    ins = synthkeys.insert_keys(5000, seed=41)
+    dup = np.concatenate([ins, ins[::-1], ins[:100]])
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    f = gpu_filter(geom, torch)
+    f.add(dev_keys(torch, dup))
+    f.add(dev_keys(torch, ins))
+    assert np.array_equal(words_np(f), ref.as_bytes())
+    f.clear()
+    assert not f.contains(dev_keys(torch, ins)).any().item()
+
+
+def test_library_allocated_filter(torch):
+    from paper_2512_15595_gb300 import _lib, bf_params, device_tensor
+    geom = oracle.Geometry(num_blocks=2000, block_bits=256, word_bits=64, k=16, seed=77)
+    ins = synthkeys.insert_keys(20_000, seed=51)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    h = _lib.bf_create(bf_params(2000, 256, 64, 16, 0, 77), None)
+    try:
+        ptr, nbytes = _lib.bf_words(h)
+        assert nbytes == geom.nbytes
+        words = device_tensor(ptr, nbytes, "cuda")
+        assert not words.any().item()  # zeroed at creation
+        dk = dev_keys(torch, ins)
+        _lib.bf_add(h, dk.data_ptr(), dk.numel())
+        torch.cuda.synchronize()
+        assert np.array_equal(words.cpu().numpy(), ref.as_bytes())
+    finally:
+        _lib.bf_destroy(h)
+
+
+def test_host_pipeline(torch):
+    from paper_2512_15595_gb300 import _lib
+    geom = oracle.Geometry(num_blocks=10007, block_bits=256, word_bits=32, k=8, seed=3)
+    ins = synthkeys.insert_keys(300_001, seed=61)
+    q, _ = synthkeys.mixed_queries(300_001, 50_000, 70_007, seed_insert=61)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    f = gpu_filter(geom, torch)
+    _lib.bf_set_staging(f.handle, 4096 * 7 + 3)  # several chunks plus a ragged one
+    h_ins = torch.from_numpy(ins.view(np.int64)).pin_memory()
+    h_q = torch.from_numpy(q.view(np.int64)).pin_memory()
+    h_out = torch.empty(q.size, dtype=torch.uint8).pin_memory()
+    f.add_host(h_ins.numpy())
+    f.contains_host(h_q.numpy(), h_out.numpy())
+    torch.cuda.current_stream().synchronize()
+    assert np.array_equal(words_np(f), ref.as_bytes())
+    assert np.array_equal(h_out.numpy(), ref.contains(q))
+    f.close()
+
+
+def test_rejects_misaligned_keys_before_launch(torch):
+    from paper_2512_15595_gb300 import BloomError, _lib
+    geom = oracle.Geometry(num_blocks=10, block_bits=256, word_bits=32, k=8)
+    f = gpu_filter(geom, torch)
+    buf = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(BloomError):
+        _lib.bf_add(f.handle, buf.data_ptr() + 4, 1)
+    with pytest.raises(BloomError):
+        f.set_layout(0, cg=16)
+    f.close()
+
+
+# ---------------------------------------------------------------------------
+# residency regimes
+# ---------------------------------------------------------------------------
+def test_l2_resident_32mib_with_and_without_persistence(torch):
+    from paper_2512_15595_gb300 import BF_HINT_FILTER_EVICT_LAST, BF_OP_ADD, BF_OP_CONTAINS
+    geom = oracle.Geometry(num_blocks=1 << 20, block_bits=256, word_bits=32, k=8, seed=0)
+    n = (32 << 20) * 8 // 10
+    ins = synthkeys.insert_keys(n)
+    q, is_mem = synthkeys.stream_queries(0, 4_000_000, n)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    ref_out = ref.contains(q)
+    dk, dq = dev_keys(torch, ins), dev_keys(torch, q)
+    for persist, flags in [(0.0, 0), (1.0, BF_HINT_FILTER_EVICT_LAST)]:
+        f = gpu_filter(geom, torch)
+        f.set_layout(BF_OP_ADD, flags=flags)
+        f.set_layout(BF_OP_CONTAINS, flags=flags)
+        if persist:
+            f.set_l2_persist(persist)
+        f.add(dk)
+        out = f.contains(dq)
+        torch.cuda.synchronize()
+        if persist:
+            f.set_l2_persist(0.0)
+        assert np.array_equal(words_np(f), ref.as_bytes())
+        assert np.array_equal(out.cpu().numpy().astype(np.uint8), ref_out)
+        f.close()
+
+
+def test_hbm_resident_256mib(torch):
+    # 256 MiB is twice the GB300 L2, so most block accesses go to HBM
+    geom = oracle.Geometry(num_blocks=1 << 23, block_bits=256, word_bits=64, k=8, seed=0)
+    n = (256 << 20) * 8 // 10
+    ins = synthkeys.insert_keys(n)
+    q, _ = synthkeys.stream_queries(0, 2_000_000, n)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    f = gpu_filter(geom, torch)
+    f.add(dev_keys(torch, ins))
+    out = f.contains(dev_keys(torch, q))
+    assert np.array_equal(words_np(f), ref.as_bytes())
+    assert np.array_equal(out.cpu().numpy().astype(np.uint8), ref.contains(q))
+    f.close()
+
+
+@pytest.mark.parametrize("nblocks", [1 << 32, (1 << 32) + 12345])
+def test_block_index_beyond_32_bits(torch, nblocks):
+    # B = 64 bits: 2^32 blocks are a 32 GiB filter; checks the b == 2^32 and
+    # b > 2^32 block-selection paths.  The expected bits are composed from the
+    # oracle's primitives for the touched words only.
+    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS
+    geom = oracle.Geometry(num_blocks=nblocks, block_bits=64, word_bits=64, k=4, seed=99)
+    ins = synthkeys.insert_keys(50_000, seed=71)
+    expect = {}
+    for key in ins:
+        h = oracle.key_hash(int(key), geom.seed)
+        j = oracle.block_index(h, nblocks)
+        pat = 0
+        for t in range(4):
+            pat |= 1 << oracle.bit_position(h, t, 64)
+        expect[j] = expect.get(j, 0) | pat
+    f = gpu_filter(geom, torch)
+    f.add(dev_keys(torch, ins))
+    w = f.words.view(torch.int64)
+    idx = torch.tensor(sorted(expect), dtype=torch.int64, device="cuda")
+    got = w[idx].cpu().numpy().view(np.uint64)
+    assert [int(x) for x in got] == [expect[j] for j in sorted(expect)]
+    w[idx] = 0
+    assert not w.any().item()  # no stray bits anywhere else
+    w[idx] = torch.from_numpy(got.view(np.int64)).cuda()
+    q = synthkeys.splitmix64(72, 0, 20_000)
+    q[:5000] = ins[:5000]
+    f.set_layout(BF_OP_CONTAINS, kpt=4)
+    out = f.contains(dev_keys(torch, q)).cpu().numpy().astype(np.uint8)
+    want = []
+    for key in q:
+        h = oracle.key_hash(int(key), geom.seed)
+        j = oracle.block_index(h, nblocks)
+        pat = 0
+        for t in range(4):
+            pat |= 1 << oracle.bit_position(h, t, 64)
+        want.append(int((expect.get(j, 0) & pat) == pat))
+    assert np.array_equal(out, np.array(want, dtype=np.uint8))
+    f.close()
