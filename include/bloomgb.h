@@ -88,7 +88,7 @@ enum {
 /* Execution layout of one operation (Sec. IV-A, IV-C).
    cg = Theta threads per key (power of two, 1..s); phi = Phi words per thread
    per step (power of two, cg*phi <= s); kpt = keys each thread hashes per
-   tile (1, 2 or 4); block_threads = CTA size (multiple of 32, <= 1024);
+   tile (1, 2 or 4); block_threads = CTA size (multiple of 32, <= 512);
    grid_ctas = number of CTAs (0 = SM count x resident CTAs per SM).
    A zero in cg/phi/kpt/block_threads selects the library default. */
 typedef struct {
@@ -139,8 +139,8 @@ bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, ui
    after prior work on `stream` and all of it is complete when `stream` is.
    h_keys / h_out must stay valid until then; page-locked (pinned) memory is
    needed for overlap.  The first call allocates the device staging buffers
-   (2 x chunk_keys x 9 bytes, see bf_set_staging) and keeps them until
-   bf_destroy. */
+   (3 slots of about 9 x chunk_keys bytes, see bf_set_staging) and keeps them
+   until bf_destroy. */
 bf_status bf_add_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, bf_stream_t stream);
 bf_status bf_contains_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
                            bf_stream_t stream);

@@ -150,7 +150,7 @@ struct bf_filter {
   const KernelEntry* entry[2]{};
   // host-buffer pipeline
   uint64_t chunk_keys = 1ull << 24;
-  void* staging = nullptr;  // kPipelineDepth x (chunk_keys*8 + chunk_keys) bytes
+  void* staging = nullptr;  // kPipelineDepth slots of slot_bytes(chunk_keys)
   cudaStream_t pipe[kPipelineDepth]{};
   cudaEvent_t ev_start = nullptr;
   cudaEvent_t ev_done[kPipelineDepth]{};
@@ -220,6 +220,8 @@ bf_status resolve_layout(const bf_params& p, int op, const bf_layout* in, bf_lay
 
 bf_status launch_sbf(const bf_filter* f, int op, const uint64_t* keys, uint64_t n, uint8_t* out,
                      cudaStream_t stream) {
+  if (reinterpret_cast<uintptr_t>(keys) % 8 || (op == BF_OP_CONTAINS && !out))
+    return fail(BF_EINVAL, "keys must be 8-byte aligned and out non-NULL");
   const bf_layout& l = f->layout[op];
   const KernelEntry* e = f->entry[op];
   uint32_t grid = 0;
@@ -233,9 +235,15 @@ bf_status launch_sbf(const bf_filter* f, int op, const uint64_t* keys, uint64_t 
   return BF_OK;
 }
 
+// Bytes of one staging slot: the keys, then the results, each region padded
+// to 256 bytes so every slot's key pointer keeps the alignment the kernels'
+// vector loads need.
+uint64_t keys_region(uint64_t chunk_keys) { return (chunk_keys * 8 + 255) / 256 * 256; }
+uint64_t slot_bytes(uint64_t chunk_keys) { return keys_region(chunk_keys) + (chunk_keys + 255) / 256 * 256; }
+
 bf_status ensure_pipeline(bf_filter* f) {
   if (f->staging) return BF_OK;
-  const uint64_t per = f->chunk_keys * 9;
+  const uint64_t per = slot_bytes(f->chunk_keys);
   cudaError_t e = cudaMalloc(&f->staging, per * kPipelineDepth);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -277,14 +285,15 @@ bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n
   if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   for (int i = 0; i < kPipelineDepth; ++i)
     if ((e = cudaStreamWaitEvent(f->pipe[i], f->ev_start, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
-  const uint64_t per = f->chunk_keys * 9;
+  const uint64_t per = slot_bytes(f->chunk_keys);
   uint64_t c = 0;
   for (uint64_t lo = 0; lo < n; lo += f->chunk_keys, ++c) {
     const uint64_t cnt = std::min(f->chunk_keys, n - lo);
     const int slot = static_cast<int>(c % kPipelineDepth);
     cudaStream_t st = f->pipe[slot];
-    uint64_t* d_keys = reinterpret_cast<uint64_t*>(static_cast<char*>(f->staging) + slot * per);
-    uint8_t* d_out = reinterpret_cast<uint8_t*>(d_keys + f->chunk_keys);
+    char* slot_base = static_cast<char*>(f->staging) + slot * per;
+    uint64_t* d_keys = reinterpret_cast<uint64_t*>(slot_base);
+    uint8_t* d_out = reinterpret_cast<uint8_t*>(slot_base + keys_region(f->chunk_keys));
     if ((e = cudaMemcpyAsync(d_keys, h_keys + lo, cnt * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync H2D");
     if ((s = launch_sbf(f, op, d_keys, cnt, d_out, st)) != BF_OK) return s;
