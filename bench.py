@@ -39,6 +39,9 @@ WORKLOADS = {
     "32MiB": dict(nbytes=32 << 20, block_bits=256, word_bits=32, k=8, n_lookup=10**9, member_den=10,
                   desc="32 MiB L2-resident SBF, 2^20 x 256-bit blocks, S=32, K=8; insert 10 bits/key "
                        "(26,843,545 keys), look up 1e9 keys at 10% members"),
+    "256MiB": dict(nbytes=256 << 20, block_bits=256, word_bits=32, k=8, n_lookup=10**8, member_den=10,
+                   desc="256 MiB HBM-resident SBF (2x L2), 2^23 x 256-bit blocks, S=32, K=8; insert 10 bits/key "
+                        "(214,748,364 keys), look up 1e8 keys at 10% members (profiling size)"),
     "1MiB": dict(nbytes=1 << 20, block_bits=256, word_bits=32, k=8, n_insert=10**6, n_lookup=10**6,
                  member_den=2,
                  desc="1 MiB SBF, 2^15 x 256-bit blocks, S=32, K=8; insert 1e6 keys, look up 1e6 keys"),
