@@ -331,19 +331,24 @@ def run_ours(args, w, wname):
 
     bounds = gups_bounds(torch, w, ins, qd, device) if not args.no_gups else None
 
+    launches = []
+
     def step(ev=None):
         if ev:
             ev[0].record(stream)
         f.add(ins)
+        n_add_launch = f.last_launches()
         if ev:
             ev[1].record(stream)
         f.contains(qd, out=out)
+        launches.append(n_add_launch + f.last_launches())
         if ev:
             ev[2].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    launches.clear()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     sampler = ClockSampler(local, getattr(props, "uuid", None) and f"GPU-{props.uuid}")
     barrier(world)
@@ -416,7 +421,8 @@ def run_ours(args, w, wname):
             "data": "synthetic (SplitMix64 key streams generated on the device)",
             "config": {"workload": wname, "desc": w["desc"], "num_blocks": b, "block_bits": w["block_bits"],
                        "word_bits": w["word_bits"], "k": w["k"], "n_insert": n_ins, "n_lookup": n_q,
-                       "regime": regime, "layouts": layouts, "parallelism": f"replicas x{world}",
+                       "regime": regime, "layouts": layouts, "partition": f.partition(),
+                       "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (no flush)" if n_ins * 8 > props.L2_cache_size
                              else "warm L2 (cache-resident regime)"},
             "insert_gkeys_s": ins_g, "lookup_gkeys_s": look_g, "insert_ms": add_ms, "lookup_ms": con_ms,
@@ -424,7 +430,7 @@ def run_ours(args, w, wname):
             "fpr": {"bits_per_key": w["nbytes"] * 8 / n_ins, "measured": measured_fpr,
                     "realized_filter": realized_fpr, "fresh_queries": n_fresh, "false_negatives": missed},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 2 * args.steps, "clocks": clocks,
+            "gpu_launches": sum(launches), "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     f.close()
@@ -477,12 +483,17 @@ def run_sweep(args, w, wname):
     b, n_ins, n_q = wl_sizes(w)
     regime = autotune.regime_of(w["nbytes"], props.L2_cache_size)
     ins, qd, flags = gen_inputs(torch, w, device)
-    n_add = min(n_ins, args.sweep_keys)
+    # construction is swept at the full insert count: the partitioned path's
+    # benefit depends on how many keys share an L2 window
+    n_add = n_ins
     n_con = min(n_q, args.sweep_keys)
     f = Filter(b, w["block_bits"], w["word_bits"], w["k"], 0, device=device)
     f.add(ins)  # occupancy of the real workload
     out = torch.empty(n_con, dtype=torch.uint8, device=device)
-    res = autotune.sweep(torch, f, ins[:n_add], qd[:n_con], out, regime,
+    parts = [dict(mode=0)]
+    if regime == "hbm":
+        parts += [dict(mode=1, slice_log2=sl, window_log2=wl) for sl, wl in ((23, 25), (24, 25), (24, 26), (25, 26))]
+    res = autotune.sweep(torch, f, ins[:n_add], qd[:n_con], out, regime, partitions=parts, kpts=(1, 4), reps=3,
                          log=lambda r: print(json.dumps(r), file=sys.stderr, flush=True))
     table = autotune.load_tuned()
     table[res["key"]] = res["entry"]

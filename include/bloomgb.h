@@ -133,22 +133,30 @@ bf_status bf_add(bf_filter* f, const uint64_t* d_keys, uint64_t n, bf_stream_t s
 bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, uint8_t* d_out,
                       bf_stream_t stream);
 
-/* End-to-end variants over HOST buffers: keys are copied to the device in
-   chunks on internal streams, overlapping the copies with the kernels; the
-   contains variant copies the results back into h_out.  The work is ordered
-   after prior work on `stream` and all of it is complete when `stream` is.
-   h_keys / h_out must stay valid until then; page-locked (pinned) memory is
-   needed for overlap.  The first call allocates the device staging buffers
-   (3 slots of about 9 x chunk_keys bytes, see bf_set_staging) and keeps them
-   until bf_destroy. */
+/* End-to-end variants over HOST buffers.  The work is ordered after prior
+   work on `stream` and all of it is complete when `stream` is; h_keys / h_out
+   must stay valid until then.  Two ways, chosen per call:
+     direct: when the device can address the buffers (pinned memory from
+       cudaHostAlloc / cudaHostRegister, or any host memory on a GPU with
+       pageable memory access, as on Grace-coupled GB300), the kernels read the
+       keys and write the results in place over the CPU-GPU link; bf_add_host
+       then takes the same construction path as bf_add;
+     staged: otherwise, or when bf_set_staging selected BF_HOST_STAGED, keys
+       are copied in chunks into device staging buffers on three internal
+       streams, overlapping the copies with the kernels, and results are
+       copied back.  The first staged call allocates the staging buffers
+       (3 slots of about 9 x chunk_keys bytes) and keeps them until
+       bf_destroy. */
 bf_status bf_add_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, bf_stream_t stream);
 bf_status bf_contains_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
                            bf_stream_t stream);
 
-/* Keys per staging chunk of the host variants (default 1<<24).  Frees the
-   current staging buffers; must not be called while host-variant work on
-   this filter is in flight. */
-bf_status bf_set_staging(bf_filter* f, uint64_t chunk_keys);
+/* Host-variant settings: keys per staging chunk (default 1<<24) and mode
+   (BF_HOST_AUTO = direct when possible, BF_HOST_STAGED = always stage).
+   Frees the current staging buffers; must not be called while host-variant
+   work on this filter is in flight. */
+typedef enum { BF_HOST_AUTO = 0, BF_HOST_STAGED = 1 } bf_host_mode;
+bf_status bf_set_staging(bf_filter* f, uint64_t chunk_keys, int mode);
 
 /* Raw bit array: device pointer and size in bytes. */
 bf_status bf_words(const bf_filter* f, void** d_ptr, uint64_t* nbytes);
@@ -156,7 +164,9 @@ bf_status bf_words(const bf_filter* f, void** d_ptr, uint64_t* nbytes);
 /* Geometry of an existing filter. */
 bf_status bf_get_params(const bf_filter* f, bf_params* out);
 
-/* Select the layout of one operation (op = BF_OP_ADD or BF_OP_CONTAINS). */
+/* Select the layout of one operation (op = BF_OP_ADD or BF_OP_CONTAINS).  The
+   construction layout also drives the record-insert kernel of the
+   partitioned construction. */
 bf_status bf_set_layout(bf_filter* f, int op, const bf_layout* layout);
 bf_status bf_get_layout(const bf_filter* f, int op, bf_layout* out);
 
@@ -166,6 +176,42 @@ bf_status bf_get_layout(const bf_filter* f, int op, bf_layout* out);
    given hit ratio.  hit_ratio <= 0 removes the window, resets persisting
    lines and sets the limit back to 0. */
 bf_status bf_set_l2_persist(bf_filter* f, bf_stream_t stream, float hit_ratio);
+
+/* L2-blocked construction (this library's addition; the paper's kernel is the
+   direct one).  For a filter larger than L2 the keys are hashed and radix-
+   partitioned by filter slice (2^slice_log2 bytes of the bit array), then each
+   slice's atomic ORs run while the slice sits in L2.  The bits set are the
+   same as with direct construction (OR is commutative and idempotent).  The
+   partition buffers (about 8 bytes per key of a pass, at most chunk_keys keys
+   per pass) are allocated on the first partitioned bf_add and kept until
+   bf_destroy; if that allocation fails bf_add uses the direct kernel.  A key
+   whose slice buffer is full is inserted directly, so any key distribution is
+   handled.  Partitioning needs num_blocks <= 2^32 and more than one slice.
+   mode: BF_PART_OFF = direct kernel only; BF_PART_ON = partition whenever it
+   applies; BF_PART_AUTO (default) = partition when the bit array is larger
+   than half the L2 and the pass has at least num_blocks/2 keys.
+   cap_override: slots per slice buffer (0 = computed from the pass size;
+   small values force the overflow path, for tests).  window_log2: the
+   record-insert kernel is launched once per 2^window_log2 bytes of the bit
+   array (at least one slice per launch), so that all warps stay inside one
+   L2-sized window of the filter. */
+typedef enum { BF_PART_OFF = 0, BF_PART_ON = 1, BF_PART_AUTO = 2 } bf_part_mode;
+typedef struct {
+    uint32_t mode;
+    uint32_t slice_log2;     /* 16..34; default 24 (16 MiB) */
+    uint64_t chunk_keys;     /* >= 4096; default 2^32 */
+    uint64_t cap_override;   /* 0 = computed; else a multiple of 128 */
+    uint32_t window_log2;    /* 16..36, >= slice_log2 in effect; default 26 (64 MiB) */
+    uint32_t reserved;       /* must be 0 */
+} bf_partition;
+bf_status bf_set_partition(bf_filter* f, const bf_partition* cfg);
+bf_status bf_get_partition(const bf_filter* f, bf_partition* out);
+
+/* Kernel launches made by the last bf_add / bf_contains / bf_add_host /
+   bf_contains_host call on this filter (1 for a direct call; per pass of a
+   partitioned construction, one partition launch plus one record-insert
+   launch per window; per chunk for the staged host variants). */
+bf_status bf_last_launches(const bf_filter* f, uint32_t* n);
 
 /* Random-access microbenchmark that bounds the filter kernels (Sec. V-B
    measures the bound with random 64-bit accesses, GUPS).  For each i in
@@ -182,10 +228,6 @@ typedef enum { BF_GUPS_LOAD = 0, BF_GUPS_RED_OR = 1 } bf_gups_mode;
 bf_status bf_gups(int mode, void* d_table, uint64_t table_bytes, uint32_t unit_bytes,
                   const uint64_t* d_keys, uint64_t n, uint8_t* d_out, const bf_layout* layout,
                   bf_stream_t stream);
-
-/* Number of kernel launches one bf_add / bf_contains / bf_gups call makes:
-   always 1 (the host variants make one per chunk). */
-uint32_t bf_launches_per_call(void);
 
 const char* bf_status_str(bf_status s);
 

@@ -103,6 +103,18 @@ class Filter:
     def layout(self, op: int) -> dict:
         return _lib.bf_get_layout(self.handle, op).as_dict()
 
+    def set_partition(self, mode: int = 2, slice_log2: int = 24, chunk_keys: int = 1 << 32,
+                      cap_override: int = 0, window_log2: int = 26) -> None:
+        """L2-blocked construction settings (mode 0 off, 1 on, 2 auto)."""
+        _lib.bf_set_partition(self.handle, _lib.bf_partition(mode, slice_log2, chunk_keys, cap_override,
+                                                             window_log2, 0))
+
+    def partition(self) -> dict:
+        return _lib.bf_get_partition(self.handle).as_dict()
+
+    def last_launches(self) -> int:
+        return _lib.bf_last_launches(self.handle)
+
     def set_l2_persist(self, hit_ratio: float, stream=None) -> None:
         _lib.bf_set_l2_persist(self.handle, hit_ratio, stream)
 

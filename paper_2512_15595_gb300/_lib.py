@@ -18,13 +18,15 @@ BF_OP_ADD, BF_OP_CONTAINS = 0, 1
 BF_HINT_FILTER_EVICT_LAST = 1 << 0
 BF_HINT_KEYS_EVICT_NORMAL = 1 << 1
 BF_GUPS_LOAD, BF_GUPS_RED_OR = 0, 1
+BF_HOST_AUTO, BF_HOST_STAGED = 0, 1
 
 # every symbol include/bloomgb.h declares
 EXPORTED = (
     "bf_params_check", "bf_layout_check", "bf_create", "bf_destroy", "bf_clear", "bf_add",
     "bf_contains", "bf_add_host", "bf_contains_host", "bf_set_staging", "bf_words",
     "bf_get_params", "bf_set_layout", "bf_get_layout", "bf_set_l2_persist", "bf_gups",
-    "bf_launches_per_call", "bf_status_str", "bf_last_error", "bf_version",
+    "bf_set_partition", "bf_get_partition", "bf_last_launches", "bf_status_str", "bf_last_error",
+    "bf_version",
 )
 
 
@@ -41,6 +43,18 @@ class bf_params(ctypes.Structure):
     _fields_ = [("num_blocks", ctypes.c_uint64), ("block_bits", ctypes.c_uint32),
                 ("word_bits", ctypes.c_uint32), ("k", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+BF_PART_OFF, BF_PART_ON, BF_PART_AUTO = 0, 1, 2
+
+
+class bf_partition(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_uint32), ("slice_log2", ctypes.c_uint32),
+                ("chunk_keys", ctypes.c_uint64), ("cap_override", ctypes.c_uint64),
+                ("window_log2", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class bf_layout(ctypes.Structure):
@@ -75,14 +89,16 @@ def lib():
         "bf_contains": (i32, [vp, vp, u64, vp, vp]),
         "bf_add_host": (i32, [vp, vp, u64, vp]),
         "bf_contains_host": (i32, [vp, vp, u64, vp, vp]),
-        "bf_set_staging": (i32, [vp, u64]),
+        "bf_set_staging": (i32, [vp, u64, i32]),
         "bf_words": (i32, [vp, ctypes.POINTER(vp), ctypes.POINTER(u64)]),
         "bf_get_params": (i32, [vp, P]),
         "bf_set_layout": (i32, [vp, i32, LY]),
         "bf_get_layout": (i32, [vp, i32, LY]),
         "bf_set_l2_persist": (i32, [vp, vp, ctypes.c_float]),
         "bf_gups": (i32, [i32, vp, u64, u32, vp, u64, vp, LY, vp]),
-        "bf_launches_per_call": (u32, []),
+        "bf_set_partition": (i32, [vp, ctypes.POINTER(bf_partition)]),
+        "bf_get_partition": (i32, [vp, ctypes.POINTER(bf_partition)]),
+        "bf_last_launches": (i32, [vp, ctypes.POINTER(u32)]),
         "bf_status_str": (ctypes.c_char_p, [i32]),
         "bf_last_error": (ctypes.c_char_p, []),
         "bf_version": (ctypes.c_char_p, []),
@@ -150,8 +166,8 @@ def bf_contains_host(f: int, h_keys: int, n: int, h_out: int, stream=None) -> No
     _check(lib().bf_contains_host(f, h_keys, n, h_out, _stream(stream)), "bf_contains_host")
 
 
-def bf_set_staging(f: int, chunk_keys: int) -> None:
-    _check(lib().bf_set_staging(f, chunk_keys), "bf_set_staging")
+def bf_set_staging(f: int, chunk_keys: int, mode: int = 0) -> None:
+    _check(lib().bf_set_staging(f, chunk_keys, mode), "bf_set_staging")
 
 
 def bf_words(f: int) -> tuple[int, int]:
@@ -186,8 +202,20 @@ def bf_gups(mode: int, d_table: int, table_bytes: int, unit_bytes: int, d_keys: 
                          ctypes.byref(layout) if layout else None, _stream(stream)), "bf_gups")
 
 
-def bf_launches_per_call() -> int:
-    return lib().bf_launches_per_call()
+def bf_set_partition(f: int, cfg: bf_partition) -> None:
+    _check(lib().bf_set_partition(f, ctypes.byref(cfg)), "bf_set_partition")
+
+
+def bf_get_partition(f: int) -> bf_partition:
+    out = bf_partition()
+    _check(lib().bf_get_partition(f, ctypes.byref(out)), "bf_get_partition")
+    return out
+
+
+def bf_last_launches(f: int) -> int:
+    n = ctypes.c_uint32()
+    _check(lib().bf_last_launches(f, ctypes.byref(n)), "bf_last_launches")
+    return n.value
 
 
 def bf_status_str(s: int) -> str:

@@ -49,13 +49,17 @@ def tuned_layout(block_bits: int, word_bits: int, k: int, regime: str, op: int) 
 
 
 def apply_tuned(f: Filter, regime: str) -> dict:
-    """Set the filter's layouts from the tuned table (if it has an entry)."""
+    """Set the filter's layouts (and construction partitioning) from the tuned table."""
     p = f.params
     used = {}
     for op, name in ((BF_OP_ADD, "add"), (BF_OP_CONTAINS, "contains")):
         lay = tuned_layout(p.block_bits, p.word_bits, p.k, regime, op)
         if lay:
+            lay = dict(lay)
+            part = lay.pop("partition", None)
             f.set_layout(op, **lay)
+            if part is not None and op == BF_OP_ADD:
+                f.set_partition(**part)
         used[name] = f.layout(op)
     return used
 
@@ -82,25 +86,35 @@ def time_op(torch, f: Filter, op: int, keys, out, reps: int = 5, warmup: int = 2
 
 
 def sweep(torch, f: Filter, keys_add, keys_q, out, regime: str, kpts=(1, 2, 4), block_threads=(256,),
-          flags=0, reps: int = 5, flush=None, log=None) -> dict:
-    """Time every layout of both operations; returns the table entry (and rows)."""
+          flags=0, reps: int = 5, flush=None, log=None, partitions=None) -> dict:
+    """Time every layout of both operations; returns the table entry (and rows).
+
+    ``partitions``: list of construction-partitioning settings to sweep (dicts
+    for ``Filter.set_partition``), or None to keep the filter's setting.
+    """
     p = f.params
     rows = []
     best = {}
+    part_modes = [None] if partitions is None else partitions
     for op, name, keys in ((BF_OP_ADD, "add", keys_add), (BF_OP_CONTAINS, "contains", keys_q)):
-        for cg, phi in valid_layouts(p.block_bits, p.word_bits):
-            for kpt in kpts:
-                for bt in block_threads:
-                    lay = dict(cg=cg, phi=phi, kpt=kpt, block_threads=bt, flags=flags)
-                    f.set_layout(op, **lay)
-                    ms = time_op(torch, f, op, keys, out, reps=reps, flush=flush)
-                    g = keys.numel() / (ms * 1e-3) / 1e9
-                    row = dict(op=name, gkeys_s=g, ms=ms, **lay)
-                    rows.append(row)
-                    if log:
-                        log(row)
-                    if name not in best or g > best[name]["gkeys_s"]:
-                        best[name] = dict(gkeys_s=g, layout=lay)
+        for part in (part_modes if op == BF_OP_ADD else [None]):
+            if part is not None:
+                f.set_partition(**part)
+            for cg, phi in valid_layouts(p.block_bits, p.word_bits):
+                for kpt in kpts:
+                    for bt in block_threads:
+                        lay = dict(cg=cg, phi=phi, kpt=kpt, block_threads=bt, flags=flags)
+                        f.set_layout(op, **lay)
+                        ms = time_op(torch, f, op, keys, out, reps=reps, flush=flush)
+                        g = keys.numel() / (ms * 1e-3) / 1e9
+                        if part is not None:
+                            lay = dict(lay, partition=part)
+                        row = dict(op=name, gkeys_s=g, ms=ms, **lay)
+                        rows.append(row)
+                        if log:
+                            log(row)
+                        if name not in best or g > best[name]["gkeys_s"]:
+                            best[name] = dict(gkeys_s=g, layout=lay)
     entry = {"add": best["add"], "contains": best["contains"],
              "n_add": keys_add.numel(), "n_contains": keys_q.numel(), "filter_bytes": f.nbytes}
     return {"key": key_of(p.block_bits, p.word_bits, p.k, regime), "entry": entry, "rows": rows}

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -154,7 +155,14 @@ struct bf_filter {
   cudaStream_t pipe[kPipelineDepth]{};
   cudaEvent_t ev_start = nullptr;
   cudaEvent_t ev_done[kPipelineDepth]{};
+  int host_access = 0;  // 0: kernels read device-accessible host buffers directly; 1: always stage
   bool l2_window = false;
+  // L2-blocked construction
+  bf_partition part{BF_PART_AUTO, 24, 1ull << 32, 0, 26, 0};
+  void* part_ws = nullptr;
+  uint64_t part_ws_bytes = 0;
+  uint64_t l2_bytes = 0;
+  uint32_t last_launches = 0;
 };
 
 namespace {
@@ -232,7 +240,141 @@ bf_status launch_sbf(const bf_filter* f, int op, const uint64_t* keys, uint64_t 
   void* args[] = {&a};
   cudaError_t err = cudaLaunchKernel(e->fn, dim3(grid), dim3(l.block_threads), args, 0, stream);
   if (err != cudaSuccess) return cuda_fail(err, op == BF_OP_ADD ? "launch add kernel" : "launch contains kernel");
+  const_cast<bf_filter*>(f)->last_launches += 1;
   return BF_OK;
+}
+
+// --- L2-blocked construction ------------------------------------------------
+
+struct PartPlan {
+  uint32_t shift = 0, nparts = 0;
+};
+
+// slice geometry: 2^shift blocks per slice, at most static_cast<uint32_t>(kMaxParts) slices
+PartPlan part_plan(const bf_filter* f) {
+  PartPlan pl;
+  const uint64_t b = f->p.num_blocks;
+  const uint32_t block_log2 = static_cast<uint32_t>(__builtin_ctz(f->p.block_bits / 8));
+  uint32_t shift = f->part.slice_log2 > block_log2 ? f->part.slice_log2 - block_log2 : 0;
+  while (((b + (1ull << shift) - 1) >> shift) > static_cast<uint32_t>(kMaxParts)) ++shift;
+  pl.shift = shift;
+  pl.nparts = static_cast<uint32_t>((b + (1ull << shift) - 1) >> shift);
+  return pl;
+}
+
+// slots per slice buffer for a pass of `keys` keys: the expected count of the
+// fullest slice plus 8 standard deviations, rounded up to the record tile
+uint64_t part_cap(const bf_filter* f, const PartPlan& pl, uint64_t keys) {
+  if (f->part.cap_override) return f->part.cap_override;
+  const double frac = std::min(1.0, static_cast<double>(1ull << pl.shift) / static_cast<double>(f->p.num_blocks));
+  const double mean = static_cast<double>(keys) * frac;
+  const double cap = mean + 8.0 * std::sqrt(mean) + 256.0;
+  return (static_cast<uint64_t>(cap) + kRecTile - 1) / kRecTile * kRecTile;
+}
+
+bool use_partitioned(const bf_filter* f, uint64_t n) {
+  if (f->part.mode == BF_PART_OFF || f->p.num_blocks > (1ull << 32)) return false;
+  const PartPlan pl = part_plan(f);
+  if (pl.nparts < 2) return false;
+  if (f->part.mode == BF_PART_ON) return true;
+  return f->nbytes * 2 > f->l2_bytes && n >= f->p.num_blocks / 2;
+}
+
+const KernelEntry* find_op(int op, const bf_params& p, uint32_t cg, uint32_t phi, uint32_t kpt) {
+  bf_layout l{};
+  l.cg = cg;
+  l.phi = phi;
+  l.kpt = kpt;
+  return find_sbf(op, p, l);
+}
+
+bf_status ensure_part_ws(bf_filter* f, uint64_t bytes) {
+  if (f->part_ws && f->part_ws_bytes >= bytes) return BF_OK;
+  if (f->part_ws) {
+    cudaFree(f->part_ws);
+    f->part_ws = nullptr;
+    f->part_ws_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&f->part_ws, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    f->part_ws = nullptr;
+    return fail(BF_ENOMEM, "partition workspace allocation failed");
+  }
+  f->part_ws_bytes = bytes;
+  return BF_OK;
+}
+
+bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
+  const PartPlan pl = part_plan(f);
+  const uint64_t pass = std::min<uint64_t>(n, f->part.chunk_keys);
+  const uint64_t cap_max = part_cap(f, pl, pass);
+  const uint64_t counts_bytes = 8ull * static_cast<uint32_t>(kMaxParts);
+  bf_status s = ensure_part_ws(f, counts_bytes + static_cast<uint64_t>(pl.nparts) * cap_max * 8);
+  if (s != BF_OK) return launch_sbf(f, BF_OP_ADD, keys, n, nullptr, stream);  // no memory: direct kernel
+  const KernelEntry* pe = find_op(3, f->p, 0, 0, 0);
+  const bf_layout& l = f->layout[BF_OP_ADD];
+  const KernelEntry* re = find_op(2, f->p, l.cg, l.phi, l.kpt);
+  if (!pe || !re) return fail(BF_EUNSUPPORTED, "no partition kernels for this geometry");
+  unsigned long long* counts = static_cast<unsigned long long*>(f->part_ws);
+  uint64_t* records = reinterpret_cast<uint64_t*>(static_cast<char*>(f->part_ws) + counts_bytes);
+  const size_t smem = partition_smem_bytes(static_cast<int>(pl.nparts));
+  cudaError_t e = cudaFuncSetAttribute(pe->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(partition)");
+  int sms = 0, per_sm = 0;
+  if ((s = sm_count(f->device, &sms)) != BF_OK) return s;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pe->fn, kPartThreads, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(partition)");
+  per_sm = std::max(per_sm, 1);
+  for (uint64_t lo = 0; lo < n; lo += pass) {
+    const uint64_t cnt = std::min(pass, n - lo);
+    const uint64_t cap = part_cap(f, pl, cnt);
+    if ((e = cudaMemsetAsync(counts, 0, 8ull * pl.nparts, stream)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    PartArgs pa{keys + lo, cnt, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, f->p.num_blocks,
+                f->p.num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, f->words};
+    const uint64_t tiles = (cnt + kPartTile - 1) / kPartTile;
+    const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, static_cast<uint64_t>(sms) * per_sm));
+    void* pargs[] = {&pa};
+    if ((e = cudaLaunchKernel(pe->fn, dim3(grid), dim3(kPartThreads), pargs, smem, stream)) != cudaSuccess)
+      return cuda_fail(e, "launch partition kernel");
+    f->last_launches += 1;
+    const uint32_t slice_bytes_log2 = pl.shift + static_cast<uint32_t>(__builtin_ctz(f->p.block_bits / 8));
+    const uint32_t per_launch =
+        f->part.window_log2 > slice_bytes_log2 ? 1u << std::min<uint32_t>(f->part.window_log2 - slice_bytes_log2, 20) : 1u;
+    for (uint32_t plo = 0; plo < pl.nparts; plo += per_launch) {
+      const uint32_t phi = std::min(pl.nparts, plo + per_launch);
+      RecArgs ra{f->words, records, counts, plo, phi, cap, l.flags};
+      uint32_t rgrid = 0;
+      if ((s = resolve_grid(re->fn, f->device, l.block_threads, l.grid_ctas, (phi - plo) * cap, l.kpt, &rgrid)) !=
+          BF_OK)
+        return s;
+      void* rargs[] = {&ra};
+      if ((e = cudaLaunchKernel(re->fn, dim3(rgrid), dim3(l.block_threads), rargs, 0, stream)) != cudaSuccess)
+        return cuda_fail(e, "launch record-insert kernel");
+      f->last_launches += 1;
+    }
+  }
+  return BF_OK;
+}
+
+bf_status run_add(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
+  if (use_partitioned(f, n)) return launch_partitioned(f, keys, n, stream);
+  return launch_sbf(f, BF_OP_ADD, keys, n, nullptr, stream);
+}
+
+// Can the kernels read (and for results, write) this host buffer directly?
+bool device_can_access(const bf_filter* f, const void* h) {
+  if (f->host_access != 0) return false;
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, h) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) return true;
+  if (attr.type == cudaMemoryTypeHost) return attr.devicePointer == h;
+  int pageable = 0;
+  cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, f->device);
+  return pageable == 1;
 }
 
 // Bytes of one staging slot: the keys, then the results, each region padded
@@ -279,6 +421,12 @@ void release_pipeline(bf_filter* f) {
 // depth-many streams overlap one chunk's copies with another's kernel.
 bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
                         cudaStream_t stream) {
+  // Grace-coupled GPUs read host memory coherently over NVLink-C2C: the
+  // kernels then stream the keys (and write the results) in place.
+  if (device_can_access(f, h_keys) && (op == BF_OP_ADD || device_can_access(f, h_out))) {
+    if (op == BF_OP_ADD) return run_add(f, h_keys, n, stream);
+    return launch_sbf(f, BF_OP_CONTAINS, h_keys, n, h_out, stream);
+  }
   bf_status s = ensure_pipeline(f);
   if (s != BF_OK) return s;
   cudaError_t e = cudaEventRecord(f->ev_start, stream);
@@ -296,7 +444,8 @@ bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n
     uint8_t* d_out = reinterpret_cast<uint8_t*>(slot_base + keys_region(f->chunk_keys));
     if ((e = cudaMemcpyAsync(d_keys, h_keys + lo, cnt * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync H2D");
-    if ((s = launch_sbf(f, op, d_keys, cnt, d_out, st)) != BF_OK) return s;
+    if ((s = op == BF_OP_ADD ? run_add(f, d_keys, cnt, st) : launch_sbf(f, op, d_keys, cnt, d_out, st)) != BF_OK)
+      return s;
     if (op == BF_OP_CONTAINS &&
         (e = cudaMemcpyAsync(h_out + lo, d_out, cnt, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync D2H");
@@ -345,6 +494,9 @@ bf_status bf_create(const bf_params* params, void* d_words, bf_filter** out) {
     return cuda_fail(e, "cudaGetDevice");
   }
   for (int op = 0; op < 2; ++op) resolve_layout(f->p, op, nullptr, &f->layout[op], &f->entry[op]);
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, f->device);
+  f->l2_bytes = static_cast<uint64_t>(l2);
   if (d_words) {
     const uint64_t align = std::max<uint64_t>(32, params->block_bits / 8);
     if (reinterpret_cast<uintptr_t>(d_words) % align != 0) {
@@ -376,6 +528,7 @@ bf_status bf_destroy(bf_filter* f) {
   if (!f) return fail(BF_EINVAL, "filter is NULL");
   DeviceGuard g(f->device);
   release_pipeline(f);
+  if (f->part_ws) cudaFree(f->part_ws);
   if (f->owned && f->words) cudaFree(f->words);
   delete f;
   return BF_OK;
@@ -394,7 +547,8 @@ bf_status bf_add(bf_filter* f, const uint64_t* d_keys, uint64_t n, bf_stream_t s
   if (!d_keys) return fail(BF_EINVAL, "keys is NULL");
   if (reinterpret_cast<uintptr_t>(d_keys) % 8) return fail(BF_EINVAL, "keys must be 8-byte aligned");
   DeviceGuard g(f->device);
-  return launch_sbf(f, BF_OP_ADD, d_keys, n, nullptr, reinterpret_cast<cudaStream_t>(stream));
+  f->last_launches = 0;
+  return run_add(f, d_keys, n, reinterpret_cast<cudaStream_t>(stream));
 }
 
 bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, uint8_t* d_out,
@@ -404,6 +558,7 @@ bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, ui
   if (!d_keys || !d_out) return fail(BF_EINVAL, "keys or out is NULL");
   if (reinterpret_cast<uintptr_t>(d_keys) % 8) return fail(BF_EINVAL, "keys must be 8-byte aligned");
   DeviceGuard g(f->device);
+  const_cast<bf_filter*>(f)->last_launches = 0;
   return launch_sbf(f, BF_OP_CONTAINS, d_keys, n, d_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -412,6 +567,7 @@ bf_status bf_add_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, bf_strea
   if (n == 0) return BF_OK;
   if (!h_keys) return fail(BF_EINVAL, "keys is NULL");
   DeviceGuard g(f->device);
+  f->last_launches = 0;
   return host_pipeline(f, BF_OP_ADD, h_keys, n, nullptr, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -421,16 +577,19 @@ bf_status bf_contains_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, uin
   if (n == 0) return BF_OK;
   if (!h_keys || !h_out) return fail(BF_EINVAL, "keys or out is NULL");
   DeviceGuard g(f->device);
+  f->last_launches = 0;
   return host_pipeline(f, BF_OP_CONTAINS, h_keys, n, h_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
-bf_status bf_set_staging(bf_filter* f, uint64_t chunk_keys) {
+bf_status bf_set_staging(bf_filter* f, uint64_t chunk_keys, int mode) {
   if (!f) return fail(BF_EINVAL, "filter is NULL");
   if (chunk_keys < 1024 || chunk_keys > (1ull << 32))
     return fail(BF_EINVAL, "chunk_keys must be in [1024, 2^32]");
+  if (mode != BF_HOST_AUTO && mode != BF_HOST_STAGED) return fail(BF_EINVAL, "mode must be BF_HOST_AUTO or BF_HOST_STAGED");
   DeviceGuard g(f->device);
   release_pipeline(f);
   f->chunk_keys = chunk_keys;
+  f->host_access = mode;
   return BF_OK;
 }
 
@@ -534,7 +693,29 @@ bf_status bf_gups(int mode, void* d_table, uint64_t table_bytes, uint32_t unit_b
   return err == cudaSuccess ? BF_OK : cuda_fail(err, "launch gups kernel");
 }
 
-uint32_t bf_launches_per_call(void) { return 1; }
+bf_status bf_set_partition(bf_filter* f, const bf_partition* cfg) {
+  if (!f || !cfg) return fail(BF_EINVAL, "NULL argument");
+  if (cfg->mode > BF_PART_AUTO) return fail(BF_EINVAL, "mode must be BF_PART_OFF, BF_PART_ON or BF_PART_AUTO");
+  if (cfg->slice_log2 < 16 || cfg->slice_log2 > 34) return fail(BF_EINVAL, "slice_log2 must be in [16, 34]");
+  if (cfg->chunk_keys < 4096) return fail(BF_EINVAL, "chunk_keys must be >= 4096");
+  if (cfg->cap_override % kRecTile) return fail(BF_EINVAL, "cap_override must be a multiple of 128");
+  if (cfg->window_log2 < 16 || cfg->window_log2 > 36) return fail(BF_EINVAL, "window_log2 must be in [16, 36]");
+  if (cfg->reserved != 0) return fail(BF_EINVAL, "reserved must be 0");
+  f->part = *cfg;
+  return BF_OK;
+}
+
+bf_status bf_get_partition(const bf_filter* f, bf_partition* out) {
+  if (!f || !out) return fail(BF_EINVAL, "NULL argument");
+  *out = f->part;
+  return BF_OK;
+}
+
+bf_status bf_last_launches(const bf_filter* f, uint32_t* n) {
+  if (!f || !n) return fail(BF_EINVAL, "NULL argument");
+  *n = f->last_launches;
+  return BF_OK;
+}
 
 const char* bf_status_str(bf_status s) {
   switch (s) {

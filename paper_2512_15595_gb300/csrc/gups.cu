@@ -10,7 +10,7 @@
 #include <vector>
 
 #include "registry.h"
-#include "sbf_kernels.cuh"
+#include "sbf_register.cuh"
 
 namespace bloomgb {
 

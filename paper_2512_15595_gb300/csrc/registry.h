@@ -2,6 +2,7 @@
 // (operation, geometry, layout) to its kernel.  Plain structs, shared by the
 // kernel translation units and the host API.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <vector>
 
@@ -29,8 +30,52 @@ struct GupsArgs {
   int unit_mode;  // same encoding as SbfArgs::block_mode
 };
 
+// Launch geometry of the slice-partition kernel, shared by the kernel and the host.
+constexpr int kPartThreads = 512;
+constexpr int kPartKeysPerThread = 8;
+constexpr int kPartTile = kPartThreads * kPartKeysPerThread;  // keys per CTA tile
+constexpr int kMaxParts = 1024;
+constexpr uint64_t kRecTile = 128;  // slice buffer capacity granule: the largest record tile (32 x KPT)
+
+// dynamic shared memory of the partition kernel for `nparts` slices
+constexpr size_t partition_smem_bytes(int nparts) {
+  return static_cast<size_t>(kPartTile) * 8        // records of the tile, sorted by slice
+         + static_cast<size_t>(kPartTile) * 2      // slice of each sorted record
+         + static_cast<size_t>(nparts) * 4 * 2     // per-slice count and start in the tile
+         + static_cast<size_t>(nparts) * 8         // per-slice reserved global position
+         + 64 * 4;                                 // scan scratch (one entry per warp)
+}
+
+// Arguments of the slice-partition kernel (L2-blocked construction).
+struct PartArgs {
+  const uint64_t* keys;
+  uint64_t n;
+  uint64_t acc0;
+  uint64_t nblocks;              // b <= 2^32 (records hold the block index in 32 bits)
+  int block_mode;
+  uint32_t shift;                // slice of block j = j >> shift
+  uint32_t nparts;               // number of slices (<= 1024)
+  uint64_t cap;                  // record slots per slice buffer (multiple of 128)
+  unsigned long long* counts;    // [nparts] records reserved per slice (zeroed before launch)
+  uint64_t* records;             // [nparts * cap] records (j << 32 | h_lo)
+  void* filter;                  // overflow records are inserted here directly
+};
+
+// Arguments of the record-insert kernel.
+// Arguments of the record-insert kernel: slices [part_lo, part_hi) of the
+// slice buffers (one launch per group of slices keeps the warps within one
+// L2-sized window of the filter; a kernel boundary re-synchronises them).
+struct RecArgs {
+  void* filter;
+  const uint64_t* records;
+  const unsigned long long* counts;
+  uint32_t part_lo, part_hi;
+  uint64_t cap;
+  uint32_t flags;
+};
+
 struct KernelEntry {
-  int op;  // 0 add, 1 contains
+  int op;  // 0 add, 1 contains, 2 add from slice records, 3 slice partition
   int B, S, K, theta, phi, kpt;
   const void* fn;
 };

@@ -2,7 +2,7 @@
 // per pair with -DSBF_B=<block bits> -DSBF_S=<word bits>, so the kernel
 // instantiations are spread over parallel compiler processes.
 #include "registry.h"
-#include "sbf_kernels.cuh"
+#include "sbf_register.cuh"
 
 #if !defined(SBF_B) || !defined(SBF_S)
 #error "compile with -DSBF_B=<block bits> -DSBF_S=<word bits>"

@@ -230,43 +230,4 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_add_kernel(const SbfArgs
   }
 }
 
-// ---------------------------------------------------------------------------
-// kernel registry
-// ---------------------------------------------------------------------------
-template <class F, int... I>
-__host__ void host_static_for_impl(F&& f, std::integer_sequence<int, I...>) {
-  (f(std::integral_constant<int, I>{}), ...);
-}
-template <int N, class F>
-__host__ void host_static_for(F&& f) {
-  host_static_for_impl(f, std::make_integer_sequence<int, N>{});
-}
-
-constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
-
-template <int B, int S, int K>
-void register_k(std::vector<KernelEntry>& v) {
-  constexpr int s = B / S;
-  host_static_for<ilog2(s) + 1>([&](auto lt) {
-    constexpr int T = 1 << decltype(lt)::value;
-    host_static_for<ilog2(s / T) + 1>([&](auto lp) {
-      constexpr int P = 1 << decltype(lp)::value;
-      host_static_for<3>([&](auto lk) {
-        constexpr int KPT = 1 << decltype(lk)::value;
-        using C = Cfg<B, S, K, T, P, KPT>;
-        v.push_back({0, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_add_kernel<C>)});
-        v.push_back({1, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_contains_kernel<C>)});
-      });
-    });
-  });
-}
-
-template <int B, int S>
-void register_geometry(std::vector<KernelEntry>& v) {
-  constexpr int s = B / S;
-  if constexpr (4 % s == 0) register_k<B, S, 4>(v);
-  if constexpr (s <= 8) register_k<B, S, 8>(v);
-  if constexpr (s <= 16) register_k<B, S, 16>(v);
-}
-
 }  // namespace bloomgb

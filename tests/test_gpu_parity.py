@@ -201,7 +201,8 @@ def test_library_allocated_filter(torch):
         _lib.bf_destroy(h)
 
 
-def test_host_pipeline(torch):
+@pytest.mark.parametrize("mode", ["direct_pinned", "direct_pageable", "staged"])
+def test_host_pipeline(torch, mode):
     from paper_2512_15595_gb300 import _lib
     geom = oracle.Geometry(num_blocks=10007, block_bits=256, word_bits=32, k=8, seed=3)
     ins = synthkeys.insert_keys(300_001, seed=61)
@@ -209,15 +210,86 @@ def test_host_pipeline(torch):
     ref = oracle.SBF(geom)
     ref.add(ins)
     f = gpu_filter(geom, torch)
-    _lib.bf_set_staging(f.handle, 4096 * 7 + 3)  # several chunks plus a ragged one
-    h_ins = torch.from_numpy(ins.view(np.int64)).pin_memory()
-    h_q = torch.from_numpy(q.view(np.int64)).pin_memory()
-    h_out = torch.empty(q.size, dtype=torch.uint8).pin_memory()
-    f.add_host(h_ins.numpy())
-    f.contains_host(h_q.numpy(), h_out.numpy())
+    # several chunks plus a ragged one when staged
+    _lib.bf_set_staging(f.handle, 4096 * 7 + 3, _lib.BF_HOST_STAGED if mode == "staged" else _lib.BF_HOST_AUTO)
+    if mode == "direct_pageable":
+        h_ins, h_q = ins.copy(), q.copy()
+        h_out = np.empty(q.size, dtype=np.uint8)
+    else:
+        h_ins = torch.from_numpy(ins.view(np.int64)).pin_memory().numpy()
+        h_q = torch.from_numpy(q.view(np.int64)).pin_memory().numpy()
+        h_out = torch.empty(q.size, dtype=torch.uint8).pin_memory().numpy()
+    f.add_host(h_ins)
+    f.contains_host(h_q, h_out)
     torch.cuda.current_stream().synchronize()
+    if mode == "staged":
+        assert f.last_launches() == -(-q.size // (4096 * 7 + 3))
+    elif mode == "direct_pinned":
+        assert f.last_launches() == 1
     assert np.array_equal(words_np(f), ref.as_bytes())
-    assert np.array_equal(h_out.numpy(), ref.contains(q))
+    assert np.array_equal(h_out, ref.contains(q))
+    f.close()
+
+
+# ---------------------------------------------------------------------------
+# L2-blocked (partitioned) construction
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("B,S,k", [(256, 32, 8), (512, 64, 16), (64, 64, 4), (128, 32, 16), (1024, 64, 16)])
+def test_partitioned_add_bit_exact(torch, B, S, k):
+    from paper_2512_15595_gb300 import BF_OP_ADD, valid_layouts
+    geom = oracle.Geometry(num_blocks=(1 << 14) + 77, block_bits=B, word_bits=S, k=k, seed=123)
+    ins = synthkeys.insert_keys(150_001, seed=81)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    dk = dev_keys(torch, ins)
+    cases = [dict(slice_log2=16), dict(slice_log2=17, chunk_keys=4096 * 5 + 1), dict(slice_log2=16, cap_override=128),
+             dict(slice_log2=16, window_log2=17)]
+    for cfg in cases:
+        nparts = -(-geom.nbytes // (1 << cfg["slice_log2"]))
+        per_launch = 1 << max(0, cfg.get("window_log2", 26) - cfg["slice_log2"])
+        per_pass = 1 + -(-nparts // per_launch)
+        for cg, phi in valid_layouts(B, S)[:: max(1, len(valid_layouts(B, S)) // 4)]:
+            for kpt in (1, 4):
+                f = gpu_filter(geom, torch)
+                f.set_partition(mode=1, **cfg)
+                f.set_layout(BF_OP_ADD, cg=cg, phi=phi, kpt=kpt)
+                f.add(dk)
+                launches = f.last_launches()
+                assert np.array_equal(words_np(f), ref.as_bytes()), (cfg, cg, phi, kpt)
+                passes = -(-ins.size // cfg.get("chunk_keys", 1 << 32))
+                assert launches == per_pass * passes, (cfg, launches)
+                f.close()
+
+
+def test_partitioned_add_skewed_keys(torch):
+    # every key lands in one slice (duplicates): the slice buffer overflows and
+    # the overflow records take the direct path
+    geom = oracle.Geometry(num_blocks=1 << 15, block_bits=256, word_bits=32, k=8, seed=0)
+    base = synthkeys.insert_keys(64, seed=91)
+    ins = np.concatenate([np.repeat(base[:1], 200_000), base, np.repeat(base[5:7], 30_000)])
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    f = gpu_filter(geom, torch)
+    f.set_partition(mode=1, slice_log2=16)
+    f.add(dev_keys(torch, ins))
+    assert np.array_equal(words_np(f), ref.as_bytes())
+    f.close()
+
+
+def test_partition_auto_and_off(torch):
+    from paper_2512_15595_gb300 import _lib
+    geom = oracle.Geometry(num_blocks=1 << 12, block_bits=256, word_bits=32, k=8, seed=0)
+    f = gpu_filter(geom, torch)
+    assert f.partition()["mode"] == _lib.BF_PART_AUTO
+    f.add(dev_keys(torch, synthkeys.insert_keys(10_000)))
+    assert f.last_launches() == 1  # 128 KiB filter: fits L2, direct kernel
+    f.set_partition(mode=0)
+    f.add(dev_keys(torch, synthkeys.insert_keys(10_000)))
+    assert f.last_launches() == 1
+    with pytest.raises(Exception):
+        f.set_partition(mode=1, slice_log2=8)
+    with pytest.raises(Exception):
+        f.set_partition(mode=1, cap_override=100)
     f.close()
 
 
@@ -263,19 +335,26 @@ def test_l2_resident_32mib_with_and_without_persistence(torch):
 
 
 def test_hbm_resident_256mib(torch):
-    # 256 MiB is twice the GB300 L2, so most block accesses go to HBM
+    # 256 MiB is twice the GB300 L2, so most block accesses go to HBM; the
+    # default (auto) construction partitions by slice, the direct kernel must agree
     geom = oracle.Geometry(num_blocks=1 << 23, block_bits=256, word_bits=64, k=8, seed=0)
     n = (256 << 20) * 8 // 10
     ins = synthkeys.insert_keys(n)
     q, _ = synthkeys.stream_queries(0, 2_000_000, n)
     ref = oracle.SBF(geom)
     ref.add(ins)
-    f = gpu_filter(geom, torch)
-    f.add(dev_keys(torch, ins))
-    out = f.contains(dev_keys(torch, q))
-    assert np.array_equal(words_np(f), ref.as_bytes())
-    assert np.array_equal(out.cpu().numpy().astype(np.uint8), ref.contains(q))
-    f.close()
+    ref_out = ref.contains(q)
+    dk, dq = dev_keys(torch, ins), dev_keys(torch, q)
+    # auto: 16 MiB slices, 64 MiB windows -> 1 partition + 4 record-insert launches
+    for mode, launches in ((2, 5), (0, 1)):
+        f = gpu_filter(geom, torch)
+        f.set_partition(mode=mode)
+        f.add(dk)
+        assert f.last_launches() == launches
+        out = f.contains(dq)
+        assert np.array_equal(words_np(f), ref.as_bytes())
+        assert np.array_equal(out.cpu().numpy().astype(np.uint8), ref_out)
+        f.close()
 
 
 @pytest.mark.parametrize("nblocks", [1 << 32, (1 << 32) + 12345])
