@@ -229,6 +229,30 @@ bf_status bf_gups(int mode, void* d_table, uint64_t table_bytes, uint32_t unit_b
                   const uint64_t* d_keys, uint64_t n, uint8_t* d_out, const bf_layout* layout,
                   bf_stream_t stream);
 
+/* Construction that allocates nothing (the paper has no counterpart: this is
+   an interface for callers of this library).  Some callers cannot let a
+   library call cudaMalloc -- services whose own caching allocator owns the
+   GPU's free memory, and latency-critical loops that must not pay for the
+   device synchronization cudaMalloc / cudaFree imply.  bf_add_noalloc sets
+   the same bits as bf_add (slice-partitioned construction with the default
+   layout) into the caller's bit array d_words (geometry `params`, alignment as
+   for bf_create), with its scratch in one 16 MiB array that the library keeps
+   on every GPU that loads it, until the process exits.  No filter handle is
+   needed.
+   Limits: num_blocks <= 2^32, and n must fit the array: *max_keys (if not
+   NULL) receives the largest n accepted for this geometry (from about 2.08
+   million keys for a filter of one 16 MiB slice down to about 1.40 million
+   for 1024 slices), and a larger n returns BF_EINVAL with nothing enqueued --
+   split the keys over several calls.
+   Every call shares the one array (the call clears the counters it needs):
+   calls whose work overlaps on the GPU -- other streams, other host threads --
+   race and corrupt each other's scratch; serialize them.  The first call on
+   each device looks up the array's device address (cudaGetSymbolAddress) with
+   that device current; make that first call before any stream capture.
+   Errors are reported by the status only (bf_last_error is not updated). */
+bf_status bf_add_noalloc(const bf_params* params, void* d_words, const uint64_t* d_keys, uint64_t n,
+                         uint64_t* max_keys, bf_stream_t stream);
+
 const char* bf_status_str(bf_status s);
 
 /* Message of the last error on the calling host thread ("" if none). */

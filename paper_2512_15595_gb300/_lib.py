@@ -25,8 +25,8 @@ EXPORTED = (
     "bf_params_check", "bf_layout_check", "bf_create", "bf_destroy", "bf_clear", "bf_add",
     "bf_contains", "bf_add_host", "bf_contains_host", "bf_set_staging", "bf_words",
     "bf_get_params", "bf_set_layout", "bf_get_layout", "bf_set_l2_persist", "bf_gups",
-    "bf_set_partition", "bf_get_partition", "bf_last_launches", "bf_status_str", "bf_last_error",
-    "bf_version",
+    "bf_set_partition", "bf_get_partition", "bf_last_launches", "bf_add_noalloc", "bf_status_str",
+    "bf_last_error", "bf_version",
 )
 
 
@@ -99,6 +99,7 @@ def lib():
         "bf_set_partition": (i32, [vp, ctypes.POINTER(bf_partition)]),
         "bf_get_partition": (i32, [vp, ctypes.POINTER(bf_partition)]),
         "bf_last_launches": (i32, [vp, ctypes.POINTER(u32)]),
+        "bf_add_noalloc": (i32, [P, vp, vp, u64, ctypes.POINTER(u64), vp]),
         "bf_status_str": (ctypes.c_char_p, [i32]),
         "bf_last_error": (ctypes.c_char_p, []),
         "bf_version": (ctypes.c_char_p, []),

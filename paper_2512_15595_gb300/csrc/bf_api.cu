@@ -733,3 +733,132 @@ const char* bf_last_error(void) { return g_last_error.c_str(); }
 const char* bf_version(void) { return "bloomgb 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Construction with library-owned static scratch (no allocation per call).
+//
+// Some callers cannot let a library call cudaMalloc: services that give the
+// GPU's memory to their own caching allocator up front (a cudaMalloc would
+// then fail, or force the pool to hand memory back), and latency-critical
+// loops that must not pay for cudaMalloc / cudaFree, which synchronize the
+// device.  For them, bf_add_noalloc runs the slice-partitioned construction
+// with its scratch (per-slice counters and slice buffers) in one file-scope
+// device array, kNoAllocScratchBytes in size, that every GPU loading this
+// library holds until the process exits.  The caller passes the bit array
+// and the keys; nothing is allocated by a call.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint64_t kNoAllocScratchBytes = 16ull << 20;            // 16 MiB per device
+constexpr uint64_t kNoAllocCountsBytes = 8ull * kMaxParts;         // per-slice counters
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// The kernel table is built while the library loads, so that the first
+// bf_add_noalloc call does not build it.
+const bool g_noalloc_registry_ready = (registry(), true);
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current.
+cudaError_t noalloc_scratch(int device, void** out) {
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[device] = ptr;
+  }
+  *out = g_noalloc_ptr[device];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" bf_status bf_add_noalloc(const bf_params* params, void* d_words, const uint64_t* d_keys, uint64_t n,
+                                    uint64_t* max_keys, bf_stream_t stream) {
+  (void)g_noalloc_registry_ready;
+  if (max_keys) *max_keys = 0;
+  if (!params || !d_words) return BF_EINVAL;
+  if (params->reserved != 0 || params->num_blocks == 0 || params->num_blocks > (1ull << 32) ||
+      (params->word_bits != 32 && params->word_bits != 64) || !is_pow2(params->block_bits) ||
+      params->block_bits < params->word_bits || params->block_bits > 1024)
+    return BF_EINVAL;
+  const uint32_t s = params->block_bits / params->word_bits;
+  if (params->k < s || params->k % s != 0 || params->k > 64) return BF_EINVAL;
+  if (reinterpret_cast<uintptr_t>(d_words) % std::max<uint32_t>(32, params->block_bits / 8) != 0) return BF_EINVAL;
+  const KernelEntry* pe = nullptr;
+  const KernelEntry* re = nullptr;
+  for (const auto& e : registry().sbf) {
+    if (e.B != static_cast<int>(params->block_bits) || e.S != static_cast<int>(params->word_bits) ||
+        e.K != static_cast<int>(params->k))
+      continue;
+    if (e.op == 3) pe = &e;
+    if (e.op == 2 && e.theta == static_cast<int>(s) && e.phi == 1 && e.kpt == 1) re = &e;
+  }
+  if (!pe || !re) return BF_EUNSUPPORTED;
+
+  // slice plan of the default partitioned construction (16 MiB slices, one
+  // record-insert launch per 64 MiB window)
+  bf_filter plan{};
+  plan.p = *params;
+  plan.nbytes = params->num_blocks * (params->block_bits / 8);
+  const PartPlan pl = part_plan(&plan);
+  // the largest n whose slice buffers fit next to the counters
+  uint64_t lo = 0, hi = kNoAllocScratchBytes / 8;
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo + 1) / 2;
+    if (kNoAllocCountsBytes + static_cast<uint64_t>(pl.nparts) * part_cap(&plan, pl, mid) * 8 <= kNoAllocScratchBytes)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  if (max_keys) *max_keys = lo;
+  if (n > lo) return BF_EINVAL;  // too many keys for the static scratch: split the call
+  if (n == 0) return BF_OK;
+  if (!d_keys || reinterpret_cast<uintptr_t>(d_keys) % 8) return BF_EINVAL;
+
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kNoAllocMaxDevices) return BF_ECUDA;
+  void* scratch = nullptr;
+  if (noalloc_scratch(device, &scratch) != cudaSuccess) return BF_ECUDA;
+  unsigned long long* counts = static_cast<unsigned long long*>(scratch);
+  uint64_t* records = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + kNoAllocCountsBytes);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+  // the array keeps the previous call's contents: the counters must start at zero
+  if (cudaMemsetAsync(counts, 0, 8ull * pl.nparts, st) != cudaSuccess) return BF_ECUDA;
+  const uint64_t cap = part_cap(&plan, pl, n);
+  const size_t smem = partition_smem_bytes(static_cast<int>(pl.nparts));
+  if (cudaFuncSetAttribute(pe->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+    return BF_ECUDA;
+  int sms = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return BF_ECUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pe->fn, kPartThreads, smem) != cudaSuccess)
+    return BF_ECUDA;
+  const uint64_t tiles = (n + kPartTile - 1) / kPartTile;
+  PartArgs pa{d_keys, n, params->seed + 0x27D4EB2F165667C5ull + 8ull, params->num_blocks,
+              params->num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, d_words};
+  void* pargs[] = {&pa};
+  const uint32_t pgrid = static_cast<uint32_t>(std::min<uint64_t>(tiles, static_cast<uint64_t>(sms) * std::max(per_sm, 1)));
+  if (cudaLaunchKernel(pe->fn, dim3(pgrid), dim3(kPartThreads), pargs, smem, st) != cudaSuccess) return BF_ECUDA;
+
+  constexpr uint32_t kThreads = 256;
+  int rper_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper_sm, re->fn, kThreads, 0) != cudaSuccess) return BF_ECUDA;
+  const uint32_t slice_bytes_log2 = pl.shift + static_cast<uint32_t>(__builtin_ctz(params->block_bits / 8));
+  const uint32_t per_launch = 26 > slice_bytes_log2 ? 1u << (26 - slice_bytes_log2) : 1u;
+  for (uint32_t plo = 0; plo < pl.nparts; plo += per_launch) {
+    const uint32_t phi = std::min(pl.nparts, plo + per_launch);
+    RecArgs ra{d_words, records, counts, plo, phi, cap, 0u};
+    const uint64_t rtiles = (static_cast<uint64_t>(phi - plo) * cap + 31) / 32;
+    const uint64_t rctas = (rtiles + kThreads / 32 - 1) / (kThreads / 32);
+    const uint32_t rgrid =
+        static_cast<uint32_t>(std::min<uint64_t>(rctas, static_cast<uint64_t>(sms) * std::max(rper_sm, 1)));
+    void* rargs[] = {&ra};
+    if (cudaLaunchKernel(re->fn, dim3(rgrid), dim3(kThreads), rargs, 0, st) != cudaSuccess) return BF_ECUDA;
+  }
+  return BF_OK;
+}
