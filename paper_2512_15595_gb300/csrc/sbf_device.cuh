@@ -134,18 +134,20 @@ __device__ __forceinline__ void ld_key4(const uint64_t* p, uint64_t pol, uint64_
 }
 
 // filter word loads for lookup: read-only during the kernel, no L1 allocation
-// (random blocks have no reuse in L1), L2 policy chosen by the caller.
+// (random blocks have no reuse in L1), L2 policy chosen by the caller, and an
+// L2 fetch of 64 bytes: a random 32-byte access otherwise pulls a whole
+// 128-byte line from HBM (measured), wasting bandwidth the key stream needs.
 // NWORDS contiguous words starting at p (aligned to the access width).
 template <int NW>
 __device__ __forceinline__ void ld_words(const uint32_t* p, uint64_t pol, uint32_t* w) {
   if constexpr (NW == 1) {
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;"
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.L2::64B.u32 %0, [%1], %2;"
                  : "=r"(w[0]) : "l"(p), "l"(pol));
   } else if constexpr (NW == 2) {
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.L2::64B.v2.u32 {%0,%1}, [%2], %3;"
                  : "=r"(w[0]), "=r"(w[1]) : "l"(p), "l"(pol));
   } else if constexpr (NW == 4) {
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.L2::64B.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
                  : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p), "l"(pol));
   } else {
     static_assert(NW % 8 == 0, "word count");
@@ -153,7 +155,7 @@ __device__ __forceinline__ void ld_words(const uint32_t* p, uint64_t pol, uint32
     for (int c = 0; c < NW / 8; ++c) {
       uint32_t* o = w + 8 * c;
       asm volatile(
-          "ld.global.nc.L1::no_allocate.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+          "ld.global.nc.L1::no_allocate.L2::cache_hint.L2::64B.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
           : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]),
             "=r"(o[7])
           : "l"(p + 8 * c), "l"(pol));
@@ -163,17 +165,17 @@ __device__ __forceinline__ void ld_words(const uint32_t* p, uint64_t pol, uint32
 template <int NW>
 __device__ __forceinline__ void ld_words(const uint64_t* p, uint64_t pol, uint64_t* w) {
   if constexpr (NW == 1) {
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;"
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.L2::64B.u64 %0, [%1], %2;"
                  : "=l"(w[0]) : "l"(p), "l"(pol));
   } else if constexpr (NW == 2) {
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0,%1}, [%2], %3;"
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.L2::64B.v2.u64 {%0,%1}, [%2], %3;"
                  : "=l"(w[0]), "=l"(w[1]) : "l"(p), "l"(pol));
   } else {
     static_assert(NW % 4 == 0, "word count");
 #pragma unroll
     for (int c = 0; c < NW / 4; ++c) {
       uint64_t* o = w + 4 * c;
-      asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u64 {%0,%1,%2,%3}, [%4], %5;"
+      asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.L2::64B.v4.u64 {%0,%1,%2,%3}, [%4], %5;"
                    : "=l"(o[0]), "=l"(o[1]), "=l"(o[2]), "=l"(o[3])
                    : "l"(p + 4 * c), "l"(pol));
     }

@@ -66,6 +66,29 @@ struct LaneSalts {
   }
 };
 
+// OR one lane's PHI consecutive pattern words of step q into the filter at
+// `bp` (the lane's first word of the step).  For 32-bit words and an even PHI,
+// neighbouring words are merged into one 64-bit red (bits of word 2i in the
+// low half, word 2i+1 in the high half: the same bits, half the red
+// instructions through L1); word addresses are then 8-byte aligned because
+// block starts, steps and lane offsets are all even.
+template <class C>
+__device__ __forceinline__ void red_lane_words(typename C::word_t* bp, const LaneSalts<C>& salts, uint32_t hlo,
+                                               int q, uint64_t pol) {
+  if constexpr (C::S == 32 && C::PHI % 2 == 0) {
+    uint64_t* bp64 = reinterpret_cast<uint64_t*>(bp);
+#pragma unroll
+    for (int p = 0; p < C::PHI / 2; ++p) {
+      const uint64_t v = static_cast<uint64_t>(salts.pattern(hlo, q, 2 * p)) |
+                         (static_cast<uint64_t>(salts.pattern(hlo, q, 2 * p + 1)) << 32);
+      red_or(bp64 + p, v, pol);
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < C::PHI; ++p) red_or(bp + p, salts.pattern(hlo, q, p), pol);
+  }
+}
+
 // Load the lane's KPT keys; returns the validity mask.
 template <int KPT>
 __device__ __forceinline__ uint32_t load_keys(const uint64_t* keys, uint64_t n, uint64_t base,
@@ -220,10 +243,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_add_kernel(const SbfArgs
           // instruction, so L1 merges them into one request per sector
           W* bp = filter + bm * C::s + r * PHI;
 #pragma unroll
-          for (int q = 0; q < STEPS; ++q) {
-#pragma unroll
-            for (int p = 0; p < PHI; ++p) red_or(bp + q * C::chunk + p, salts.pattern(hm, q, p), pol_filter);
-          }
+          for (int q = 0; q < STEPS; ++q) red_lane_words<C>(bp + q * C::chunk, salts, hm, q, pol_filter);
         }
       }
     }

@@ -39,7 +39,7 @@ __device__ __forceinline__ void insert_one(typename WordOf<S>::type* filter, uin
 }
 
 template <int B, int S, int K>
-__global__ void __launch_bounds__(kPartThreads) sbf_partition_kernel(const PartArgs a) {
+__global__ void __launch_bounds__(kPartThreads, 3) sbf_partition_kernel(const PartArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* tile_rec = reinterpret_cast<uint64_t*>(smem);
   uint16_t* tile_part = reinterpret_cast<uint16_t*>(tile_rec + kPartTile);
@@ -60,20 +60,25 @@ __global__ void __launch_bounds__(kPartThreads) sbf_partition_kernel(const PartA
     for (uint32_t p = tid; p < a.nparts; p += kPartThreads) cnt[p] = 0;
     __syncthreads();
 
-    // hash and count; key i of the tile is handled by thread i % kPartThreads
+    // key i of the tile is handled by thread i % kPartThreads; all loads are
+    // issued before any hashing so that their latencies overlap
     uint64_t rec[kPartKeysPerThread];
-    uint32_t part[kPartKeysPerThread];
-    uint32_t rank[kPartKeysPerThread];
 #pragma unroll
     for (int u = 0; u < kPartKeysPerThread; ++u) {
       const uint32_t i = u * kPartThreads + tid;
-      part[u] = 0xFFFFFFFFu;
-      if (i < tile_n) {
-        const uint64_t h = xxh64_key(ld_key1(a.keys + base + i, pol_keys), a.acc0);
+      rec[u] = i < tile_n ? ld_key1(a.keys + base + i, pol_keys) : 0;
+    }
+    // hash, count; pr = slice << 12 | rank within the tile's slice run
+    uint32_t pr[kPartKeysPerThread];
+#pragma unroll
+    for (int u = 0; u < kPartKeysPerThread; ++u) {
+      pr[u] = 0xFFFFFFFFu;
+      if (u * kPartThreads + tid < tile_n) {
+        const uint64_t h = xxh64_key(rec[u], a.acc0);
         const uint64_t j = block_of(h, a.nblocks, a.block_mode);
         rec[u] = (j << 32) | static_cast<uint32_t>(h);
-        part[u] = static_cast<uint32_t>(j >> a.shift);
-        rank[u] = atomicAdd(&cnt[part[u]], 1u);
+        const uint32_t part = static_cast<uint32_t>(j >> a.shift);
+        pr[u] = (part << 12) | atomicAdd(&cnt[part], 1u);
       }
     }
     __syncthreads();
@@ -113,10 +118,11 @@ __global__ void __launch_bounds__(kPartThreads) sbf_partition_kernel(const PartA
       gpos[p] = cnt[p] ? atomicAdd(a.counts + p, static_cast<unsigned long long>(cnt[p])) : 0ull;
 #pragma unroll
     for (int u = 0; u < kPartKeysPerThread; ++u) {
-      if (part[u] != 0xFFFFFFFFu) {
-        const uint32_t pos = start[part[u]] + rank[u];
+      if (pr[u] != 0xFFFFFFFFu) {
+        const uint32_t part = pr[u] >> 12;
+        const uint32_t pos = start[part] + (pr[u] & 0xFFFu);
         tile_rec[pos] = rec[u];
-        tile_part[pos] = static_cast<uint16_t>(part[u]);
+        tile_part[pos] = static_cast<uint16_t>(part);
       }
     }
     __syncthreads();
@@ -182,10 +188,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_add_records_kernel(const
           const uint32_t hm = static_cast<uint32_t>(rm);
           W* bp = filter + (rm >> 32) * C::s + r * PHI;
 #pragma unroll
-          for (int q = 0; q < STEPS; ++q) {
-#pragma unroll
-            for (int pp = 0; pp < PHI; ++pp) red_or(bp + q * C::chunk + pp, salts.pattern(hm, q, pp), pol_filter);
-          }
+          for (int q = 0; q < STEPS; ++q) red_lane_words<C>(bp + q * C::chunk, salts, hm, q, pol_filter);
         }
       }
     }
