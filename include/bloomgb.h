@@ -177,32 +177,39 @@ bf_status bf_get_layout(const bf_filter* f, int op, bf_layout* out);
    lines and sets the limit back to 0. */
 bf_status bf_set_l2_persist(bf_filter* f, bf_stream_t stream, float hit_ratio);
 
-/* L2-blocked construction (this library's addition; the paper's kernel is the
-   direct one).  For a filter larger than L2 the keys are hashed and radix-
-   partitioned by filter slice (2^slice_log2 bytes of the bit array), then each
-   slice's atomic ORs run while the slice sits in L2.  The bits set are the
-   same as with direct construction (OR is commutative and idempotent).  The
-   partition buffers (about 8 bytes per key of a pass, at most chunk_keys keys
-   per pass) are allocated on the first partitioned bf_add and kept until
-   bf_destroy; if that allocation fails bf_add uses the direct kernel.  A key
-   whose slice buffer is full is inserted directly, so any key distribution is
-   handled.  Partitioning needs num_blocks <= 2^32 and more than one slice.
-   mode: BF_PART_OFF = direct kernel only; BF_PART_ON = partition whenever it
-   applies; BF_PART_AUTO (default) = partition when the bit array is larger
-   than half the L2 and the pass has at least num_blocks/2 keys.
-   cap_override: slots per slice buffer (0 = computed from the pass size;
-   small values force the overflow path, for tests).  window_log2: the
-   record-insert kernel is launched once per 2^window_log2 bytes of the bit
-   array (at least one slice per launch), so that all warps stay inside one
-   L2-sized window of the filter. */
+/* Slice-partitioned construction and lookup (this library's addition; the
+   paper's kernels are the direct ones).  For a filter larger than L2 the keys
+   are hashed and radix-partitioned by filter slice (2^slice_log2 bytes of the
+   bit array); then the slices are processed one L2-sized window
+   (2^window_log2 bytes, at least one slice) per kernel launch, so the
+   window's blocks are read and updated from L2 instead of HBM.
+   Construction ORs each key's pattern into its block exactly as the direct
+   kernel does (OR is commutative and idempotent: the same bits).  Lookup
+   keeps each query's index with its record, sets one bit per positive query
+   in a result bitmap, and expands the bitmap into the result bytes: the same
+   answers as the direct kernel.  A key or query whose slice buffer is full
+   is handled on the spot by the direct method, so any key distribution is
+   handled.  The buffers (about 8 bytes per key of a construction pass; 12
+   bytes per query plus a bit per query of a lookup pass) are allocated on
+   first use and kept until bf_destroy; if an allocation fails the direct
+   kernel runs.  Partitioning needs num_blocks <= 2^32 and more than one slice.
+   mode (construction) and lookup_mode: BF_PART_OFF = direct kernel only;
+   BF_PART_ON = partition whenever it applies; BF_PART_AUTO (default) =
+   partition when the bit array is larger than half the L2 and the call has
+   at least num_blocks/2 keys (construction) or num_blocks/4 queries (lookup).
+   chunk_keys / lookup_chunk_keys: keys per pass (lookup default 2^28, so that
+   the pass's result bitmap stays in L2).  cap_override: slots per slice
+   buffer (0 = computed from the pass size; small values force the overflow
+   path, for tests). */
 typedef enum { BF_PART_OFF = 0, BF_PART_ON = 1, BF_PART_AUTO = 2 } bf_part_mode;
 typedef struct {
-    uint32_t mode;
-    uint32_t slice_log2;     /* 16..34; default 24 (16 MiB) */
-    uint64_t chunk_keys;     /* >= 4096; default 2^32 */
-    uint64_t cap_override;   /* 0 = computed; else a multiple of 128 */
-    uint32_t window_log2;    /* 16..36, >= slice_log2 in effect; default 26 (64 MiB) */
-    uint32_t reserved;       /* must be 0 */
+    uint32_t mode;               /* construction; default BF_PART_AUTO */
+    uint32_t slice_log2;         /* 16..34; default 24 (16 MiB) */
+    uint64_t chunk_keys;         /* >= 4096; default 2^32 */
+    uint64_t cap_override;       /* 0 = computed; else a multiple of 128 */
+    uint32_t window_log2;        /* 16..36; default 26 (64 MiB) */
+    uint32_t lookup_mode;        /* default BF_PART_AUTO */
+    uint64_t lookup_chunk_keys;  /* 4096..2^32; default 2^28 */
 } bf_partition;
 bf_status bf_set_partition(bf_filter* f, const bf_partition* cfg);
 bf_status bf_get_partition(const bf_filter* f, bf_partition* out);

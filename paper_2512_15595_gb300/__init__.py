@@ -103,11 +103,18 @@ class Filter:
     def layout(self, op: int) -> dict:
         return _lib.bf_get_layout(self.handle, op).as_dict()
 
-    def set_partition(self, mode: int = 2, slice_log2: int = 24, chunk_keys: int = 1 << 32,
-                      cap_override: int = 0, window_log2: int = 26) -> None:
-        """L2-blocked construction settings (mode 0 off, 1 on, 2 auto)."""
-        _lib.bf_set_partition(self.handle, _lib.bf_partition(mode, slice_log2, chunk_keys, cap_override,
-                                                             window_log2, 0))
+    def set_partition(self, mode: int | None = None, slice_log2: int | None = None, chunk_keys: int | None = None,
+                      cap_override: int | None = None, window_log2: int | None = None,
+                      lookup_mode: int | None = None, lookup_chunk_keys: int | None = None) -> None:
+        """Slice-partitioned construction / lookup settings (modes: 0 off, 1 on,
+        2 auto); arguments left as None keep their current value."""
+        cur = _lib.bf_get_partition(self.handle)
+        for name, val in (("mode", mode), ("slice_log2", slice_log2), ("chunk_keys", chunk_keys),
+                          ("cap_override", cap_override), ("window_log2", window_log2),
+                          ("lookup_mode", lookup_mode), ("lookup_chunk_keys", lookup_chunk_keys)):
+            if val is not None:
+                setattr(cur, name, val)
+        _lib.bf_set_partition(self.handle, cur)
 
     def partition(self) -> dict:
         return _lib.bf_get_partition(self.handle).as_dict()

@@ -51,7 +51,8 @@ BF_PART_OFF, BF_PART_ON, BF_PART_AUTO = 0, 1, 2
 class bf_partition(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("slice_log2", ctypes.c_uint32),
                 ("chunk_keys", ctypes.c_uint64), ("cap_override", ctypes.c_uint64),
-                ("window_log2", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("window_log2", ctypes.c_uint32), ("lookup_mode", ctypes.c_uint32),
+                ("lookup_chunk_keys", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -58,7 +58,7 @@ def apply_tuned(f: Filter, regime: str) -> dict:
             lay = dict(lay)
             part = lay.pop("partition", None)
             f.set_layout(op, **lay)
-            if part is not None and op == BF_OP_ADD:
+            if part is not None:
                 f.set_partition(**part)
         used[name] = f.layout(op)
     return used
@@ -86,18 +86,22 @@ def time_op(torch, f: Filter, op: int, keys, out, reps: int = 5, warmup: int = 2
 
 
 def sweep(torch, f: Filter, keys_add, keys_q, out, regime: str, kpts=(1, 2, 4), block_threads=(256,),
-          flags=0, reps: int = 5, flush=None, log=None, partitions=None) -> dict:
+          flags=0, reps: int = 5, flush=None, log=None, partitions=None, lookup_partitions=None) -> dict:
     """Time every layout of both operations; returns the table entry (and rows).
 
-    ``partitions``: list of construction-partitioning settings to sweep (dicts
-    for ``Filter.set_partition``), or None to keep the filter's setting.
+    ``partitions`` / ``lookup_partitions``: lists of slice-partitioning
+    settings (dicts for ``Filter.set_partition``) to sweep for construction /
+    lookup, or None to keep the filter's setting.  The lookup sweep runs with
+    the best construction setting applied (they share the slice geometry).
     """
     p = f.params
     rows = []
     best = {}
-    part_modes = [None] if partitions is None else partitions
     for op, name, keys in ((BF_OP_ADD, "add", keys_add), (BF_OP_CONTAINS, "contains", keys_q)):
-        for part in (part_modes if op == BF_OP_ADD else [None]):
+        parts = partitions if op == BF_OP_ADD else lookup_partitions
+        if op == BF_OP_CONTAINS and best.get("add", {}).get("layout", {}).get("partition"):
+            f.set_partition(**best["add"]["layout"]["partition"])
+        for part in ([None] if parts is None else parts):
             if part is not None:
                 f.set_partition(**part)
             for cg, phi in valid_layouts(p.block_bits, p.word_bits):

@@ -49,6 +49,7 @@ const Registry& registry() {
     BLOOMGB_GEOMETRIES(BLOOMGB_REGISTER)
 #undef BLOOMGB_REGISTER
     register_gups(reg.gups);
+    register_expand(reg.sbf);
     return reg;
   }();
   return r;
@@ -158,9 +159,11 @@ struct bf_filter {
   int host_access = 0;  // 0: kernels read device-accessible host buffers directly; 1: always stage
   bool l2_window = false;
   // L2-blocked construction
-  bf_partition part{BF_PART_AUTO, 24, 1ull << 32, 0, 26, 0};
+  bf_partition part{BF_PART_AUTO, 24, 1ull << 32, 0, 26, BF_PART_AUTO, 1ull << 28};
   void* part_ws = nullptr;
   uint64_t part_ws_bytes = 0;
+  void* look_ws = nullptr;  // slice-partitioned lookup workspace
+  uint64_t look_ws_bytes = 0;
   uint64_t l2_bytes = 0;
   uint32_t last_launches = 0;
 };
@@ -288,22 +291,24 @@ const KernelEntry* find_op(int op, const bf_params& p, uint32_t cg, uint32_t phi
   return find_sbf(op, p, l);
 }
 
-bf_status ensure_part_ws(bf_filter* f, uint64_t bytes) {
-  if (f->part_ws && f->part_ws_bytes >= bytes) return BF_OK;
-  if (f->part_ws) {
-    cudaFree(f->part_ws);
-    f->part_ws = nullptr;
-    f->part_ws_bytes = 0;
+bf_status ensure_ws(void** ws, uint64_t* ws_bytes, uint64_t bytes) {
+  if (*ws && *ws_bytes >= bytes) return BF_OK;
+  if (*ws) {
+    cudaFree(*ws);
+    *ws = nullptr;
+    *ws_bytes = 0;
   }
-  cudaError_t e = cudaMalloc(&f->part_ws, bytes);
+  cudaError_t e = cudaMalloc(ws, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    f->part_ws = nullptr;
+    *ws = nullptr;
     return fail(BF_ENOMEM, "partition workspace allocation failed");
   }
-  f->part_ws_bytes = bytes;
+  *ws_bytes = bytes;
   return BF_OK;
 }
+
+bf_status ensure_part_ws(bf_filter* f, uint64_t bytes) { return ensure_ws(&f->part_ws, &f->part_ws_bytes, bytes); }
 
 bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
   const PartPlan pl = part_plan(f);
@@ -355,6 +360,100 @@ bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cud
     }
   }
   return BF_OK;
+}
+
+bool use_partitioned_lookup(const bf_filter* f, uint64_t n) {
+  if (f->part.lookup_mode == BF_PART_OFF || f->p.num_blocks > (1ull << 32)) return false;
+  const PartPlan pl = part_plan(f);
+  if (pl.nparts < 2) return false;
+  if (f->part.lookup_mode == BF_PART_ON) return true;
+  return f->nbytes * 2 > f->l2_bytes && n >= f->p.num_blocks / 4;
+}
+
+const KernelEntry* find_expand() {
+  for (const auto& e : registry().sbf)
+    if (e.op == 6) return &e;
+  return nullptr;
+}
+
+// Slice-partitioned lookup: per pass of at most lookup_chunk_keys queries,
+// partition the queries by slice (with their indices), probe each L2-sized
+// window's records, setting a bit per positive query in a result bitmap
+// that stays in L2, then expand the bitmap into the result bytes.
+bf_status launch_contains_partitioned(const bf_filter* fc, const uint64_t* keys, uint64_t n, uint8_t* out,
+                                      cudaStream_t stream) {
+  bf_filter* f = const_cast<bf_filter*>(fc);
+  const PartPlan pl = part_plan(f);
+  const uint64_t pass = std::min<uint64_t>(n, f->part.lookup_chunk_keys);
+  const uint64_t cap_max = part_cap(f, pl, pass);
+  const uint64_t counts_bytes = 8ull * kMaxParts;
+  const uint64_t rec_bytes = static_cast<uint64_t>(pl.nparts) * cap_max * 8;
+  const uint64_t idx_bytes = static_cast<uint64_t>(pl.nparts) * cap_max * 4;
+  const uint64_t bitmap_bytes = ((pass + 31) / 32 * 4 + 255) / 256 * 256;
+  bf_status s = ensure_ws(&f->look_ws, &f->look_ws_bytes, counts_bytes + rec_bytes + idx_bytes + bitmap_bytes);
+  if (s != BF_OK) return launch_sbf(f, BF_OP_CONTAINS, keys, n, out, stream);  // no memory: direct kernel
+  const KernelEntry* pe = find_op(5, f->p, 0, 0, 0);
+  const bf_layout& l = f->layout[BF_OP_CONTAINS];
+  const KernelEntry* qe = find_op(4, f->p, l.cg, l.phi, l.kpt);
+  const KernelEntry* xe = find_expand();
+  if (!pe || !qe || !xe) return fail(BF_EUNSUPPORTED, "no partitioned lookup kernels for this geometry");
+  char* ws = static_cast<char*>(f->look_ws);
+  unsigned long long* counts = reinterpret_cast<unsigned long long*>(ws);
+  uint64_t* records = reinterpret_cast<uint64_t*>(ws + counts_bytes);
+  uint32_t* idx = reinterpret_cast<uint32_t*>(ws + counts_bytes + rec_bytes);
+  uint32_t* bitmap = reinterpret_cast<uint32_t*>(ws + counts_bytes + rec_bytes + idx_bytes);
+  const size_t smem = partition_smem_bytes(static_cast<int>(pl.nparts), true);
+  cudaError_t e = cudaFuncSetAttribute(pe->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(partition)");
+  int sms = 0, per_sm = 0;
+  if ((s = sm_count(f->device, &sms)) != BF_OK) return s;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pe->fn, kPartThreads, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(partition)");
+  per_sm = std::max(per_sm, 1);
+  const uint32_t slice_bytes_log2 = pl.shift + static_cast<uint32_t>(__builtin_ctz(f->p.block_bits / 8));
+  const uint32_t per_launch =
+      f->part.window_log2 > slice_bytes_log2 ? 1u << std::min<uint32_t>(f->part.window_log2 - slice_bytes_log2, 20) : 1u;
+  for (uint64_t lo = 0; lo < n; lo += pass) {
+    const uint64_t cnt = std::min(pass, n - lo);
+    const uint64_t cap = part_cap(f, pl, cnt);
+    if ((e = cudaMemsetAsync(counts, 0, 8ull * pl.nparts, stream)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if ((e = cudaMemsetAsync(bitmap, 0, (cnt + 31) / 32 * 4, stream)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemsetAsync");
+    PartArgs pa{keys + lo, cnt, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, f->p.num_blocks,
+                f->p.num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, f->words, idx,
+                bitmap};
+    const uint64_t tiles = (cnt + kPartTile - 1) / kPartTile;
+    const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, static_cast<uint64_t>(sms) * per_sm));
+    void* pargs[] = {&pa};
+    if ((e = cudaLaunchKernel(pe->fn, dim3(grid), dim3(kPartThreads), pargs, smem, stream)) != cudaSuccess)
+      return cuda_fail(e, "launch partition kernel (lookup)");
+    f->last_launches += 1;
+    for (uint32_t plo = 0; plo < pl.nparts; plo += per_launch) {
+      const uint32_t phi = std::min(pl.nparts, plo + per_launch);
+      ProbeArgs qa{f->words, records, idx, counts, plo, phi, cap, bitmap, l.flags};
+      uint32_t qgrid = 0;
+      if ((s = resolve_grid(qe->fn, f->device, l.block_threads, l.grid_ctas, (phi - plo) * cap, l.kpt, &qgrid)) !=
+          BF_OK)
+        return s;
+      void* qargs[] = {&qa};
+      if ((e = cudaLaunchKernel(qe->fn, dim3(qgrid), dim3(l.block_threads), qargs, 0, stream)) != cudaSuccess)
+        return cuda_fail(e, "launch record-probe kernel");
+      f->last_launches += 1;
+    }
+    ExpandArgs xa{bitmap, cnt, out + lo};
+    const uint64_t words = (cnt + 31) / 32;
+    const uint32_t xgrid = static_cast<uint32_t>(std::min<uint64_t>((words + 255) / 256, static_cast<uint64_t>(sms) * 8));
+    void* xargs[] = {&xa};
+    if ((e = cudaLaunchKernel(xe->fn, dim3(xgrid), dim3(256), xargs, 0, stream)) != cudaSuccess)
+      return cuda_fail(e, "launch bitmap expansion");
+    f->last_launches += 1;
+  }
+  return BF_OK;
+}
+
+bf_status run_contains(const bf_filter* f, const uint64_t* keys, uint64_t n, uint8_t* out, cudaStream_t stream) {
+  if (use_partitioned_lookup(f, n)) return launch_contains_partitioned(f, keys, n, out, stream);
+  return launch_sbf(f, BF_OP_CONTAINS, keys, n, out, stream);
 }
 
 bf_status run_add(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
@@ -425,7 +524,7 @@ bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n
   // kernels then stream the keys (and write the results) in place.
   if (device_can_access(f, h_keys) && (op == BF_OP_ADD || device_can_access(f, h_out))) {
     if (op == BF_OP_ADD) return run_add(f, h_keys, n, stream);
-    return launch_sbf(f, BF_OP_CONTAINS, h_keys, n, h_out, stream);
+    return run_contains(f, h_keys, n, h_out, stream);
   }
   bf_status s = ensure_pipeline(f);
   if (s != BF_OK) return s;
@@ -444,7 +543,7 @@ bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n
     uint8_t* d_out = reinterpret_cast<uint8_t*>(slot_base + keys_region(f->chunk_keys));
     if ((e = cudaMemcpyAsync(d_keys, h_keys + lo, cnt * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync H2D");
-    if ((s = op == BF_OP_ADD ? run_add(f, d_keys, cnt, st) : launch_sbf(f, op, d_keys, cnt, d_out, st)) != BF_OK)
+    if ((s = op == BF_OP_ADD ? run_add(f, d_keys, cnt, st) : run_contains(f, d_keys, cnt, d_out, st)) != BF_OK)
       return s;
     if (op == BF_OP_CONTAINS &&
         (e = cudaMemcpyAsync(h_out + lo, d_out, cnt, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -529,6 +628,7 @@ bf_status bf_destroy(bf_filter* f) {
   DeviceGuard g(f->device);
   release_pipeline(f);
   if (f->part_ws) cudaFree(f->part_ws);
+  if (f->look_ws) cudaFree(f->look_ws);
   if (f->owned && f->words) cudaFree(f->words);
   delete f;
   return BF_OK;
@@ -559,7 +659,7 @@ bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, ui
   if (reinterpret_cast<uintptr_t>(d_keys) % 8) return fail(BF_EINVAL, "keys must be 8-byte aligned");
   DeviceGuard g(f->device);
   const_cast<bf_filter*>(f)->last_launches = 0;
-  return launch_sbf(f, BF_OP_CONTAINS, d_keys, n, d_out, reinterpret_cast<cudaStream_t>(stream));
+  return run_contains(f, d_keys, n, d_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 bf_status bf_add_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, bf_stream_t stream) {
@@ -700,7 +800,9 @@ bf_status bf_set_partition(bf_filter* f, const bf_partition* cfg) {
   if (cfg->chunk_keys < 4096) return fail(BF_EINVAL, "chunk_keys must be >= 4096");
   if (cfg->cap_override % kRecTile) return fail(BF_EINVAL, "cap_override must be a multiple of 128");
   if (cfg->window_log2 < 16 || cfg->window_log2 > 36) return fail(BF_EINVAL, "window_log2 must be in [16, 36]");
-  if (cfg->reserved != 0) return fail(BF_EINVAL, "reserved must be 0");
+  if (cfg->lookup_mode > BF_PART_AUTO) return fail(BF_EINVAL, "lookup_mode must be BF_PART_OFF, BF_PART_ON or BF_PART_AUTO");
+  if (cfg->lookup_chunk_keys < 4096 || cfg->lookup_chunk_keys > (1ull << 32))
+    return fail(BF_EINVAL, "lookup_chunk_keys must be in [4096, 2^32]");
   f->part = *cfg;
   return BF_OK;
 }

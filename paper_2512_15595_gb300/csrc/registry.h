@@ -37,13 +37,15 @@ constexpr int kPartTile = kPartThreads * kPartKeysPerThread;  // keys per CTA ti
 constexpr int kMaxParts = 1024;
 constexpr uint64_t kRecTile = 128;  // slice buffer capacity granule: the largest record tile (32 x KPT)
 
-// dynamic shared memory of the partition kernel for `nparts` slices
-constexpr size_t partition_smem_bytes(int nparts) {
+// dynamic shared memory of the partition kernel for `nparts` slices (the
+// lookup flavour also keeps each record's query index)
+constexpr size_t partition_smem_bytes(int nparts, bool lookup = false) {
   return static_cast<size_t>(kPartTile) * 8        // records of the tile, sorted by slice
          + static_cast<size_t>(kPartTile) * 2      // slice of each sorted record
          + static_cast<size_t>(nparts) * 4 * 2     // per-slice count and start in the tile
          + static_cast<size_t>(nparts) * 8         // per-slice reserved global position
-         + 64 * 4;                                 // scan scratch (one entry per warp)
+         + 64 * 4                                  // scan scratch (one entry per warp)
+         + (lookup ? static_cast<size_t>(kPartTile) * 4 : 0);  // query index of each sorted record
 }
 
 // Arguments of the slice-partition kernel (L2-blocked construction).
@@ -58,7 +60,29 @@ struct PartArgs {
   uint64_t cap;                  // record slots per slice buffer (multiple of 128)
   unsigned long long* counts;    // [nparts] records reserved per slice (zeroed before launch)
   uint64_t* records;             // [nparts * cap] records (j << 32 | h_lo)
-  void* filter;                  // overflow records are inserted here directly
+  void* filter;                  // overflow records are inserted (or looked up) here directly
+  uint32_t* idx;                 // lookup: [nparts * cap] query index of each record
+  uint32_t* bitmap;              // lookup: one result bit per query (zeroed before launch)
+};
+
+// Arguments of the record-probe kernel (slice-partitioned lookup): records
+// of slices [part_lo, part_hi); a positive query sets its bit in `bitmap`.
+struct ProbeArgs {
+  const void* filter;
+  const uint64_t* records;
+  const uint32_t* idx;
+  const unsigned long long* counts;
+  uint32_t part_lo, part_hi;
+  uint64_t cap;
+  uint32_t* bitmap;
+  uint32_t flags;
+};
+
+// Arguments of the bitmap expansion: out[i] = bit i of `bitmap`, i < n.
+struct ExpandArgs {
+  const uint32_t* bitmap;
+  uint64_t n;
+  uint8_t* out;
 };
 
 // Arguments of the record-insert kernel.
@@ -75,7 +99,9 @@ struct RecArgs {
 };
 
 struct KernelEntry {
-  int op;  // 0 add, 1 contains, 2 add from slice records, 3 slice partition
+  // 0 add, 1 contains, 2 add from slice records, 3 slice partition (add),
+  // 4 probe slice records, 5 slice partition (lookup), 6 bitmap expansion
+  int op;
   int B, S, K, theta, phi, kpt;
   const void* fn;
 };
@@ -92,5 +118,6 @@ struct GupsEntry {
 BLOOMGB_GEOMETRIES(BLOOMGB_DECLARE)
 #undef BLOOMGB_DECLARE
 void register_gups(std::vector<GupsEntry>& v);
+void register_expand(std::vector<KernelEntry>& v);
 
 }  // namespace bloomgb

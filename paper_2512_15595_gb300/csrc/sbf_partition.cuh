@@ -38,7 +38,29 @@ __device__ __forceinline__ void insert_one(typename WordOf<S>::type* filter, uin
   });
 }
 
+// Look a record up with one thread (Theta = 1, Phi = s): the overflow path of
+// the lookup flavour of the partition kernel.
 template <int B, int S, int K>
+__device__ __forceinline__ bool lookup_one(const typename WordOf<S>::type* filter, uint64_t blk, uint32_t hlo,
+                                           uint64_t pol) {
+  using C = Cfg<B, S, K, 1, B / S, 1>;
+  using W = typename C::word_t;
+  W data[C::s];
+  ld_words<C::s>(filter + blk * C::s, pol, data);
+  W miss = 0;
+  static_for<C::s>([&](auto w) {
+    constexpr int Wd = decltype(w)::value;
+    W pat = 0;
+    static_for<C::kp>([&](auto t) { pat |= pattern_bit(hlo, salt_at<S>(Wd + C::s * decltype(t)::value)); });
+    miss |= pat & ~data[Wd];
+  });
+  return miss == 0;
+}
+
+// LOOKUP = false: construction records.  LOOKUP = true: lookup records, each
+// with the index of its query in `idx`; a query whose slice buffer is full is
+// answered on the spot (its result bit is set if it is found).
+template <int B, int S, int K, bool LOOKUP>
 __global__ void __launch_bounds__(kPartThreads, 3) sbf_partition_kernel(const PartArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* tile_rec = reinterpret_cast<uint64_t*>(smem);
@@ -47,6 +69,7 @@ __global__ void __launch_bounds__(kPartThreads, 3) sbf_partition_kernel(const Pa
   uint32_t* start = cnt + a.nparts;
   unsigned long long* gpos = reinterpret_cast<unsigned long long*>(start + a.nparts);
   uint32_t* warp_sum = reinterpret_cast<uint32_t*>(gpos + a.nparts);
+  uint32_t* tile_idx = warp_sum + 64;  // lookup only (kPartTile entries)
 
   using W = typename WordOf<S>::type;
   const uint64_t pol_keys = policy_evict_first();
@@ -123,6 +146,7 @@ __global__ void __launch_bounds__(kPartThreads, 3) sbf_partition_kernel(const Pa
         const uint32_t pos = start[part] + (pr[u] & 0xFFFu);
         tile_rec[pos] = rec[u];
         tile_part[pos] = static_cast<uint16_t>(part);
+        if constexpr (LOOKUP) tile_idx[pos] = static_cast<uint32_t>(base) + u * kPartThreads + tid;
       }
     }
     __syncthreads();
@@ -133,10 +157,21 @@ __global__ void __launch_bounds__(kPartThreads, 3) sbf_partition_kernel(const Pa
       const uint32_t p = tile_part[i];
       const uint64_t dst = gpos[p] + (i - start[p]);
       const uint64_t r = tile_rec[i];
-      if (dst < a.cap) {
-        a.records[static_cast<uint64_t>(p) * a.cap + dst] = r;
+      if constexpr (LOOKUP) {
+        const uint32_t q = tile_idx[i];
+        if (dst < a.cap) {
+          a.records[static_cast<uint64_t>(p) * a.cap + dst] = r;
+          a.idx[static_cast<uint64_t>(p) * a.cap + dst] = q;
+        } else if (lookup_one<B, S, K>(static_cast<const W*>(a.filter), r >> 32, static_cast<uint32_t>(r),
+                                       pol_filter)) {
+          atomicOr(a.bitmap + (q >> 5), 1u << (q & 31u));
+        }
       } else {
-        insert_one<B, S, K>(static_cast<W*>(a.filter), r >> 32, static_cast<uint32_t>(r), pol_filter);
+        if (dst < a.cap) {
+          a.records[static_cast<uint64_t>(p) * a.cap + dst] = r;
+        } else {
+          insert_one<B, S, K>(static_cast<W*>(a.filter), r >> 32, static_cast<uint32_t>(r), pol_filter);
+        }
       }
     }
     __syncthreads();
@@ -190,6 +225,77 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_add_records_kernel(const
 #pragma unroll
           for (int q = 0; q < STEPS; ++q) red_lane_words<C>(bp + q * C::chunk, salts, hm, q, pol_filter);
         }
+      }
+    }
+  }
+}
+
+// Probe the records of slices [part_lo, part_hi) (lookup, slice-partitioned):
+// the same cooperative-group test as sbf_contains_kernel, on records (no
+// hashing) whose block lies in an L2-resident window of the filter; the
+// owning lane of a found query sets the query's bit in the result bitmap
+// (the bitmap starts zeroed, so only positives write).
+template <class C>
+__global__ void __launch_bounds__(kMaxBlockThreads) sbf_probe_records_kernel(const ProbeArgs a) {
+  using W = typename C::word_t;
+  constexpr int KPT = C::KPT, THETA = C::THETA, PHI = C::PHI, STEPS = C::steps;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t r = lane & (THETA - 1);
+  const uint32_t g0 = lane - r;
+  const LaneSalts<C> salts(r);
+  const uint64_t pol_rec = policy_evict_first();
+  const uint64_t pol_filter = (a.flags & kHintFilterEvictLast) ? policy_evict_last() : policy_evict_normal();
+  const W* __restrict__ filter = static_cast<const W*>(a.filter);
+  constexpr uint64_t kTile = 32u * KPT;
+  const uint64_t first_tile = static_cast<uint64_t>(a.part_lo) * a.cap / kTile;
+  const uint64_t ntiles = static_cast<uint64_t>(a.part_hi) * a.cap / kTile;
+  const uint64_t warps_per_cta = blockDim.x >> 5;
+  const uint64_t nwarps = static_cast<uint64_t>(gridDim.x) * warps_per_cta;
+
+  for (uint64_t tile = first_tile + blockIdx.x * warps_per_cta + (threadIdx.x >> 5); tile < ntiles;
+       tile += nwarps) {
+    const uint64_t v0 = tile * kTile;
+    const uint64_t p = v0 / a.cap;
+    const uint64_t slot0 = v0 - p * a.cap;
+    const uint64_t count = a.counts[p];
+    if (slot0 >= count) continue;  // warp-uniform
+    const uint64_t base = slot0 + static_cast<uint64_t>(lane) * KPT;
+    const uint64_t lim = count < a.cap ? count : a.cap;
+    uint64_t rec[KPT];
+    const uint32_t valid = load_keys<KPT>(a.records + p * a.cap, lim, base, true, pol_rec, rec);
+    uint32_t q[KPT];
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) q[u] = ((valid >> u) & 1u) ? a.idx[p * a.cap + base + u] : 0u;
+    W data[KPT][THETA][STEPS][PHI];
+    uint32_t hk[KPT][THETA];
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+#pragma unroll
+      for (int m = 0; m < THETA; ++m) {
+        uint64_t rm = ((valid >> u) & 1u) ? rec[u] : 0ull;  // invalid slots read block 0
+        if constexpr (THETA > 1) rm = __shfl_sync(kFullMask, rm, m, THETA);
+        hk[u][m] = static_cast<uint32_t>(rm);
+        const W* bp = filter + (rm >> 32) * C::s + r * PHI;
+#pragma unroll
+        for (int qq = 0; qq < STEPS; ++qq) ld_words<PHI>(bp + qq * C::chunk, pol_filter, data[u][m][qq]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+#pragma unroll
+      for (int m = 0; m < THETA; ++m) {
+        W miss = 0;
+#pragma unroll
+        for (int qq = 0; qq < STEPS; ++qq) {
+#pragma unroll
+          for (int pp = 0; pp < PHI; ++pp) miss |= salts.pattern(hk[u][m], qq, pp) & ~data[u][m][qq][pp];
+        }
+        bool ok = (miss == 0);
+        if constexpr (THETA > 1) {
+          const uint32_t seg = (__ballot_sync(kFullMask, ok) >> g0) & ((1u << THETA) - 1u);
+          ok = (seg == (1u << THETA) - 1u) && (r == static_cast<uint32_t>(m));
+        }
+        if (ok && ((valid >> u) & 1u)) atomicOr(a.bitmap + (q[u] >> 5), 1u << (q[u] & 31u));
       }
     }
   }

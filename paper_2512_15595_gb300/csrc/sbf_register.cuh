@@ -33,10 +33,12 @@ void register_k(std::vector<KernelEntry>& v) {
         v.push_back({0, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_add_kernel<C>)});
         v.push_back({1, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_contains_kernel<C>)});
         v.push_back({2, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_add_records_kernel<C>)});
+        v.push_back({4, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_probe_records_kernel<C>)});
       });
     });
   });
-  v.push_back({3, B, S, K, 0, 0, 0, reinterpret_cast<const void*>(&sbf_partition_kernel<B, S, K>)});
+  v.push_back({3, B, S, K, 0, 0, 0, reinterpret_cast<const void*>(&sbf_partition_kernel<B, S, K, false>)});
+  v.push_back({5, B, S, K, 0, 0, 0, reinterpret_cast<const void*>(&sbf_partition_kernel<B, S, K, true>)});
 }
 
 template <int B, int S>

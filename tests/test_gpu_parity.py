@@ -276,6 +276,43 @@ def test_partitioned_add_skewed_keys(torch):
     f.close()
 
 
+@pytest.mark.parametrize("B,S,k", [(256, 32, 8), (512, 64, 16), (64, 64, 4), (128, 32, 16), (1024, 64, 16)])
+def test_partitioned_lookup_bit_exact(torch, B, S, k):
+    from paper_2512_15595_gb300 import BF_OP_CONTAINS, valid_layouts
+    geom = oracle.Geometry(num_blocks=(1 << 14) + 77, block_bits=B, word_bits=S, k=k, seed=321)
+    ins = synthkeys.insert_keys(150_001, seed=83)
+    q, is_mem = synthkeys.mixed_queries(150_001, 30_000, 70_013, seed_insert=83)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    ref_out = ref.contains(q)
+    dk, dq = dev_keys(torch, ins), dev_keys(torch, q)
+    out_buf = torch.zeros(q.size + 1, dtype=torch.uint8, device="cuda")
+    cases = [dict(slice_log2=16), dict(slice_log2=17, lookup_chunk_keys=4096 * 3 + 1),
+             dict(slice_log2=16, cap_override=128), dict(slice_log2=16, window_log2=17)]
+    f = gpu_filter(geom, torch)
+    f.set_partition(mode=0)
+    f.add(dk)
+    assert np.array_equal(words_np(f), ref.as_bytes())
+    for cfg in cases:
+        nparts = -(-geom.nbytes // (1 << cfg["slice_log2"]))
+        per_launch = 1 << max(0, cfg.get("window_log2", 26) - cfg["slice_log2"])
+        per_pass = 2 + -(-nparts // per_launch)
+        passes = -(-q.size // cfg.get("lookup_chunk_keys", 1 << 28))
+        for cg, phi in valid_layouts(B, S)[:: max(1, len(valid_layouts(B, S)) // 4)]:
+            for kpt, offset in ((1, 0), (4, 1)):
+                f.set_partition(mode=0, lookup_mode=1, window_log2=26, cap_override=0, lookup_chunk_keys=1 << 28)
+                f.set_partition(**cfg)
+                f.set_layout(BF_OP_CONTAINS, cg=cg, phi=phi, kpt=kpt)
+                out = out_buf[offset:offset + q.size]
+                out.zero_()
+                f.contains(dq, out=out)
+                assert f.last_launches() == per_pass * passes, (cfg, f.last_launches())
+                got = out.cpu().numpy()
+                assert np.array_equal(got, ref_out), (cfg, cg, phi, kpt)
+                assert got[is_mem == 1].all()
+    f.close()
+
+
 def test_partition_auto_and_off(torch):
     from paper_2512_15595_gb300 import _lib
     geom = oracle.Geometry(num_blocks=1 << 12, block_bits=256, word_bits=32, k=8, seed=0)

@@ -40,7 +40,7 @@ def test_noalloc_matches_bf_add_on_two_calls(env, num_blocks, B, S, k):
     h = L.bf_create(p, ref.data_ptr())
     try:
         # the regular path, forced to its partitioned construction
-        L.bf_set_partition(h, L.bf_partition(L.BF_PART_ON, 24, 1 << 32, 0, 26, 0))
+        L.bf_set_partition(h, L.bf_partition(L.BF_PART_ON, 24, 1 << 32, 0, 26, L.BF_PART_AUTO, 1 << 28))
         stream = torch.cuda.current_stream().cuda_stream
         limit = ctypes.c_uint64()
         for call, (seed, n) in enumerate([(101, 1_000_003), (102, 777_777)]):
