@@ -214,22 +214,26 @@ def run_reference(args, w, wname):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+KERNEL_SOURCES = ("sbf_kernels.cuh", "sbf_device.cuh", "salts.cuh", "sbf_partition.cuh", "sbf_expand.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("sbf_kernels.cuh", "sbf_device.cuh", "salts.cuh"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2512_15595_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str, wname: str):
-    """Per-launch DRAM bytes from the committed ncu summary, if it is current."""
+def measured_traffic(op: str, wname: str):
+    """DRAM bytes of one call of `op` from the committed ncu summary, if the
+    kernel sources have not changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         t = json.load(f)
-    e = t.get(f"{kernel}/{wname}")
+    e = t.get(f"{op}/{wname}")
     if not e or e.get("kernel_source_hash") != kernel_source_hash():
         return None
     return e.get("dram_bytes_per_launch")
@@ -332,16 +336,18 @@ def run_ours(args, w, wname):
     bounds = gups_bounds(torch, w, ins, qd, device) if not args.no_gups else None
 
     launches = []
+    launches_add, launches_con = [], []
 
     def step(ev=None):
         if ev:
             ev[0].record(stream)
         f.add(ins)
-        n_add_launch = f.last_launches()
+        launches_add.append(f.last_launches())
         if ev:
             ev[1].record(stream)
         f.contains(qd, out=out)
-        launches.append(n_add_launch + f.last_launches())
+        launches_con.append(f.last_launches())
+        launches.append(launches_add[-1] + launches_con[-1])
         if ev:
             ev[2].record(stream)
 
@@ -379,7 +385,10 @@ def run_ours(args, w, wname):
     missed = int((out[flags == 1] == 0).sum().item())
     realized_fpr = popcount_fpr(torch, f.words, w)
 
-    # roofline of the dominant kernel (construction: one random sector RMW per key)
+    # roofline of the dominant operation, per call (one call = one launch of
+    # the direct kernel, or the partition + windowed kernels of the
+    # slice-partitioned path); algorithmic bytes per key: key + random sector
+    # read-modify-write (construction) or key + sector read + result (lookup)
     sectors = max(1, w["block_bits"] // 256)
     bytes_add = 8 + 2 * 32 * sectors
     bytes_con = 8 + 32 * sectors + 1
@@ -389,9 +398,17 @@ def run_ours(args, w, wname):
     n_dom = n_ins if dominant == "add" else n_q
     achieved = per_key * n_dom / (dur * 1e-3) / 1e9
     peak, peak_kind = peaks()
+    part = f.partition()
+    if dominant == "add":
+        desc = ("bf_add: sbf_partition_kernel + sbf_add_records_kernel (windowed)" if launches_add[-1] > 1
+                else "bf_add: sbf_add_kernel")
+    else:
+        desc = ("bf_contains: sbf_partition_kernel + sbf_probe_records_kernel + bitmap_expand_kernel"
+                if launches_con[-1] > 1 else "bf_contains: sbf_contains_kernel")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": measured_traffic(f"sbf_{dominant}_kernel", wname), "kernel": f"sbf_{dominant}_kernel",
-            "peak_source": f"{peak_kind} HBM copy bandwidth", "algorithmic_bytes_per_key": per_key}
+            "traffic": measured_traffic(dominant, wname), "kernel": desc, "per": "one call",
+            "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)",
+            "algorithmic_bytes_per_key": per_key, "keys_per_call": n_dom, "ms_per_call": dur}
     ra = None
     if bounds:
         ra = {"lookup_bound_gkeys_s": bounds["load"]["gkeys_s"], "insert_bound_gkeys_s": bounds["red_or"]["gkeys_s"],
