@@ -236,6 +236,35 @@ bf_status bf_gups(int mode, void* d_table, uint64_t table_bytes, uint32_t unit_b
                   const uint64_t* d_keys, uint64_t n, uint8_t* d_out, const bf_layout* layout,
                   bf_stream_t stream);
 
+/* Batched filters (SURVEY-level extension of the paper's bulk operations to
+   many independent filters): one launch builds, or probes, every filter of
+   a batch.  All filters share params->block_bits / word_bits / k / seed
+   (params->num_blocks is ignored); each has its own bit array and its own
+   run [key_offset, key_offset + key_count) of one key array, and lookup
+   results use the same indexing in one result array.  Per filter the bits
+   and answers are exactly those of bf_add / bf_contains on that filter
+   (Sec. II-A).  bf_batch_create copies the descriptors to the device (a
+   blocking copy) and resolves kernels and grids; bf_batch_add /
+   bf_batch_contains then only enqueue one kernel each, so they can be
+   captured into a CUDA graph and replayed.  Filters may share bit arrays or
+   key runs (ORs commute); filters with key_count = 0 are skipped. */
+typedef struct bf_batch bf_batch;
+typedef struct {
+    void* d_words;         /* num_blocks * block_bits / 8 bytes, aligned to max(32, block_bits/8) */
+    uint64_t num_blocks;
+    uint64_t key_offset;
+    uint64_t key_count;
+} bf_batch_filter;
+bf_status bf_batch_create(const bf_params* params, const bf_batch_filter* h_filters, uint32_t nfilters,
+                          bf_batch** out);
+bf_status bf_batch_destroy(bf_batch* b);
+bf_status bf_batch_set_layout(bf_batch* b, int op, const bf_layout* layout);
+bf_status bf_batch_get_layout(const bf_batch* b, int op, bf_layout* out);
+bf_status bf_batch_add(bf_batch* b, const uint64_t* d_keys, bf_stream_t stream);
+bf_status bf_batch_contains(const bf_batch* b, const uint64_t* d_keys, uint8_t* d_out, bf_stream_t stream);
+/* Number of filters, and the length the key / result arrays must have. */
+bf_status bf_batch_info(const bf_batch* b, uint32_t* nfilters, uint64_t* total_keys);
+
 /* Construction that allocates nothing (the paper has no counterpart: this is
    an interface for callers of this library).  Some callers cannot let a
    library call cudaMalloc -- services whose own caching allocator owns the

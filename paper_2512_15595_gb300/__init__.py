@@ -13,7 +13,7 @@ from ._lib import (BF_GUPS_LOAD, BF_GUPS_RED_OR, BF_HINT_FILTER_EVICT_LAST, BF_H
 
 __all__ = ["Filter", "BloomError", "bf_params", "bf_layout", "BF_OP_ADD", "BF_OP_CONTAINS",
            "BF_HINT_FILTER_EVICT_LAST", "BF_HINT_KEYS_EVICT_NORMAL", "BF_GUPS_LOAD", "BF_GUPS_RED_OR",
-           "valid_layouts", "device_tensor"]
+           "valid_layouts", "device_tensor", "Batch"]
 
 
 def valid_layouts(block_bits: int, word_bits: int):
@@ -128,6 +128,57 @@ class Filter:
     def close(self) -> None:
         if getattr(self, "handle", None):
             _lib.bf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many filters of one geometry built / probed by one launch per operation.
+
+    ``filters``: list of (words_tensor, num_blocks, key_offset, key_count);
+    every words tensor is a contiguous CUDA byte buffer of num_blocks*B/8
+    bytes (slices of one arena are fine).  Keys and results are single arrays
+    indexed by each filter's key run.
+    """
+
+    def __init__(self, filters, block_bits: int = 256, word_bits: int = 32, k: int = 8, seed: int = 0):
+        self.params = bf_params(1, block_bits, word_bits, k, 0, seed)
+        self._keep = [f[0] for f in filters]
+        descs = [(f[0].data_ptr(), f[1], f[2], f[3]) for f in filters]
+        self.handle = _lib.bf_batch_create(self.params, descs)
+        self.nfilters, self.total_keys = _lib.bf_batch_info(self.handle)
+
+    def add(self, keys, stream=None) -> None:
+        ptr, n = _key_ptr(keys)
+        if n < self.total_keys:
+            raise ValueError("key array shorter than the batch's key runs")
+        _lib.bf_batch_add(self.handle, ptr, stream)
+
+    def contains(self, keys, out=None, stream=None):
+        import torch
+        ptr, n = _key_ptr(keys)
+        if n < self.total_keys:
+            raise ValueError("key array shorter than the batch's key runs")
+        if out is None:
+            out = torch.zeros(n, dtype=torch.bool, device=keys.device)
+        _lib.bf_batch_contains(self.handle, ptr, out.data_ptr(), stream)
+        return out
+
+    def set_layout(self, op: int, cg: int = 0, phi: int = 0, kpt: int = 0, block_threads: int = 0,
+                   grid_ctas: int = 0, flags: int = 0) -> None:
+        _lib.bf_batch_set_layout(self.handle, op, bf_layout(cg, phi, kpt, block_threads, grid_ctas, flags))
+
+    def layout(self, op: int) -> dict:
+        return _lib.bf_batch_get_layout(self.handle, op).as_dict()
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            _lib.bf_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

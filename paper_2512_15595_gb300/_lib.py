@@ -25,8 +25,9 @@ EXPORTED = (
     "bf_params_check", "bf_layout_check", "bf_create", "bf_destroy", "bf_clear", "bf_add",
     "bf_contains", "bf_add_host", "bf_contains_host", "bf_set_staging", "bf_words",
     "bf_get_params", "bf_set_layout", "bf_get_layout", "bf_set_l2_persist", "bf_gups",
-    "bf_set_partition", "bf_get_partition", "bf_last_launches", "bf_add_noalloc", "bf_status_str",
-    "bf_last_error", "bf_version",
+    "bf_set_partition", "bf_get_partition", "bf_last_launches", "bf_add_noalloc", "bf_batch_create",
+    "bf_batch_destroy", "bf_batch_set_layout", "bf_batch_get_layout", "bf_batch_add", "bf_batch_contains",
+    "bf_batch_info", "bf_status_str", "bf_last_error", "bf_version",
 )
 
 
@@ -56,6 +57,11 @@ class bf_partition(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class bf_batch_filter(ctypes.Structure):
+    _fields_ = [("d_words", ctypes.c_void_p), ("num_blocks", ctypes.c_uint64),
+                ("key_offset", ctypes.c_uint64), ("key_count", ctypes.c_uint64)]
 
 
 class bf_layout(ctypes.Structure):
@@ -101,6 +107,13 @@ def lib():
         "bf_get_partition": (i32, [vp, ctypes.POINTER(bf_partition)]),
         "bf_last_launches": (i32, [vp, ctypes.POINTER(u32)]),
         "bf_add_noalloc": (i32, [P, vp, vp, u64, ctypes.POINTER(u64), vp]),
+        "bf_batch_create": (i32, [P, ctypes.POINTER(bf_batch_filter), u32, ctypes.POINTER(vp)]),
+        "bf_batch_destroy": (i32, [vp]),
+        "bf_batch_set_layout": (i32, [vp, i32, LY]),
+        "bf_batch_get_layout": (i32, [vp, i32, LY]),
+        "bf_batch_add": (i32, [vp, vp, vp]),
+        "bf_batch_contains": (i32, [vp, vp, vp, vp]),
+        "bf_batch_info": (i32, [vp, ctypes.POINTER(u32), ctypes.POINTER(u64)]),
         "bf_status_str": (ctypes.c_char_p, [i32]),
         "bf_last_error": (ctypes.c_char_p, []),
         "bf_version": (ctypes.c_char_p, []),
@@ -230,3 +243,40 @@ def bf_last_error() -> str:
 
 def bf_version() -> str:
     return lib().bf_version().decode()
+
+
+def bf_batch_create(p: bf_params, filters) -> int:
+    """filters: sequence of bf_batch_filter (or (d_words, num_blocks, key_offset, key_count))."""
+    arr = (bf_batch_filter * len(filters))(*[f if isinstance(f, bf_batch_filter) else bf_batch_filter(*f)
+                                              for f in filters])
+    h = ctypes.c_void_p()
+    _check(lib().bf_batch_create(ctypes.byref(p), arr, len(filters), ctypes.byref(h)), "bf_batch_create")
+    return h.value
+
+
+def bf_batch_destroy(b: int) -> None:
+    _check(lib().bf_batch_destroy(b), "bf_batch_destroy")
+
+
+def bf_batch_set_layout(b: int, op: int, layout: bf_layout) -> None:
+    _check(lib().bf_batch_set_layout(b, op, ctypes.byref(layout)), "bf_batch_set_layout")
+
+
+def bf_batch_get_layout(b: int, op: int) -> bf_layout:
+    out = bf_layout()
+    _check(lib().bf_batch_get_layout(b, op, ctypes.byref(out)), "bf_batch_get_layout")
+    return out
+
+
+def bf_batch_add(b: int, d_keys: int, stream=None) -> None:
+    _check(lib().bf_batch_add(b, d_keys, _stream(stream)), "bf_batch_add")
+
+
+def bf_batch_contains(b: int, d_keys: int, d_out: int, stream=None) -> None:
+    _check(lib().bf_batch_contains(b, d_keys, d_out, _stream(stream)), "bf_batch_contains")
+
+
+def bf_batch_info(b: int) -> tuple[int, int]:
+    n, k = ctypes.c_uint32(), ctypes.c_uint64()
+    _check(lib().bf_batch_info(b, ctypes.byref(n), ctypes.byref(k)), "bf_batch_info")
+    return n.value, k.value

@@ -964,3 +964,153 @@ extern "C" bf_status bf_add_noalloc(const bf_params* params, void* d_words, cons
   }
   return BF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched filters: many filters of one geometry in one launch per operation
+// ---------------------------------------------------------------------------
+struct bf_batch {
+  bf_params p{};
+  uint32_t nfilters = 0;
+  uint64_t total_chunks = 0;
+  uint64_t total_keys = 0;  // keys the batch's key array must hold
+  BatchFilter* d_filters = nullptr;
+  uint64_t* d_chunk_begin = nullptr;
+  int device = 0;
+  bf_layout layout[2]{};
+  const KernelEntry* entry[2]{};
+  uint32_t grid[2]{};
+};
+
+namespace {
+
+// Resolve a batched operation's kernel and its grid (done when the layout is
+// set, so that the add / contains calls only launch: capturable in a graph).
+bf_status batch_resolve(bf_batch* b, int op, const bf_layout* in) {
+  bf_layout l{};
+  bf_status s = resolve_layout(b->p, op, in, &l, nullptr);
+  if (s != BF_OK) return s;
+  if (32u * l.kpt > kBatchChunk) return fail(BF_EINVAL, "kpt too large for the batch chunk");
+  const KernelEntry* e = find_op(op == BF_OP_ADD ? 7 : 8, b->p, l.cg, l.phi, l.kpt);
+  if (!e) return fail(BF_EUNSUPPORTED, "no batched kernel for this geometry and layout");
+  uint32_t grid = 0;
+  if (b->total_chunks) {
+    s = resolve_grid(e->fn, b->device, l.block_threads, l.grid_ctas, b->total_chunks * 32, 1, &grid);
+    if (s != BF_OK) return s;
+  }
+  b->layout[op] = l;
+  b->entry[op] = e;
+  b->grid[op] = grid;
+  return BF_OK;
+}
+
+bf_status batch_launch(const bf_batch* b, int op, const uint64_t* keys, uint8_t* out, cudaStream_t stream) {
+  if (b->total_chunks == 0) return BF_OK;
+  BatchArgs a{b->d_filters, b->d_chunk_begin, b->nfilters, b->total_chunks, keys, out,
+              b->p.seed + 0x27D4EB2F165667C5ull + 8ull, b->layout[op].flags};
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchKernel(b->entry[op]->fn, dim3(b->grid[op]), dim3(b->layout[op].block_threads), args, 0,
+                                   stream);
+  return e == cudaSuccess ? BF_OK : cuda_fail(e, "launch batched kernel");
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_batch_create(const bf_params* params, const bf_batch_filter* filters, uint32_t nfilters,
+                          bf_batch** out) {
+  if (!out) return fail(BF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!params || (!filters && nfilters)) return fail(BF_EINVAL, "NULL argument");
+  bf_params p = *params;
+  p.num_blocks = 1;  // per filter
+  bf_status s = bf_params_check(&p);
+  if (s != BF_OK) return s;
+  const uint64_t align = std::max<uint64_t>(32, p.block_bits / 8);
+  std::vector<BatchFilter> hf(nfilters);
+  std::vector<uint64_t> begin(static_cast<size_t>(nfilters) + 1, 0);
+  uint64_t total_keys = 0;
+  for (uint32_t i = 0; i < nfilters; ++i) {
+    const bf_batch_filter& f = filters[i];
+    if (!f.d_words || reinterpret_cast<uintptr_t>(f.d_words) % align)
+      return fail(BF_EINVAL, "every filter's bit array must be non-NULL and aligned to max(32, block_bits/8)");
+    if (f.num_blocks == 0 || f.num_blocks > (~0ull) / 128) return fail(BF_EINVAL, "bad num_blocks in a filter");
+    if (f.key_offset > (~0ull) - f.key_count) return fail(BF_EINVAL, "key range overflows");
+    hf[i] = BatchFilter{f.d_words, f.num_blocks, f.key_offset, f.key_count};
+    begin[i + 1] = begin[i] + (f.key_count + kBatchChunk - 1) / kBatchChunk;
+    total_keys = std::max(total_keys, f.key_offset + f.key_count);
+  }
+  bf_batch* b = new (std::nothrow) bf_batch();
+  if (!b) return fail(BF_ENOMEM, "host allocation failed");
+  b->p = p;
+  b->nfilters = nfilters;
+  b->total_chunks = begin[nfilters];
+  b->total_keys = total_keys;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess && nfilters) e = cudaMalloc(&b->d_filters, sizeof(BatchFilter) * nfilters);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_chunk_begin, sizeof(uint64_t) * (nfilters + 1));
+  if (e == cudaSuccess && nfilters)
+    e = cudaMemcpy(b->d_filters, hf.data(), sizeof(BatchFilter) * nfilters, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_chunk_begin, begin.data(), sizeof(uint64_t) * (nfilters + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    bf_batch_destroy(b);
+    return fail(BF_ENOMEM, "device allocation for the batch failed");
+  }
+  for (int op = 0; op < 2; ++op) {
+    if ((s = batch_resolve(b, op, nullptr)) != BF_OK) {
+      bf_batch_destroy(b);
+      return s;
+    }
+  }
+  *out = b;
+  return BF_OK;
+}
+
+bf_status bf_batch_destroy(bf_batch* b) {
+  if (!b) return fail(BF_EINVAL, "batch is NULL");
+  DeviceGuard g(b->device);
+  if (b->d_filters) cudaFree(b->d_filters);
+  if (b->d_chunk_begin) cudaFree(b->d_chunk_begin);
+  delete b;
+  return BF_OK;
+}
+
+bf_status bf_batch_set_layout(bf_batch* b, int op, const bf_layout* layout) {
+  if (!b) return fail(BF_EINVAL, "batch is NULL");
+  DeviceGuard g(b->device);
+  return batch_resolve(b, op, layout);
+}
+
+bf_status bf_batch_get_layout(const bf_batch* b, int op, bf_layout* out) {
+  if (!b || !out) return fail(BF_EINVAL, "NULL argument");
+  if (op != BF_OP_ADD && op != BF_OP_CONTAINS) return fail(BF_EINVAL, "bad op");
+  *out = b->layout[op];
+  return BF_OK;
+}
+
+bf_status bf_batch_add(bf_batch* b, const uint64_t* d_keys, bf_stream_t stream) {
+  if (!b) return fail(BF_EINVAL, "batch is NULL");
+  if (b->total_chunks && (!d_keys || reinterpret_cast<uintptr_t>(d_keys) % 8))
+    return fail(BF_EINVAL, "keys must be non-NULL and 8-byte aligned");
+  DeviceGuard g(b->device);
+  return batch_launch(b, BF_OP_ADD, d_keys, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+bf_status bf_batch_contains(const bf_batch* b, const uint64_t* d_keys, uint8_t* d_out, bf_stream_t stream) {
+  if (!b) return fail(BF_EINVAL, "batch is NULL");
+  if (b->total_chunks && (!d_keys || !d_out || reinterpret_cast<uintptr_t>(d_keys) % 8))
+    return fail(BF_EINVAL, "keys (8-byte aligned) and out must be non-NULL");
+  DeviceGuard g(b->device);
+  return batch_launch(b, BF_OP_CONTAINS, d_keys, d_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+bf_status bf_batch_info(const bf_batch* b, uint32_t* nfilters, uint64_t* total_keys) {
+  if (!b) return fail(BF_EINVAL, "batch is NULL");
+  if (nfilters) *nfilters = b->nfilters;
+  if (total_keys) *total_keys = b->total_keys;
+  return BF_OK;
+}
+
+}  // extern "C"

@@ -98,9 +98,34 @@ struct RecArgs {
   uint32_t flags;
 };
 
+// One filter of a batch: its bit array and its run of the batch's keys.
+struct BatchFilter {
+  void* words;          // b*B/8 bytes
+  uint64_t nblocks;     // b
+  uint64_t key_offset;  // first key of this filter in the batch's key array
+  uint64_t key_count;
+};
+
+// Batched construction / lookup over many filters in one launch.  The keys
+// of all filters are cut into work chunks of kBatchChunk keys that never
+// straddle two filters; chunk_begin[f] is the first chunk of filter f
+// (nfilters + 1 entries).
+constexpr uint64_t kBatchChunk = 128;
+struct BatchArgs {
+  const BatchFilter* filters;
+  const uint64_t* chunk_begin;
+  uint32_t nfilters;
+  uint64_t total_chunks;
+  const uint64_t* keys;
+  uint8_t* out;         // lookup results, same indexing as keys
+  uint64_t acc0;
+  uint32_t flags;
+};
+
 struct KernelEntry {
   // 0 add, 1 contains, 2 add from slice records, 3 slice partition (add),
-  // 4 probe slice records, 5 slice partition (lookup), 6 bitmap expansion
+  // 4 probe slice records, 5 slice partition (lookup), 6 bitmap expansion,
+  // 7 batched add, 8 batched contains
   int op;
   int B, S, K, theta, phi, kpt;
   const void* fn;

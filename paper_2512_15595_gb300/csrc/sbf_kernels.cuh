@@ -40,6 +40,9 @@ struct Cfg {
 };
 
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
+
+template <class C>
+using W_of = typename C::word_t;
 // CTA size bound the kernels are compiled for (leaves up to 128 registers per thread)
 constexpr int kMaxBlockThreads = 512;
 
@@ -111,143 +114,162 @@ __device__ __forceinline__ uint32_t load_keys(const uint64_t* keys, uint64_t n, 
   return valid;
 }
 
+// Everything a tile needs that does not change from tile to tile.
 template <class C>
-__global__ void __launch_bounds__(kMaxBlockThreads) sbf_contains_kernel(const SbfArgs a) {
+struct TileCtx {
+  LaneSalts<C> salts;
+  uint32_t lane, r, g0;
+  uint64_t pol_keys, pol_filter;
+  __device__ __forceinline__ TileCtx(uint32_t flags)
+      : salts(threadIdx.x & (C::THETA - 1)),
+        lane(threadIdx.x & 31u),
+        r(threadIdx.x & (C::THETA - 1)),
+        g0((threadIdx.x & 31u) - (threadIdx.x & (C::THETA - 1))),
+        pol_keys((flags & kHintKeysEvictNormal) ? policy_evict_normal() : policy_evict_first()),
+        pol_filter((flags & kHintFilterEvictLast) ? policy_evict_last() : policy_evict_normal()) {}
+};
+
+// Lookup of the warp's tile of 32*KPT keys starting at key `tile_base`
+// (lane L owns keys tile_base + L*KPT + [0, KPT)); warp-uniform call.
+template <class C>
+__device__ __forceinline__ void contains_tile(const TileCtx<C>& t, const typename C::word_t* __restrict__ filter,
+                                              uint64_t nblocks, int block_mode, const uint64_t* keys, uint64_t n,
+                                              uint8_t* out, uint64_t acc0, bool vec_ok, uint64_t tile_base) {
   using W = typename C::word_t;
   constexpr int KPT = C::KPT, THETA = C::THETA, PHI = C::PHI, STEPS = C::steps;
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t r = lane & (THETA - 1);
-  const uint32_t g0 = lane - r;
-  const LaneSalts<C> salts(r);
-  const uint64_t pol_keys = (a.flags & kHintKeysEvictNormal) ? policy_evict_normal() : policy_evict_first();
-  const uint64_t pol_filter = (a.flags & kHintFilterEvictLast) ? policy_evict_last() : policy_evict_normal();
-  const W* __restrict__ filter = static_cast<const W*>(a.filter);
-  constexpr uint64_t kTile = 32u * KPT;
-  const uint64_t ntiles = (a.n + kTile - 1) / kTile;
-  const uint64_t warps_per_cta = blockDim.x >> 5;
-  const uint64_t nwarps = static_cast<uint64_t>(gridDim.x) * warps_per_cta;
-  const bool vec_ok = (reinterpret_cast<uintptr_t>(a.keys) % (8u * KPT) == 0) &&
-                      (reinterpret_cast<uintptr_t>(a.out) % KPT == 0);
+  const uint64_t base = tile_base + static_cast<uint64_t>(t.lane) * KPT;
+  uint64_t key[KPT];
+  const uint32_t valid = load_keys<KPT>(keys, n, base, vec_ok, t.pol_keys, key);
+  uint32_t hlo[KPT];
+  uint64_t blk[KPT];
+#pragma unroll
+  for (int u = 0; u < KPT; ++u) {
+    const uint64_t h = xxh64_key(key[u], acc0);
+    hlo[u] = static_cast<uint32_t>(h);
+    // invalid (tail) keys read block 0, which always exists; their result is dropped
+    blk[u] = ((valid >> u) & 1u) ? block_of(h, nblocks, block_mode) : 0;
+  }
+  // phase 1: issue every load of the tile before any test (memory-level parallelism)
+  W data[KPT][THETA][STEPS][PHI];
+  uint32_t hk[KPT][THETA];
+#pragma unroll
+  for (int u = 0; u < KPT; ++u) {
+#pragma unroll
+    for (int m = 0; m < THETA; ++m) {
+      uint64_t bm = blk[u];
+      uint32_t hm = hlo[u];
+      if constexpr (THETA > 1) {
+        bm = __shfl_sync(kFullMask, bm, m, THETA);
+        hm = __shfl_sync(kFullMask, hm, m, THETA);
+      }
+      hk[u][m] = hm;
+      const W* bp = filter + bm * C::s + t.r * PHI;
+#pragma unroll
+      for (int q = 0; q < STEPS; ++q) ld_words<PHI>(bp + q * C::chunk, t.pol_filter, data[u][m][q]);
+    }
+  }
+  // phase 2: test every word against its pattern; AND across the CG
+  uint32_t res = 0;
+#pragma unroll
+  for (int u = 0; u < KPT; ++u) {
+#pragma unroll
+    for (int m = 0; m < THETA; ++m) {
+      W miss = 0;
+#pragma unroll
+      for (int q = 0; q < STEPS; ++q) {
+#pragma unroll
+        for (int p = 0; p < PHI; ++p) {
+          const W pat = t.salts.pattern(hk[u][m], q, p);
+          miss |= pat & ~data[u][m][q][p];
+        }
+      }
+      bool ok = (miss == 0);
+      if constexpr (THETA > 1) {
+        const uint32_t seg = (__ballot_sync(kFullMask, ok) >> t.g0) & ((1u << THETA) - 1u);
+        ok = (seg == (1u << THETA) - 1u);
+        ok = ok && (t.r == static_cast<uint32_t>(m));
+      }
+      res |= static_cast<uint32_t>(ok) << u;
+    }
+  }
+  // coalesced write-back of the lane's own results
+  if (vec_ok && valid == (1u << KPT) - 1u) {
+    if constexpr (KPT == 1) st_out1(out + base, res);
+    else if constexpr (KPT == 2) st_out2(out + base, (res & 1u) | ((res & 2u) << 7));
+    else st_out4(out + base, (res & 1u) | ((res & 2u) << 7) | ((res & 4u) << 14) | ((res & 8u) << 21));
+  } else {
+#pragma unroll
+    for (int u = 0; u < KPT; ++u)
+      if ((valid >> u) & 1u) st_out1(out + base + u, (res >> u) & 1u);
+  }
+}
 
-  for (uint64_t tile = blockIdx.x * warps_per_cta + (threadIdx.x >> 5); tile < ntiles; tile += nwarps) {
-    const uint64_t base = tile * kTile + static_cast<uint64_t>(lane) * KPT;
-    uint64_t key[KPT];
-    const uint32_t valid = load_keys<KPT>(a.keys, a.n, base, vec_ok, pol_keys, key);
-    uint32_t hlo[KPT];
-    uint64_t blk[KPT];
+// Construction of the warp's tile of 32*KPT keys starting at `tile_base`.
+template <class C>
+__device__ __forceinline__ void add_tile(const TileCtx<C>& t, typename C::word_t* __restrict__ filter,
+                                         uint64_t nblocks, int block_mode, const uint64_t* keys, uint64_t n,
+                                         uint64_t acc0, bool vec_ok, uint64_t tile_base) {
+  using W = typename C::word_t;
+  constexpr int KPT = C::KPT, THETA = C::THETA, PHI = C::PHI, STEPS = C::steps;
+  const uint64_t base = tile_base + static_cast<uint64_t>(t.lane) * KPT;
+  uint64_t key[KPT];
+  const uint32_t valid = load_keys<KPT>(keys, n, base, vec_ok, t.pol_keys, key);
+  uint32_t hlo[KPT];
+  uint64_t blk[KPT];
 #pragma unroll
-    for (int u = 0; u < KPT; ++u) {
-      const uint64_t h = xxh64_key(key[u], a.acc0);
-      hlo[u] = static_cast<uint32_t>(h);
-      // invalid (tail) keys read block 0, which always exists; their result is dropped
-      blk[u] = ((valid >> u) & 1u) ? block_of(h, a.nblocks, a.block_mode) : 0;
-    }
-    // phase 1: issue every load of the tile before any test (memory-level parallelism)
-    W data[KPT][THETA][STEPS][PHI];
-    uint32_t hk[KPT][THETA];
+  for (int u = 0; u < KPT; ++u) {
+    const uint64_t h = xxh64_key(key[u], acc0);
+    hlo[u] = static_cast<uint32_t>(h);
+    blk[u] = block_of(h, nblocks, block_mode);
+  }
 #pragma unroll
-    for (int u = 0; u < KPT; ++u) {
+  for (int u = 0; u < KPT; ++u) {
 #pragma unroll
-      for (int m = 0; m < THETA; ++m) {
-        uint64_t bm = blk[u];
-        uint32_t hm = hlo[u];
-        if constexpr (THETA > 1) {
-          bm = __shfl_sync(kFullMask, bm, m, THETA);
-          hm = __shfl_sync(kFullMask, hm, m, THETA);
-        }
-        hk[u][m] = hm;
-        const W* bp = filter + bm * C::s + r * PHI;
-#pragma unroll
-        for (int q = 0; q < STEPS; ++q) ld_words<PHI>(bp + q * C::chunk, pol_filter, data[u][m][q]);
+    for (int m = 0; m < THETA; ++m) {
+      uint64_t bm = blk[u];
+      uint32_t hm = hlo[u];
+      uint32_t vm = valid;
+      if constexpr (THETA > 1) {
+        bm = __shfl_sync(kFullMask, bm, m, THETA);
+        hm = __shfl_sync(kFullMask, hm, m, THETA);
+        vm = __shfl_sync(kFullMask, vm, m, THETA);
       }
-    }
-    // phase 2: test every word against its pattern; AND across the CG
-    uint32_t res = 0;
+      if ((vm >> u) & 1u) {
+        // the CG's lanes update neighbouring words of one block in the same
+        // instruction, so L1 merges them into one request per sector
+        W* bp = filter + bm * C::s + t.r * PHI;
 #pragma unroll
-    for (int u = 0; u < KPT; ++u) {
-#pragma unroll
-      for (int m = 0; m < THETA; ++m) {
-        W miss = 0;
-#pragma unroll
-        for (int q = 0; q < STEPS; ++q) {
-#pragma unroll
-          for (int p = 0; p < PHI; ++p) {
-            const W pat = salts.pattern(hk[u][m], q, p);
-            miss |= pat & ~data[u][m][q][p];
-          }
-        }
-        bool ok = (miss == 0);
-        if constexpr (THETA > 1) {
-          const uint32_t seg = (__ballot_sync(kFullMask, ok) >> g0) & ((1u << THETA) - 1u);
-          ok = (seg == (1u << THETA) - 1u);
-          ok = ok && (r == static_cast<uint32_t>(m));
-        }
-        res |= static_cast<uint32_t>(ok) << u;
+        for (int q = 0; q < STEPS; ++q) red_lane_words<C>(bp + q * C::chunk, t.salts, hm, q, t.pol_filter);
       }
-    }
-    // coalesced write-back of the lane's own results
-    if (vec_ok && valid == (1u << KPT) - 1u) {
-      if constexpr (KPT == 1) st_out1(a.out + base, res);
-      else if constexpr (KPT == 2) st_out2(a.out + base, (res & 1u) | ((res & 2u) << 7));
-      else st_out4(a.out + base, (res & 1u) | ((res & 2u) << 7) | ((res & 4u) << 14) | ((res & 8u) << 21));
-    } else {
-#pragma unroll
-      for (int u = 0; u < KPT; ++u)
-        if ((valid >> u) & 1u) st_out1(a.out + base + u, (res >> u) & 1u);
     }
   }
 }
 
 template <class C>
-__global__ void __launch_bounds__(kMaxBlockThreads) sbf_add_kernel(const SbfArgs a) {
-  using W = typename C::word_t;
-  constexpr int KPT = C::KPT, THETA = C::THETA, PHI = C::PHI, STEPS = C::steps;
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t r = lane & (THETA - 1);
-  const LaneSalts<C> salts(r);
-  const uint64_t pol_keys = (a.flags & kHintKeysEvictNormal) ? policy_evict_normal() : policy_evict_first();
-  const uint64_t pol_filter = (a.flags & kHintFilterEvictLast) ? policy_evict_last() : policy_evict_normal();
-  W* __restrict__ filter = static_cast<W*>(a.filter);
-  constexpr uint64_t kTile = 32u * KPT;
+__global__ void __launch_bounds__(kMaxBlockThreads) sbf_contains_kernel(const SbfArgs a) {
+  const TileCtx<C> t(a.flags);
+  const W_of<C>* filter = static_cast<const W_of<C>*>(a.filter);
+  constexpr uint64_t kTile = 32u * C::KPT;
   const uint64_t ntiles = (a.n + kTile - 1) / kTile;
   const uint64_t warps_per_cta = blockDim.x >> 5;
   const uint64_t nwarps = static_cast<uint64_t>(gridDim.x) * warps_per_cta;
-  const bool vec_ok = reinterpret_cast<uintptr_t>(a.keys) % (8u * KPT) == 0;
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(a.keys) % (8u * C::KPT) == 0) &&
+                      (reinterpret_cast<uintptr_t>(a.out) % C::KPT == 0);
+  for (uint64_t tile = blockIdx.x * warps_per_cta + (threadIdx.x >> 5); tile < ntiles; tile += nwarps)
+    contains_tile<C>(t, filter, a.nblocks, a.block_mode, a.keys, a.n, a.out, a.acc0, vec_ok, tile * kTile);
+}
 
-  for (uint64_t tile = blockIdx.x * warps_per_cta + (threadIdx.x >> 5); tile < ntiles; tile += nwarps) {
-    const uint64_t base = tile * kTile + static_cast<uint64_t>(lane) * KPT;
-    uint64_t key[KPT];
-    const uint32_t valid = load_keys<KPT>(a.keys, a.n, base, vec_ok, pol_keys, key);
-    uint32_t hlo[KPT];
-    uint64_t blk[KPT];
-#pragma unroll
-    for (int u = 0; u < KPT; ++u) {
-      const uint64_t h = xxh64_key(key[u], a.acc0);
-      hlo[u] = static_cast<uint32_t>(h);
-      blk[u] = block_of(h, a.nblocks, a.block_mode);
-    }
-#pragma unroll
-    for (int u = 0; u < KPT; ++u) {
-#pragma unroll
-      for (int m = 0; m < THETA; ++m) {
-        uint64_t bm = blk[u];
-        uint32_t hm = hlo[u];
-        uint32_t vm = valid;
-        if constexpr (THETA > 1) {
-          bm = __shfl_sync(kFullMask, bm, m, THETA);
-          hm = __shfl_sync(kFullMask, hm, m, THETA);
-          vm = __shfl_sync(kFullMask, vm, m, THETA);
-        }
-        if ((vm >> u) & 1u) {
-          // the CG's lanes update neighbouring words of one block in the same
-          // instruction, so L1 merges them into one request per sector
-          W* bp = filter + bm * C::s + r * PHI;
-#pragma unroll
-          for (int q = 0; q < STEPS; ++q) red_lane_words<C>(bp + q * C::chunk, salts, hm, q, pol_filter);
-        }
-      }
-    }
-  }
+template <class C>
+__global__ void __launch_bounds__(kMaxBlockThreads) sbf_add_kernel(const SbfArgs a) {
+  const TileCtx<C> t(a.flags);
+  W_of<C>* filter = static_cast<W_of<C>*>(a.filter);
+  constexpr uint64_t kTile = 32u * C::KPT;
+  const uint64_t ntiles = (a.n + kTile - 1) / kTile;
+  const uint64_t warps_per_cta = blockDim.x >> 5;
+  const uint64_t nwarps = static_cast<uint64_t>(gridDim.x) * warps_per_cta;
+  const bool vec_ok = reinterpret_cast<uintptr_t>(a.keys) % (8u * C::KPT) == 0;
+  for (uint64_t tile = blockIdx.x * warps_per_cta + (threadIdx.x >> 5); tile < ntiles; tile += nwarps)
+    add_tile<C>(t, filter, a.nblocks, a.block_mode, a.keys, a.n, a.acc0, vec_ok, tile * kTile);
 }
 
 }  // namespace bloomgb

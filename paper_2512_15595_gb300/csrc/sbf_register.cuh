@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "sbf_kernels.cuh"
+#include "sbf_batch.cuh"
 #include "sbf_partition.cuh"
 
 namespace bloomgb {
@@ -34,6 +35,8 @@ void register_k(std::vector<KernelEntry>& v) {
         v.push_back({1, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_contains_kernel<C>)});
         v.push_back({2, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_add_records_kernel<C>)});
         v.push_back({4, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_probe_records_kernel<C>)});
+        v.push_back({7, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_batch_kernel<C, true>)});
+        v.push_back({8, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_batch_kernel<C, false>)});
       });
     });
   });
