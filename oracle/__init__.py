@@ -52,7 +52,7 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("num_blocks", ctypes.c_uint64), ("block_bits", ctypes.c_uint32),
                 ("word_bits", ctypes.c_uint32), ("k", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+                ("groups", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
 
 
 def lib():
@@ -70,6 +70,8 @@ def lib():
             "orc_bit_position": (u32, [u64, u32, u32]),
             "orc_check": (i32, [P]),
             "orc_word_pattern": (u64, [P, u64, u32]),
+            "orc_group_word": (u32, [P, u64, u32]),
+            "orc_group_pattern": (u64, [P, u64, u32]),
             "orc_add": (i32, [P, vp, vp, u64]),
             "orc_add_block_range": (i32, [P, vp, u64, u64, vp, u64]),
             "orc_contains": (i32, [P, vp, vp, u64, vp]),
@@ -136,19 +138,27 @@ def bit_position(h: int, salt_index: int, word_bits: int) -> int:
 # ---------------------------------------------------------------------------
 @dataclass(frozen=True)
 class Geometry:
+    """Filter geometry.  groups = z: 0 (or s) = sectorized filter (SBF);
+    0 < z < s = cache-sectorized filter (CSBF, Sec. II-A)."""
     num_blocks: int
     block_bits: int = 256
     word_bits: int = 32
     k: int = 8
     seed: int = 0
+    groups: int = 0
 
     @property
     def s(self) -> int:
         return self.block_bits // self.word_bits
 
     @property
+    def z(self) -> int:
+        return self.groups or self.s
+
+    @property
     def kp(self) -> int:
-        return self.k // self.s
+        """bits per touched word (k/s for the SBF, k/z for the CSBF)"""
+        return self.k // self.z
 
     @property
     def num_words(self) -> int:
@@ -163,7 +173,7 @@ class Geometry:
         return np.uint32 if self.word_bits == 32 else np.uint64
 
     def cparams(self) -> _Params:
-        return _Params(self.num_blocks, self.block_bits, self.word_bits, self.k, 0, self.seed)
+        return _Params(self.num_blocks, self.block_bits, self.word_bits, self.k, self.groups, self.seed)
 
     def valid(self) -> bool:
         p = self.cparams()
@@ -194,6 +204,12 @@ class SBF:
 
     def pattern(self, h: int, w: int) -> int:
         return lib().orc_word_pattern(ctypes.byref(self._p), h, w)
+
+    def group_word(self, h: int, q: int) -> int:
+        return lib().orc_group_word(ctypes.byref(self._p), h, q)
+
+    def group_pattern(self, h: int, q: int) -> int:
+        return lib().orc_group_pattern(ctypes.byref(self._p), h, q)
 
     def as_bytes(self) -> np.ndarray:
         return self.words.view(np.uint8)
@@ -299,14 +315,54 @@ def fpr_sbf_closed_form(num_blocks: int, n: int, block_bits: int, word_bits: int
     return math.fsum(acc)
 
 
+def fpr_csbf_closed_form(num_blocks: int, n: int, block_bits: int, word_bits: int, k: int, groups: int) -> float:
+    """Expected FPR of the cache-sectorized filter (Sec. II-A, CSBF), ideal hashing.
+
+    A block holds i ~ Binom(n, 1/b) keys; in each of its z groups a key selects
+    one of g = s/z words, so the word a fresh query selects has received
+    m ~ Binom(i, 1/g) keys' worth of k' = k/z throws:
+        FPR = sum_i Binom(i; n, 1/b) * [sum_m Binom(m; i, 1/g) * word_fpr(m k', k', S)]^z.
+    With z = s (g = 1) this is fpr_sbf_closed_form.
+    """
+    s = block_bits // word_bits
+    z = groups or s
+    g = s // z
+    kp = k // z
+    if g == 1:
+        return fpr_sbf_closed_form(num_blocks, n, block_bits, word_bits, k)
+    p = 1.0 / num_blocks
+    mean = n * p
+    sd = math.sqrt(max(mean * (1 - p), 1e-300))
+    i_hi = min(n, int(mean + 40 * sd + 50))
+    i_lo = max(0, int(mean - 40 * sd - 50))
+    wf_cache = {}
+
+    def wf(load):
+        if load not in wf_cache:
+            wf_cache[load] = word_fpr(load, kp, word_bits)
+        return wf_cache[load]
+
+    acc = []
+    for i in range(i_lo, i_hi + 1):
+        w = _binom_pmf(i, n, p) if num_blocks > 1 else (1.0 if i == n else 0.0)
+        if w == 0.0:
+            continue
+        grp = math.fsum(_binom_pmf(m, i, 1.0 / g) * wf(m * kp) for m in range(i + 1))
+        acc.append(w * grp ** z)
+    return math.fsum(acc)
+
+
 def fpr_given_filter(words: np.ndarray, geom: Geometry) -> float:
     """Exact FPR of a fresh key against this bit array (ideal hashing of the key).
 
-    A fresh key picks a uniform block, then k' independent uniform positions
-    per word: P(all set) = (1/b) sum_blocks prod_w (popcount_w / S)^k'.
+    A fresh key picks a uniform block, then (SBF) k' independent uniform
+    positions per word: P(all set) = (1/b) sum_blocks prod_w (popcount_w / S)^k';
+    (CSBF) in each group a uniform word of its g, then k' positions in it:
+    (1/b) sum_blocks prod_groups (1/g) sum_{w in group} (popcount_w / S)^k'.
     """
-    pc = np.bitwise_count(words).astype(np.float64).reshape(geom.num_blocks, geom.s)
-    per_block = np.prod((pc / geom.word_bits) ** geom.kp, axis=1)
+    pc = np.bitwise_count(words).astype(np.float64).reshape(geom.num_blocks, geom.z, geom.s // geom.z)
+    per_group = np.mean((pc / geom.word_bits) ** geom.kp, axis=2)
+    per_block = np.prod(per_group, axis=1)
     return float(math.fsum(per_block) / geom.num_blocks)
 
 

@@ -30,6 +30,18 @@
  *   - bit t (t = 0..k'-1) of word w (w = 0..s-1) uses salt index w + s*t;
  *   - a word's bit p is the value 1 << p (bit 0 = least significant); block
  *     j occupies words j*s .. j*s+s-1; words are stored little-endian.
+ *
+ * Cache-sectorized form (Sec. II-A, CSBF; Sec. V-A for the extra multiplier),
+ * selected by groups = z with 0 < z < s: the s words form z groups of
+ * g = s/z neighbouring words; in group q one word is selected, and it
+ * receives k/z bits.  Readings:
+ *   - the selected word of group q is q*g + sel, with sel the top log2(g)
+ *     bits of (h_lo * salt[63 - q]) (mod 2^32 for S = 32, mod 2^64 for
+ *     S = 64): "another odd multiplier", taken from the top of the table;
+ *   - bit t (t = 0..k/z-1) of group q uses salt index q + z*t (with z = s
+ *     this is the sectorized rule, and the two forms coincide);
+ *   - k must be a multiple of z and k + z <= 64 (the pattern and selection
+ *     multipliers then never share a table entry).
  */
 #include <stddef.h>
 #include <stdint.h>
@@ -202,21 +214,61 @@ typedef struct {
     uint32_t block_bits;
     uint32_t word_bits;
     uint32_t k;
-    uint32_t reserved;
+    uint32_t groups;    /* z: 0 (or s) = sectorized; 0 < z < s = cache-sectorized */
     uint64_t seed;
 } orc_params;
 
-/* 0 if the geometry is one the SBF definition admits (Sec. II-A: s = B/S
-   words, k >= s and s | k), else -1 */
+static uint32_t effective_groups(const orc_params* p)
+{
+    uint32_t s = p->block_bits / p->word_bits;
+    return (p->groups == 0) ? s : p->groups;
+}
+
+/* 0 if the geometry is one the definitions admit, else -1.
+   SBF (Sec. II-A): s = B/S words, k >= s and s | k.
+   CSBF (Sec. II-A): z groups with z | s, z | k, and k + z <= 64. */
 int orc_check(const orc_params* p)
 {
     if (p->num_blocks == 0) return -1;
     if (p->word_bits != 32 && p->word_bits != 64) return -1;
     if (p->block_bits < p->word_bits || p->block_bits % p->word_bits != 0) return -1;
     uint32_t s = p->block_bits / p->word_bits;
-    if (p->k < s || p->k % s != 0) return -1;
+    uint32_t z = effective_groups(p);
+    if (z == 0 || z > s || s % z != 0) return -1;
+    if (p->k < z || p->k % z != 0) return -1;
     if (p->k > ORC_MAX_SALTS) return -1;
+    if (z < s && p->k + z > ORC_MAX_SALTS) return -1;
     return 0;
+}
+
+/* word of group q selected by h (CSBF); for groups of one word it is that word */
+uint32_t orc_group_word(const orc_params* p, uint64_t h, uint32_t q)
+{
+    uint32_t s = p->block_bits / p->word_bits;
+    uint32_t z = effective_groups(p);
+    uint32_t g = s / z;
+    uint32_t log2g = 0;
+    while ((1u << log2g) < g) log2g++;
+    if (log2g == 0) return q;
+    uint64_t h_lo = h & 0xFFFFFFFFULL;
+    uint32_t sel;
+    if (p->word_bits == 32) {
+        uint32_t product = (uint32_t)(h_lo * (uint64_t)orc_salt32(63 - q));
+        sel = product >> (32 - log2g);
+    } else {
+        sel = (uint32_t)((h_lo * orc_salt64(63 - q)) >> (64 - log2g));
+    }
+    return q * g + sel;
+}
+
+/* pattern of the selected word of group q: the OR of its k/z bits */
+uint64_t orc_group_pattern(const orc_params* p, uint64_t h, uint32_t q)
+{
+    uint32_t z = effective_groups(p);
+    uint32_t kz = p->k / z;
+    uint64_t pattern = 0;
+    for (uint32_t t = 0; t < kz; ++t) pattern |= 1ULL << orc_bit_position(h, q + z * t, p->word_bits);
+    return pattern;
 }
 
 static uint64_t word_get(const void* words, uint32_t word_bits, uint64_t index)
@@ -248,11 +300,12 @@ int orc_add(const orc_params* p, void* words, const uint64_t* keys, uint64_t n)
 {
     if (orc_check(p) != 0) return -1;
     uint32_t s = p->block_bits / p->word_bits;
+    uint32_t z = effective_groups(p);
     for (uint64_t i = 0; i < n; ++i) {
         uint64_t h = orc_key_hash(keys[i], p->seed);
         uint64_t j = orc_block_index(h, p->num_blocks);
-        for (uint32_t w = 0; w < s; ++w)
-            word_or(words, p->word_bits, j * s + w, orc_word_pattern(p, h, w));
+        for (uint32_t q = 0; q < z; ++q)
+            word_or(words, p->word_bits, j * s + orc_group_word(p, h, q), orc_group_pattern(p, h, q));
     }
     return 0;
 }
@@ -264,12 +317,13 @@ int orc_add_block_range(const orc_params* p, void* words, uint64_t block_lo, uin
 {
     if (orc_check(p) != 0) return -1;
     uint32_t s = p->block_bits / p->word_bits;
+    uint32_t z = effective_groups(p);
     for (uint64_t i = 0; i < n; ++i) {
         uint64_t h = orc_key_hash(keys[i], p->seed);
         uint64_t j = orc_block_index(h, p->num_blocks);
         if (j < block_lo || j >= block_hi) continue;
-        for (uint32_t w = 0; w < s; ++w)
-            word_or(words, p->word_bits, (j - block_lo) * s + w, orc_word_pattern(p, h, w));
+        for (uint32_t q = 0; q < z; ++q)
+            word_or(words, p->word_bits, (j - block_lo) * s + orc_group_word(p, h, q), orc_group_pattern(p, h, q));
     }
     return 0;
 }
@@ -278,13 +332,14 @@ int orc_contains(const orc_params* p, const void* words, const uint64_t* keys, u
 {
     if (orc_check(p) != 0) return -1;
     uint32_t s = p->block_bits / p->word_bits;
+    uint32_t z = effective_groups(p);
     for (uint64_t i = 0; i < n; ++i) {
         uint64_t h = orc_key_hash(keys[i], p->seed);
         uint64_t j = orc_block_index(h, p->num_blocks);
         int member = 1;
-        for (uint32_t w = 0; w < s; ++w) {
-            uint64_t pattern = orc_word_pattern(p, h, w);
-            if ((word_get(words, p->word_bits, j * s + w) & pattern) != pattern) member = 0;
+        for (uint32_t q = 0; q < z; ++q) {
+            uint64_t pattern = orc_group_pattern(p, h, q);
+            if ((word_get(words, p->word_bits, j * s + orc_group_word(p, h, q)) & pattern) != pattern) member = 0;
         }
         out[i] = (uint8_t)member;
     }
@@ -298,14 +353,16 @@ int orc_contains_block_range(const orc_params* p, const void* words, uint64_t bl
 {
     if (orc_check(p) != 0) return -1;
     uint32_t s = p->block_bits / p->word_bits;
+    uint32_t z = effective_groups(p);
     for (uint64_t i = 0; i < n; ++i) {
         uint64_t h = orc_key_hash(keys[i], p->seed);
         uint64_t j = orc_block_index(h, p->num_blocks);
         if (j < block_lo || j >= block_hi) { out[i] = 2; continue; }
         int member = 1;
-        for (uint32_t w = 0; w < s; ++w) {
-            uint64_t pattern = orc_word_pattern(p, h, w);
-            if ((word_get(words, p->word_bits, (j - block_lo) * s + w) & pattern) != pattern) member = 0;
+        for (uint32_t q = 0; q < z; ++q) {
+            uint64_t pattern = orc_group_pattern(p, h, q);
+            uint64_t idx = (j - block_lo) * s + orc_group_word(p, h, q);
+            if ((word_get(words, p->word_bits, idx) & pattern) != pattern) member = 0;
         }
         out[i] = (uint8_t)member;
     }
