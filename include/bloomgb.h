@@ -65,15 +65,24 @@ typedef enum {
 } bf_status;
 
 /* Filter geometry (Sec. II-A).  num_blocks = b >= 1; block_bits = B in
-   {64,128,256,512,1024}; word_bits = S in {32,64}; k = pattern bits with
-   s = B/S words per block, k >= s, s | k, k <= 64; seed = XXH64 seed.
-   Builds compile k in {4,8,16}; other admissible k return BF_EUNSUPPORTED. */
+   {64,128,256,512,1024}; word_bits = S in {32,64}; seed = XXH64 seed.
+   groups = 0 (or s): sectorized filter (SBF): s = B/S words per block, k
+   pattern bits with k >= s, s | k, k <= 64, k/s bits in every word.
+   0 < groups = z < s: cache-sectorized filter (CSBF): the s words form z
+   groups of s/z neighbouring words; in group q the word q*(s/z) + sel is
+   selected, sel = the top log2(s/z) bits of (h_lo * salt[63 - q]) (mod 2^S,
+   with a 64-bit product for S = 64), and it receives k/z bits (bit t from
+   salt q + z*t); z | s, z | k, k + z <= 64.  Only the z selected words are
+   read or updated.
+   Builds compile k in {4,8,16} and, for the CSBF, z in {1,2,4,8}; other
+   admissible values return BF_EUNSUPPORTED.  The slice-partitioned paths,
+   batches and bf_add_noalloc serve sectorized filters only. */
 typedef struct {
     uint64_t num_blocks;
     uint32_t block_bits;
     uint32_t word_bits;
     uint32_t k;
-    uint32_t reserved;      /* must be 0 */
+    uint32_t groups;        /* z; 0 = sectorized */
     uint64_t seed;
 } bf_params;
 
@@ -86,8 +95,10 @@ enum {
 };
 
 /* Execution layout of one operation (Sec. IV-A, IV-C).
-   cg = Theta threads per key (power of two, 1..s); phi = Phi words per thread
-   per step (power of two, cg*phi <= s); kpt = keys each thread hashes per
+   cg = Theta threads per key (power of two, 1..s; for a cache-sectorized
+   filter a divisor of groups, each lane handling groups/cg groups); phi = Phi
+   words per thread per step (power of two, cg*phi <= s; 1 for a
+   cache-sectorized filter, which loads single words); kpt = keys each thread hashes per
    tile (1, 2 or 4); block_threads = CTA size (multiple of 32, <= 512);
    grid_ctas = number of CTAs (0 = SM count x resident CTAs per SM).
    A zero in cg/phi/kpt/block_threads selects the library default. */

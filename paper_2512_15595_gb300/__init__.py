@@ -57,9 +57,9 @@ class Filter:
     """A filter whose bit array is a torch tensor (adopted by the library)."""
 
     def __init__(self, num_blocks: int, block_bits: int = 256, word_bits: int = 32, k: int = 8,
-                 seed: int = 0, device=None, words=None):
+                 seed: int = 0, device=None, words=None, groups: int = 0):
         import torch
-        self.params = bf_params(num_blocks, block_bits, word_bits, k, 0, seed)
+        self.params = bf_params(num_blocks, block_bits, word_bits, k, groups, seed)
         self.nbytes = num_blocks * block_bits // 8
         if words is None:
             device = torch.device(device or "cuda")

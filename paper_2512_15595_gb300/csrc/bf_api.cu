@@ -65,6 +65,16 @@ const KernelEntry* find_sbf(int op, const bf_params& p, const bf_layout& l) {
   return nullptr;
 }
 
+const KernelEntry* find_csbf(int op, const bf_params& p, const bf_layout& l, uint32_t z) {
+  for (const auto& e : registry().sbf) {
+    if (e.op == op && e.B == static_cast<int>(p.block_bits) && e.S == static_cast<int>(p.word_bits) &&
+        e.K == static_cast<int>(p.k) && e.z == static_cast<int>(z) && e.theta == static_cast<int>(l.cg) &&
+        e.kpt == static_cast<int>(l.kpt))
+      return &e;
+  }
+  return nullptr;
+}
+
 const GupsEntry* find_gups(int mode, uint32_t unit, uint32_t kpt) {
   for (const auto& e : registry().gups)
     if (e.mode == mode && e.unit_bytes == static_cast<int>(unit) && e.kpt == static_cast<int>(kpt)) return &e;
@@ -170,16 +180,30 @@ struct bf_filter {
 
 namespace {
 
+// groups of a cache-sectorized filter, or 0 for the sectorized one (z = s is
+// the sectorized filter too: one word per group)
+uint32_t csbf_groups(const bf_params& p) {
+  const uint32_t s = p.block_bits / p.word_bits;
+  return (p.groups == 0 || p.groups == s) ? 0 : p.groups;
+}
+
 bf_status check_params(const bf_params* p) {
   if (!p) return fail(BF_EINVAL, "params is NULL");
-  if (p->reserved != 0) return fail(BF_EINVAL, "params.reserved must be 0");
   if (p->num_blocks == 0) return fail(BF_EINVAL, "num_blocks must be >= 1");
   if (p->word_bits != 32 && p->word_bits != 64) return fail(BF_EINVAL, "word_bits must be 32 or 64");
   if (!is_pow2(p->block_bits) || p->block_bits < p->word_bits || p->block_bits > 1024)
     return fail(BF_EINVAL, "block_bits must be a power of two in [word_bits, 1024]");
   const uint32_t s = p->block_bits / p->word_bits;
-  if (p->k < s || p->k % s != 0 || p->k > 64)
-    return fail(BF_EINVAL, "k must be a multiple of s = block_bits/word_bits, s <= k <= 64");
+  if (p->groups > s || (p->groups && s % p->groups != 0))
+    return fail(BF_EINVAL, "groups must divide s = block_bits/word_bits");
+  const uint32_t z = csbf_groups(*p);
+  if (z == 0) {
+    if (p->k < s || p->k % s != 0 || p->k > 64)
+      return fail(BF_EINVAL, "k must be a multiple of s = block_bits/word_bits, s <= k <= 64");
+  } else {
+    if (p->k < z || p->k % z != 0 || p->k + z > 64)
+      return fail(BF_EINVAL, "cache-sectorized: k must be a multiple of groups and k + groups <= 64");
+  }
   if (p->num_blocks > (~0ull) / 128) return fail(BF_EINVAL, "num_blocks too large");
   return BF_OK;
 }
@@ -187,7 +211,12 @@ bf_status check_params(const bf_params* p) {
 bf_layout default_layout(const bf_params& p, int op) {
   const uint32_t s = p.block_bits / p.word_bits;
   bf_layout l{};
-  if (op == BF_OP_ADD) {
+  if (const uint32_t z = csbf_groups(p)) {
+    // cache-sectorized: every group's word update in one instruction; lookups one thread per key
+    l.cg = op == BF_OP_ADD ? z : 1;
+    l.phi = 1;
+    l.kpt = op == BF_OP_ADD ? 1 : 2;
+  } else if (op == BF_OP_ADD) {
     // Sec. V-B: a fully horizontal layout (Theta = s) coalesces the atomics
     l.cg = s;
     l.phi = 1;
@@ -209,20 +238,25 @@ bf_status resolve_layout(const bf_params& p, int op, const bf_layout* in, bf_lay
                          const KernelEntry** entry) {
   if (op != BF_OP_ADD && op != BF_OP_CONTAINS) return fail(BF_EINVAL, "op must be BF_OP_ADD or BF_OP_CONTAINS");
   const uint32_t s = p.block_bits / p.word_bits;
+  const uint32_t z = csbf_groups(p);
   bf_layout d = default_layout(p, op);
   bf_layout l = in ? *in : d;
   if (l.cg == 0) l.cg = d.cg;
-  if (l.phi == 0) l.phi = std::max<uint32_t>(1, s / l.cg);
+  if (l.phi == 0) l.phi = z ? 1 : std::max<uint32_t>(1, s / l.cg);
   if (l.kpt == 0) l.kpt = d.kpt;
   if (l.block_threads == 0) l.block_threads = d.block_threads;
-  if (!is_pow2(l.cg) || !is_pow2(l.phi) || static_cast<uint64_t>(l.cg) * l.phi > s)
+  if (z) {
+    if (!is_pow2(l.cg) || z % l.cg != 0 || l.phi != 1)
+      return fail(BF_EINVAL, "cache-sectorized layout: cg a power of two dividing groups, phi = 1");
+  } else if (!is_pow2(l.cg) || !is_pow2(l.phi) || static_cast<uint64_t>(l.cg) * l.phi > s) {
     return fail(BF_EINVAL, "layout needs powers of two with 1 <= cg*phi <= s");
+  }
   if (l.kpt != 1 && l.kpt != 2 && l.kpt != 4) return fail(BF_EINVAL, "kpt must be 1, 2 or 4");
   if (l.block_threads % 32 != 0 || l.block_threads > static_cast<uint32_t>(kMaxBlockThreadsHost))
     return fail(BF_EINVAL, "block_threads must be a multiple of 32 and <= 512");
   if (l.flags & ~(BF_HINT_FILTER_EVICT_LAST | BF_HINT_KEYS_EVICT_NORMAL))
     return fail(BF_EINVAL, "unknown layout flag");
-  const KernelEntry* e = find_sbf(op, p, l);
+  const KernelEntry* e = z ? find_csbf(op == BF_OP_ADD ? 9 : 10, p, l, z) : find_sbf(op, p, l);
   if (!e) return fail(BF_EUNSUPPORTED, "no compiled kernel for this geometry and layout");
   *out = l;
   if (entry) *entry = e;
@@ -276,7 +310,7 @@ uint64_t part_cap(const bf_filter* f, const PartPlan& pl, uint64_t keys) {
 }
 
 bool use_partitioned(const bf_filter* f, uint64_t n) {
-  if (f->part.mode == BF_PART_OFF || f->p.num_blocks > (1ull << 32)) return false;
+  if (f->part.mode == BF_PART_OFF || f->p.num_blocks > (1ull << 32) || csbf_groups(f->p)) return false;
   const PartPlan pl = part_plan(f);
   if (pl.nparts < 2) return false;
   if (f->part.mode == BF_PART_ON) return true;
@@ -363,7 +397,7 @@ bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cud
 }
 
 bool use_partitioned_lookup(const bf_filter* f, uint64_t n) {
-  if (f->part.lookup_mode == BF_PART_OFF || f->p.num_blocks > (1ull << 32)) return false;
+  if (f->part.lookup_mode == BF_PART_OFF || f->p.num_blocks > (1ull << 32) || csbf_groups(f->p)) return false;
   const PartPlan pl = part_plan(f);
   if (pl.nparts < 2) return false;
   if (f->part.lookup_mode == BF_PART_ON) return true;
@@ -884,7 +918,7 @@ extern "C" bf_status bf_add_noalloc(const bf_params* params, void* d_words, cons
   (void)g_noalloc_registry_ready;
   if (max_keys) *max_keys = 0;
   if (!params || !d_words) return BF_EINVAL;
-  if (params->reserved != 0 || params->num_blocks == 0 || params->num_blocks > (1ull << 32) ||
+  if (params->groups != 0 || params->num_blocks == 0 || params->num_blocks > (1ull << 32) ||
       (params->word_bits != 32 && params->word_bits != 64) || !is_pow2(params->block_bits) ||
       params->block_bits < params->word_bits || params->block_bits > 1024)
     return BF_EINVAL;
@@ -1026,6 +1060,7 @@ bf_status bf_batch_create(const bf_params* params, const bf_batch_filter* filter
   p.num_blocks = 1;  // per filter
   bf_status s = bf_params_check(&p);
   if (s != BF_OK) return s;
+  if (csbf_groups(p)) return fail(BF_EUNSUPPORTED, "batches hold sectorized filters only");
   const uint64_t align = std::max<uint64_t>(32, p.block_bits / 8);
   std::vector<BatchFilter> hf(nfilters);
   std::vector<uint64_t> begin(static_cast<size_t>(nfilters) + 1, 0);

@@ -126,9 +126,11 @@ struct KernelEntry {
   // 0 add, 1 contains, 2 add from slice records, 3 slice partition (add),
   // 4 probe slice records, 5 slice partition (lookup), 6 bitmap expansion,
   // 7 batched add, 8 batched contains
+  // 9 cache-sectorized add, 10 cache-sectorized contains (z = groups)
   int op;
   int B, S, K, theta, phi, kpt;
   const void* fn;
+  int z = 0;  // groups of a cache-sectorized kernel; 0 = sectorized
 };
 
 struct GupsEntry {

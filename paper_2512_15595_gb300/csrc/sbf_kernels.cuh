@@ -43,6 +43,8 @@ constexpr unsigned kFullMask = 0xFFFFFFFFu;
 
 template <class C>
 using W_of = typename C::word_t;
+
+constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
 // CTA size bound the kernels are compiled for (leaves up to 128 registers per thread)
 constexpr int kMaxBlockThreads = 512;
 

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "sbf_kernels.cuh"
+#include "csbf_kernels.cuh"
 #include "sbf_batch.cuh"
 #include "sbf_partition.cuh"
 
@@ -44,8 +45,36 @@ void register_k(std::vector<KernelEntry>& v) {
   v.push_back({5, B, S, K, 0, 0, 0, reinterpret_cast<const void*>(&sbf_partition_kernel<B, S, K, true>)});
 }
 
+template <int B, int S, int K, int Z>
+void register_csbf(std::vector<KernelEntry>& v) {
+  host_static_for<ilog2(Z) + 1>([&](auto lt) {
+    constexpr int T = 1 << decltype(lt)::value;
+    host_static_for<3>([&](auto lk) {
+      constexpr int KPT = 1 << decltype(lk)::value;
+      using C = CCfg<B, S, K, Z, T, KPT>;
+      v.push_back({9, B, S, K, T, 1, KPT, reinterpret_cast<const void*>(&csbf_add_kernel<C>), Z});
+      v.push_back({10, B, S, K, T, 1, KPT, reinterpret_cast<const void*>(&csbf_contains_kernel<C>), Z});
+    });
+  });
+}
+
+// cache-sectorized kernels for groups Z in {1, 2, 4, 8} (Z < s) and K in {4, 8, 16} with Z | K
+template <int B, int S, int Z>
+void register_csbf_z(std::vector<KernelEntry>& v) {
+  constexpr int s = B / S;
+  if constexpr (Z < s) {
+    if constexpr (4 % Z == 0) register_csbf<B, S, 4, Z>(v);
+    if constexpr (8 % Z == 0) register_csbf<B, S, 8, Z>(v);
+    if constexpr (16 % Z == 0) register_csbf<B, S, 16, Z>(v);
+  }
+}
+
 template <int B, int S>
 void register_geometry(std::vector<KernelEntry>& v) {
+  register_csbf_z<B, S, 1>(v);
+  register_csbf_z<B, S, 2>(v);
+  register_csbf_z<B, S, 4>(v);
+  register_csbf_z<B, S, 8>(v);
   constexpr int s = B / S;
   if constexpr (4 % s == 0) register_k<B, S, 4>(v);
   if constexpr (s <= 8) register_k<B, S, 8>(v);

@@ -41,8 +41,8 @@ def test_status_strings_and_version(L):
     assert "sm_103a" in L.bf_version()
 
 
-def P(L, b=1000, B=256, S=32, k=8, seed=0, reserved=0):
-    return L.bf_params(b, B, S, k, reserved, seed)
+def P(L, b=1000, B=256, S=32, k=8, seed=0, groups=0):
+    return L.bf_params(b, B, S, k, groups, seed)
 
 
 def test_params_check(L):
@@ -54,7 +54,8 @@ def test_params_check(L):
     for B, S, k in bad:
         assert L.bf_params_check(P(L, B=B, S=S, k=k)) == L.BF_EINVAL, (B, S, k)
     assert L.bf_params_check(P(L, b=0)) == L.BF_EINVAL
-    assert L.bf_params_check(P(L, reserved=1)) == L.BF_EINVAL
+    assert L.bf_params_check(P(L, groups=3)) == L.BF_EINVAL   # groups must divide s
+    assert L.bf_params_check(P(L, groups=16)) == L.BF_EINVAL  # more groups than words
     # admissible but not compiled (k outside {4, 8, 16})
     assert L.bf_params_check(P(L, B=256, S=32, k=24)) == L.BF_EUNSUPPORTED
     assert L.bf_params_check(P(L, B=1024, S=32, k=32)) == L.BF_EUNSUPPORTED
@@ -114,3 +115,20 @@ def test_null_arguments_rejected_without_gpu(L):
     # gups argument checks happen before any CUDA call
     assert lib.bf_gups(5, None, 0, 32, None, 0, None, None, None) == L.BF_EINVAL
     assert lib.bf_gups(0, None, 1 << 20, 48, None, 10, None, None, None) == L.BF_EINVAL
+
+
+def test_csbf_params_and_layouts(L):
+    # cache-sectorized (Sec. II-A): z | s, z | k, k + z <= 64
+    for B, S, k, z in [(512, 64, 16, 2), (1024, 64, 16, 4), (256, 32, 4, 1), (256, 32, 8, 4), (1024, 64, 8, 8)]:
+        assert L.bf_params_check(P(L, B=B, S=S, k=k, groups=z)) == L.BF_OK, (B, S, k, z)
+    # z = s is the sectorized filter
+    assert L.bf_params_check(P(L, B=256, S=32, k=8, groups=8)) == L.BF_OK
+    for B, S, k, z in [(512, 64, 6, 4), (512, 64, 16, 3)]:
+        assert L.bf_params_check(P(L, B=B, S=S, k=k, groups=z)) == L.BF_EINVAL, (B, S, k, z)
+    p = P(L, B=1024, S=64, k=16, groups=4)
+    for cg in (1, 2, 4):
+        for kpt in (1, 2, 4):
+            for op in (0, 1):
+                assert L.bf_layout_check(p, op, L.bf_layout(cg, 1, kpt, 256, 0, 0)) == L.BF_OK
+    assert L.bf_layout_check(p, 0, L.bf_layout(8, 1, 1, 256, 0, 0)) == L.BF_EINVAL  # cg must divide groups
+    assert L.bf_layout_check(p, 1, L.bf_layout(1, 2, 1, 256, 0, 0)) == L.BF_EINVAL  # phi must be 1
