@@ -625,6 +625,72 @@ def run_batched(args):
     batch.close()
 
 
+def run_frontier(args):
+    """Throughput vs FPR of the sectorized (SBF) and cache-sectorized (CSBF)
+    variants, as the paper's frontier (Sec. V-A, V-B, V-C): S = 64, k = 16,
+    block sizes 256/512/1024, every compiled group count, on a 32 MiB
+    (L2-resident) and a 1 GiB (HBM-resident) filter.  The filter holds the
+    Eq. (1)-optimal number of keys for k = 16 (c = k / ln 2 bits per key);
+    throughput = best layout for inserting them and for looking them all up
+    (true positives), FPR = fraction of 10^8 fresh keys reported present.
+    One JSON line per configuration, then a summary line."""
+    import torch
+    import synthkeys
+    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS, Filter, valid_layouts
+    from paper_2512_15595_gb300.autotune import time_op
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    S, K = 64, 16
+    c_opt = K / math.log(2.0)
+    fresh_n = 10**8
+    fresh = synthkeys.splitmix64_torch(synthkeys.SEED_FRESH + 100, 0, fresh_n, device)
+    rows = []
+    for size_name, nbytes in (("32MiB", 32 << 20), ("1GiB", 1 << 30)):
+        for B in (256, 512, 1024):
+            s_ = B // S
+            nb = nbytes * 8 // B
+            n = int(nbytes * 8 / c_opt)
+            keys = synthkeys.splitmix64_torch(synthkeys.SEED_INSERT, 0, n, device)
+            out = torch.empty(max(n, fresh_n), dtype=torch.uint8, device=device)
+            variants = [0] + [z for z in (1, 2, 4, 8) if z < s_ and K % z == 0]
+            for z in variants:
+                f = Filter(nb, B, S, K, 0, device=device, groups=z)
+                if z:
+                    layouts = [(cg, 1) for cg in (1, 2, 4, 8) if z % cg == 0]
+                else:
+                    layouts = [(cg, s_ // cg) for cg in (1, 2, 4, 8, 16) if cg <= s_]  # max phi per cg (tables)
+                best = {}
+                for part in ((0,) if z else (0, 1)):
+                    f.set_partition(mode=part, lookup_mode=part)
+                    for cg, phi in layouts:
+                        for kpt in (1, 4):
+                            for op, name, ks in ((BF_OP_ADD, "add", keys), (BF_OP_CONTAINS, "contains", keys)):
+                                f.set_layout(op, cg=cg, phi=phi, kpt=kpt)
+                                if op == BF_OP_CONTAINS:
+                                    f.clear()
+                                    f.add(keys)
+                                ms = time_op(torch, f, op, ks, out[:n], reps=3, warmup=1)
+                                g = n / (ms * 1e-3) / 1e9
+                                if g > best.get(name, (0,))[0]:
+                                    best[name] = (g, dict(cg=cg, phi=phi, kpt=kpt, partitioned=bool(part)))
+                f.set_partition(mode=0, lookup_mode=0)
+                f.clear()
+                f.add(keys)
+                hits = f.contains(fresh, out=out[:fresh_n])
+                fpr = float(hits.float().mean().item())
+                row = {"size": size_name, "block_bits": B, "word_bits": S, "k": K, "groups": z or s_,
+                       "variant": "SBF" if not z else f"CSBF z={z}", "keys": n, "bits_per_key": nbytes * 8 / n,
+                       "insert_gkeys_s": best["add"][0], "insert_layout": best["add"][1],
+                       "lookup_gkeys_s": best["contains"][0], "lookup_layout": best["contains"][1],
+                       "fpr": fpr}
+                rows.append(row)
+                print(json.dumps(row), flush=True)
+                f.close()
+            del keys, out
+            torch.cuda.empty_cache()
+    print(json.dumps({"frontier": len(rows), "note": "S=64, k=16, Eq. (1)-optimal load; best layout per op"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -633,6 +699,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="4GiB", choices=sorted(WORKLOADS) + ["batched"])
     ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--frontier", action="store_true")
     ap.add_argument("--sweep-keys", type=int, default=1 << 28)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-gups", action="store_true")
@@ -641,6 +708,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.frontier:
+        run_frontier(args)
+        return
     if args.workload == "batched":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "no CPU arm for the batched workload"}))
