@@ -691,13 +691,82 @@ def run_frontier(args):
     print(json.dumps({"frontier": len(rows), "note": "S=64, k=16, Eq. (1)-optimal load; best layout per op"}))
 
 
+def run_serving(args):
+    """Serving loop: 64 device-resident filters with sizes log-uniform 1 MiB-2 GiB
+    (256-bit blocks, S=32, K=8; each holds 10 bits/key of its own key stream);
+    lookup requests arrive as a Poisson process, each for one filter (uniform)
+    with log-uniform 1K-16M keys from a pinned host pool; the server admits
+    them into a 2^28-key device arena and batches them across filters per
+    launch.  Reports p50/p99 latency and sustained G lookups/s at several
+    offered loads."""
+    import numpy as np
+    import torch
+    import synthkeys
+    from synthkeys import batches
+    from paper_2512_15595_gb300 import Filter, _lib
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    B, S, K, nf = 256, 32, 8, 64
+    bb = B // 8
+    blocks = batches.log_uniform_sizes(nf, 1 << 20, 2 << 30, bb, seed=6)
+    filters = []
+    for i, nb in enumerate(blocks):
+        f = Filter(int(nb), B, S, K, 0, device=device)
+        f.set_partition(mode=0)  # set-up only: the direct kernel needs no workspace
+        n = int(nb) * B // 10
+        for lo in range(0, n, 1 << 28):
+            c = min(1 << 28, n - lo)
+            f.add(synthkeys.splitmix64_torch(1000 + i, lo, c, device))
+        filters.append(f)
+    torch.cuda.synchronize()
+    pool_n = 1 << 28
+    pool = torch.empty(pool_n, dtype=torch.int64, pin_memory=True)
+    pool.copy_(synthkeys.splitmix64_torch(synthkeys.SEED_FRESH, 0, pool_n, device))
+    pout = torch.zeros(pool_n, dtype=torch.uint8, pin_memory=True)
+    srv = _lib.bf_server_create(_lib.bf_params(1, B, S, K, 0, 0),
+                                [(f.words.data_ptr(), int(nb)) for f, nb in zip(filters, blocks)],
+                                arena_keys=1 << 28, max_requests_per_launch=4096)
+    min_k, max_k = 1 << 10, 1 << 24
+    mean_keys = (max_k - min_k) / math.log(max_k / min_k)
+    results = []
+    try:
+        # warm-up
+        _lib.bf_server_run_poisson(srv, 200.0, 0.2, min_k, max_k, pool.data_ptr(), pool_n, pout.data_ptr(), 1)
+        for load_gkeys in (5.0, 10.0, 15.0, 20.0, 25.0):
+            rate = load_gkeys * 1e9 / mean_keys
+            st = _lib.bf_server_run_poisson(srv, rate, args.serve_seconds, min_k, max_k, pool.data_ptr(), pool_n,
+                                            pout.data_ptr(), 11)
+            results.append({"offered_gkeys_s": load_gkeys, "requests_per_s": rate,
+                            "sustained_gkeys_s": st["keys"] / st["span_s"] / 1e9 if st["span_s"] else 0.0,
+                            "p50_ms": st["p50_s"] * 1e3, "p99_ms": st["p99_s"] * 1e3, "max_ms": st["max_s"] * 1e3,
+                            "requests": st["requests"], "launches": st["launches"]})
+            print(json.dumps(results[-1]), file=sys.stderr, flush=True)
+    finally:
+        _lib.bf_server_destroy(srv)
+        for f in filters:
+            f.close()
+    best = max(results, key=lambda r: r["sustained_gkeys_s"])
+    line = {
+        "metric": "serving: sustained G lookups/s and p50/p99 latency (64 filters, Poisson requests)",
+        "value": best["sustained_gkeys_s"], "unit": "G keys/s", "n_gpus": 1, "higher_is_better": True,
+        "data": "synthetic", "dtype": "u64 keys / u32 words (integer)",
+        "config": {"workload": "serving", "filters": nf, "sizes": "log-uniform 1 MiB-2 GiB (seed 6)",
+                   "filter_bytes": int(blocks.sum()) * bb, "request_keys": "log-uniform 1K-16M",
+                   "arena_keys": 1 << 28, "seconds_per_load": args.serve_seconds,
+                   "path": "pinned host keys -> device arena -> one batched launch per admission round -> host"},
+        "loads": results,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="4GiB", choices=sorted(WORKLOADS) + ["batched"])
+    ap.add_argument("--workload", default="4GiB", choices=sorted(WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--frontier", action="store_true")
     ap.add_argument("--sweep-keys", type=int, default=1 << 28)
@@ -710,6 +779,12 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.frontier:
         run_frontier(args)
+        return
+    if args.workload == "serving":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "no CPU arm for the serving workload"}))
+        else:
+            run_serving(args)
         return
     if args.workload == "batched":
         if args.impl == "reference":

@@ -61,7 +61,8 @@ typedef enum {
     BF_EINVAL = 1,         /* bad argument: null pointer, misalignment, bad geometry */
     BF_ENOMEM = 2,         /* device or pinned-host allocation failed */
     BF_ECUDA = 3,          /* a CUDA call failed; see bf_last_error() */
-    BF_EUNSUPPORTED = 4    /* valid by the definition, but not compiled into this build */
+    BF_EUNSUPPORTED = 4,   /* valid by the definition, but not compiled into this build */
+    BF_ETIMEDOUT = 5       /* a wait ran out of time (bf_server_wait) */
 } bf_status;
 
 /* Filter geometry (Sec. II-A).  num_blocks = b >= 1; block_bits = B in
@@ -275,6 +276,48 @@ bf_status bf_batch_add(bf_batch* b, const uint64_t* d_keys, bf_stream_t stream);
 bf_status bf_batch_contains(const bf_batch* b, const uint64_t* d_keys, uint8_t* d_out, bf_stream_t stream);
 /* Number of filters, and the length the key / result arrays must have. */
 bf_status bf_batch_info(const bf_batch* b, uint32_t* nfilters, uint64_t* total_keys);
+
+/* Lookup server (an extension of the bulk lookup to request traffic): many
+   device-resident filters of one geometry (sectorized), lookup requests
+   (filter, host keys, host results) arriving over time.  A worker thread
+   admits pending requests in arrival order while a device key arena of
+   arena_keys slots (and the per-launch request limit) has room, copies their
+   keys in, runs one batched lookup launch over all of them (across filters),
+   copies each request's results back, and frees the arena in completion
+   order; up to three launches are in flight.  Answers are those of
+   bf_contains on the request's filter.  Host buffers must stay valid until
+   the request completes; pinned memory makes the copies asynchronous.
+   bf_server_create allocates the arena (9 bytes per slot) and a stream and
+   starts the worker; bf_server_destroy completes in-flight work and stops it. */
+typedef struct bf_server bf_server;
+typedef struct {
+    uint64_t requests;     /* completed since the last reset */
+    uint64_t keys;
+    uint64_t launches;
+    double p50_s, p99_s, mean_s, max_s;  /* request latency: submit -> results on the host */
+    double span_s;         /* first submit -> last completion */
+    double offered_s;      /* bf_server_run_poisson: the arrival window */
+} bf_server_stats;
+bf_status bf_server_create(const bf_params* params, const bf_batch_filter* filters /* d_words, num_blocks */,
+                           uint32_t nfilters, uint64_t arena_keys, uint32_t max_requests_per_launch,
+                           bf_server** out);
+bf_status bf_server_destroy(bf_server* s);
+/* Queue a lookup of n keys of filter `filter` (n <= arena_keys); *ticket identifies it. */
+bf_status bf_server_submit(bf_server* s, uint32_t filter, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
+                           uint64_t* ticket);
+/* Block until the request is complete (BF_OK, its latency in *latency_s if not NULL),
+   timeout_s passes (BF_ETIMEDOUT) or a CUDA error occurred (BF_ECUDA).  A completed
+   ticket is forgotten. */
+bf_status bf_server_wait(bf_server* s, uint64_t ticket, double timeout_s, double* latency_s);
+/* Counters and latency percentiles of the requests completed since the last reset. */
+bf_status bf_server_get_stats(bf_server* s, int reset, bf_server_stats* out);
+/* Load generator: for duration_s seconds, requests arrive as a Poisson process of
+   rate_per_s; each picks a filter uniformly and log-uniform(min_keys, max_keys) keys,
+   taken as consecutive runs of the pinned host pool h_key_pool (results to the same
+   runs of h_out_pool); waits for all, then reports their statistics (SplitMix64 seed). */
+bf_status bf_server_run_poisson(bf_server* s, double rate_per_s, double duration_s, uint64_t min_keys,
+                                uint64_t max_keys, const uint64_t* h_key_pool, uint64_t pool_keys,
+                                uint8_t* h_out_pool, uint64_t seed, bf_server_stats* out);
 
 /* Construction that allocates nothing (the paper has no counterpart: this is
    an interface for callers of this library).  Some callers cannot let a

@@ -13,7 +13,7 @@ import os
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_build", "libbloomgb.so")
 
-BF_OK, BF_EINVAL, BF_ENOMEM, BF_ECUDA, BF_EUNSUPPORTED = range(5)
+BF_OK, BF_EINVAL, BF_ENOMEM, BF_ECUDA, BF_EUNSUPPORTED, BF_ETIMEDOUT = range(6)
 BF_OP_ADD, BF_OP_CONTAINS = 0, 1
 BF_HINT_FILTER_EVICT_LAST = 1 << 0
 BF_HINT_KEYS_EVICT_NORMAL = 1 << 1
@@ -27,7 +27,8 @@ EXPORTED = (
     "bf_get_params", "bf_set_layout", "bf_get_layout", "bf_set_l2_persist", "bf_gups",
     "bf_set_partition", "bf_get_partition", "bf_last_launches", "bf_add_noalloc", "bf_batch_create",
     "bf_batch_destroy", "bf_batch_set_layout", "bf_batch_get_layout", "bf_batch_add", "bf_batch_contains",
-    "bf_batch_info", "bf_status_str", "bf_last_error", "bf_version",
+    "bf_batch_info", "bf_server_create", "bf_server_destroy", "bf_server_submit", "bf_server_wait",
+    "bf_server_get_stats", "bf_server_run_poisson", "bf_status_str", "bf_last_error", "bf_version",
 )
 
 
@@ -37,7 +38,7 @@ class BloomError(RuntimeError):
         self.status = status
 
 
-_STATUS = {0: "BF_OK", 1: "BF_EINVAL", 2: "BF_ENOMEM", 3: "BF_ECUDA", 4: "BF_EUNSUPPORTED"}
+_STATUS = {0: "BF_OK", 1: "BF_EINVAL", 2: "BF_ENOMEM", 3: "BF_ECUDA", 4: "BF_EUNSUPPORTED", 5: "BF_ETIMEDOUT"}
 
 
 class bf_params(ctypes.Structure):
@@ -62,6 +63,15 @@ class bf_partition(ctypes.Structure):
 class bf_batch_filter(ctypes.Structure):
     _fields_ = [("d_words", ctypes.c_void_p), ("num_blocks", ctypes.c_uint64),
                 ("key_offset", ctypes.c_uint64), ("key_count", ctypes.c_uint64)]
+
+
+class bf_server_stats_t(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("keys", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double), ("mean_s", ctypes.c_double),
+                ("max_s", ctypes.c_double), ("span_s", ctypes.c_double), ("offered_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class bf_layout(ctypes.Structure):
@@ -114,6 +124,13 @@ def lib():
         "bf_batch_add": (i32, [vp, vp, vp]),
         "bf_batch_contains": (i32, [vp, vp, vp, vp]),
         "bf_batch_info": (i32, [vp, ctypes.POINTER(u32), ctypes.POINTER(u64)]),
+        "bf_server_create": (i32, [P, ctypes.POINTER(bf_batch_filter), u32, u64, u32, ctypes.POINTER(vp)]),
+        "bf_server_destroy": (i32, [vp]),
+        "bf_server_submit": (i32, [vp, u32, vp, u64, vp, ctypes.POINTER(u64)]),
+        "bf_server_wait": (i32, [vp, u64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+        "bf_server_get_stats": (i32, [vp, i32, ctypes.POINTER(bf_server_stats_t)]),
+        "bf_server_run_poisson": (i32, [vp, ctypes.c_double, ctypes.c_double, u64, u64, vp, u64, vp, u64,
+                                        ctypes.POINTER(bf_server_stats_t)]),
         "bf_status_str": (ctypes.c_char_p, [i32]),
         "bf_last_error": (ctypes.c_char_p, []),
         "bf_version": (ctypes.c_char_p, []),
@@ -280,3 +297,42 @@ def bf_batch_info(b: int) -> tuple[int, int]:
     n, k = ctypes.c_uint32(), ctypes.c_uint64()
     _check(lib().bf_batch_info(b, ctypes.byref(n), ctypes.byref(k)), "bf_batch_info")
     return n.value, k.value
+
+
+def bf_server_create(p: bf_params, filters, arena_keys: int, max_requests_per_launch: int = 4096) -> int:
+    """filters: sequence of (d_words, num_blocks)."""
+    arr = (bf_batch_filter * len(filters))(*[bf_batch_filter(w, nb, 0, 0) for w, nb in filters])
+    h = ctypes.c_void_p()
+    _check(lib().bf_server_create(ctypes.byref(p), arr, len(filters), arena_keys, max_requests_per_launch,
+                                  ctypes.byref(h)), "bf_server_create")
+    return h.value
+
+
+def bf_server_destroy(s: int) -> None:
+    _check(lib().bf_server_destroy(s), "bf_server_destroy")
+
+
+def bf_server_submit(s: int, filt: int, h_keys: int, n: int, h_out: int) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().bf_server_submit(s, filt, h_keys, n, h_out, ctypes.byref(t)), "bf_server_submit")
+    return t.value
+
+
+def bf_server_wait(s: int, ticket: int, timeout_s: float = 60.0) -> float:
+    lat = ctypes.c_double()
+    _check(lib().bf_server_wait(s, ticket, timeout_s, ctypes.byref(lat)), "bf_server_wait")
+    return lat.value
+
+
+def bf_server_get_stats(s: int, reset: bool = False) -> dict:
+    out = bf_server_stats_t()
+    _check(lib().bf_server_get_stats(s, int(reset), ctypes.byref(out)), "bf_server_get_stats")
+    return out.as_dict()
+
+
+def bf_server_run_poisson(s: int, rate_per_s: float, duration_s: float, min_keys: int, max_keys: int,
+                          h_key_pool: int, pool_keys: int, h_out_pool: int, seed: int = 1) -> dict:
+    out = bf_server_stats_t()
+    _check(lib().bf_server_run_poisson(s, rate_per_s, duration_s, min_keys, max_keys, h_key_pool, pool_keys,
+                                       h_out_pool, seed, ctypes.byref(out)), "bf_server_run_poisson")
+    return out.as_dict()

@@ -38,7 +38,8 @@ def _flags():
 def _units():
     units = [("bf_api", os.path.join(CSRC, "bf_api.cu"), []),
              ("gups", os.path.join(CSRC, "gups.cu"), []),
-             ("sbf_expand", os.path.join(CSRC, "sbf_expand.cu"), [])]
+             ("sbf_expand", os.path.join(CSRC, "sbf_expand.cu"), []),
+             ("bf_server", os.path.join(CSRC, "bf_server.cu"), [])]
     for b, s in GEOMETRIES:
         units.append((f"sbf_B{b}_S{s}", os.path.join(CSRC, "sbf_geom.cu"), [f"-DSBF_B={b}", f"-DSBF_S={s}"]))
     return units

@@ -132,6 +132,24 @@ bf_status resolve_grid(const void* fn, int device, uint32_t threads, uint32_t gr
   return BF_OK;
 }
 
+}  // namespace
+
+namespace bloomgb {
+const KernelEntry* find_kernel(int op, int block_bits, int word_bits, int k, int theta, int phi, int kpt, int z) {
+  for (const auto& e : registry().sbf)
+    if (e.op == op && e.B == block_bits && e.S == word_bits && e.K == k && e.theta == theta && e.phi == phi &&
+        e.kpt == kpt && e.z == z)
+      return &e;
+  return nullptr;
+}
+int kernel_resident_ctas(const void* fn, int threads, int device) {
+  int n = 0;
+  return resident_ctas(fn, threads, device, &n) == BF_OK ? n : 0;
+}
+}  // namespace bloomgb
+
+namespace {
+
 struct DeviceGuard {
   int prev = -1;
   bool ok = true;
@@ -860,6 +878,7 @@ const char* bf_status_str(bf_status s) {
     case BF_ENOMEM: return "BF_ENOMEM";
     case BF_ECUDA: return "BF_ECUDA";
     case BF_EUNSUPPORTED: return "BF_EUNSUPPORTED";
+    case BF_ETIMEDOUT: return "BF_ETIMEDOUT";
   }
   return "unknown status";
 }

@@ -139,6 +139,11 @@ struct GupsEntry {
   const void* fn;
 };
 
+// Lookup of a compiled kernel (implemented with the registry in bf_api.cu).
+const KernelEntry* find_kernel(int op, int block_bits, int word_bits, int k, int theta, int phi, int kpt, int z);
+// Resident CTAs per SM of a kernel at a CTA size (cached).
+int kernel_resident_ctas(const void* fn, int threads, int device);
+
 #define BLOOMGB_GEOMETRIES(X) \
   X(64, 32) X(128, 32) X(256, 32) X(512, 32) X(64, 64) X(128, 64) X(256, 64) X(512, 64) X(1024, 64)
 #define BLOOMGB_DECLARE(B, S) void register_B##B##_S##S(std::vector<KernelEntry>& v);
