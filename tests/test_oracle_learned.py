@@ -15,10 +15,11 @@ import pytest
 import synthkeys
 from oracle import learned as L
 from synthkeys import clustered
+from synthkeys.mlp_params import init_params
 
 
 def test_backward_matches_finite_differences():
-    p = L.init_params(3, scale=0.5)
+    p = init_params(3, scale=0.5)
     keys = synthkeys.splitmix64(5, 0, 48)
     y = (np.arange(48) % 3 == 0).astype(np.float64)
     _, g = L.forward_backward(p, keys, y, quant=False)
@@ -36,7 +37,7 @@ def test_backward_matches_finite_differences():
 
 
 def test_straight_through_gradient():
-    p = L.init_params(4)
+    p = init_params(4)
     keys = synthkeys.splitmix64(6, 0, 64)
     y = (np.arange(64) % 2).astype(np.float64)
     loss_q, gq = L.forward_backward(p, keys, y, quant=True)
@@ -50,7 +51,7 @@ def test_straight_through_gradient():
 
 
 def test_zero_network_loss_closed_form():
-    p = {k: np.zeros_like(v) for k, v in L.init_params(0).items()}
+    p = {k: np.zeros_like(v) for k, v in init_params(0).items()}
     p["b3"] = np.array([0.7], dtype=np.float32)
     keys = synthkeys.splitmix64(7, 0, 10)
     y = np.array([1, 0, 1, 1, 0, 0, 0, 1, 0, 1], dtype=np.float64)
@@ -63,7 +64,7 @@ def test_zero_network_loss_closed_form():
 
 
 def test_quantization_bounds():
-    p = L.init_params(8)
+    p = init_params(8)
     for k in ("W1", "W2", "W3"):
         q, s = L._qweights(p[k])
         assert np.abs(q).max() <= 127 and np.abs(q).max() == 127
@@ -77,7 +78,7 @@ def test_quantization_bounds():
 
 
 def test_integer_inference_brute_force():
-    p = L.init_params(10)
+    p = init_params(10)
     calib = synthkeys.splitmix64(11, 0, 500)
     m = L.quantize(p, calib)
     keys = synthkeys.splitmix64(12, 0, 20)
@@ -97,7 +98,7 @@ def test_integer_inference_brute_force():
 
 
 def test_integer_scores_track_the_float_network():
-    p = L.init_params(13, scale=0.4)
+    p = init_params(13, scale=0.4)
     calib = synthkeys.splitmix64(14, 0, 4000)
     m = L.quantize(p, calib)
     keys = calib[:1000]
