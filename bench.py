@@ -759,13 +759,234 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+LEARNED_DESC = ("learned prefilter: 64M member keys from 10k clustered intervals (32 clusters, log-normal widths); "
+                "network 64->128->64->1 over the key bits, int8 weights, trained on 2M members + 2M non-members "
+                "(half uniform, half within 2x an interval's width of one); backup SBF 256-bit blocks, S=32, K=8; "
+                "10 bits/key for learned (model + backup) and plain SBF alike; lookups: 64M members + 64M non-members")
+
+
+def learned_data(n_members=1 << 26, n_train=1 << 21, n_query_non=1 << 26, n_val=1 << 21, seed=17):
+    """Host arrays of the learned-prefilter workload (seeded; see synthkeys.clustered)."""
+    import numpy as np
+    from synthkeys import clustered
+    s, w = clustered.intervals(n_intervals=10_000, n_clusters=32, seed=seed)
+    mem = clustered.members(n_members + n_members // 50, s, w, seed=seed + 1)
+    rng = np.random.default_rng(seed + 2)
+    mem = rng.permutation(mem)[:n_members]
+    tr_non, _ = clustered.non_members(n_train, s, w, seed=seed + 3)
+    val_non, val_near = clustered.non_members(n_val, s, w, seed=seed + 4)
+    q_non, q_near = clustered.non_members(n_query_non, s, w, seed=seed + 5)
+    return {"members": mem, "train_non": tr_non, "val_non": val_non, "val_near": val_near,
+            "query_non": q_non, "query_near": q_near, "n_intervals": int(s.size)}
+
+
+def run_learned(args):
+    """Learned prefilter vs the plain filter at equal bits/key: train, export,
+    pick tau on a validation set, build, then time lookups (model + backup)."""
+    import numpy as np
+    import torch
+    from paper_2512_15595_gb300 import Filter, learned as LB
+    from synthkeys.mlp_params import flatten, init_params
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    t_gen = time.perf_counter()
+    d = learned_data()
+    t_gen = time.perf_counter() - t_gen
+    n_mem = d["members"].size
+    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(device)
+    members = to_dev(d["members"])
+    n_tr = d["train_non"].size
+    train_keys = to_dev(np.concatenate([d["members"][:n_tr], d["train_non"]]))
+    train_labels = torch.cat([torch.ones(n_tr), torch.zeros(n_tr)]).to(device)
+    # training
+    batch, steps = 4096, args.train_steps
+    tr = LB.Trainer(flatten(init_params(1, scale=1.0)), batch=batch, device=device)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = tr.train(train_keys, train_labels, steps, lr=2e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    model = LB.IntModel(tr.export(train_keys), device=device)
+    bits = 10 * n_mem
+    B, S, K = 256, 32, 8
+    plain_blocks = bits // B
+    backup_blocks = (bits - LB.model_bits()) // B
+    # tau on the validation set: candidates at quantiles of the non-member scores
+    val = to_dev(d["val_non"])
+    val_scores = model.scores(val).cpu().numpy()
+    cands = sorted(set(int(x) for x in np.quantile(val_scores, [0.5, 0.8, 0.9, 0.95, 0.99, 0.999])) |
+                   {int(val_scores.max()) + 1})
+    curve = []
+    best = None
+    for tau in cands:
+        lf = LB.LearnedFilter(model, tau, members, backup_blocks, B, S, K, 0)
+        fp = lf.contains(val).float().mean().item()
+        curve.append({"tau": tau, "backup_keys": lf.n_backup, "val_fpr": fp})
+        if best is None or fp < best[1]:
+            best = (tau, fp)
+        lf.backup.close()
+    tau = best[0]
+    lf = LB.LearnedFilter(model, tau, members, backup_blocks, B, S, K, 0)
+    plain = Filter(plain_blocks, B, S, K, 0, device=device)
+    plain.add(members)
+    # query set: all members, then the non-member query set
+    qn = to_dev(d["query_non"])
+    queries = torch.cat([members, qn])
+    near = torch.from_numpy(d["query_near"]).to(device).bool()
+    out = torch.empty(queries.numel(), dtype=torch.bool, device=device)
+    pout = torch.empty_like(out)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts), ts
+
+    scores = torch.empty(queries.numel(), dtype=torch.int32, device=device)
+    score_ms, _ = timed(lambda: model.scores(queries, scores), max(3, args.steps))
+    plain_ms, _ = timed(lambda: plain.contains(queries, out=pout), max(3, args.steps))
+    props = torch.cuda.get_device_properties(device)
+    sampler = ClockSampler(0, getattr(props, "uuid", None) and f"GPU-{props.uuid}")
+    torch.cuda.synchronize()
+    sampler.start()
+    look_ms, all_ms = timed(lambda: lf.contains(queries, out=out), args.steps)
+    clocks = sampler.stop()
+    launches_per_lookup = lf.backup.last_launches() + 1  # backup filter lookup + the model kernel
+    model.check()
+    nq = queries.numel()
+    o = out.cpu().numpy()
+    po = pout.cpu().numpy()
+    nr = d["query_near"].astype(bool)
+    fn_learned = int((~o[:n_mem]).sum())
+    fn_plain = int((~po[:n_mem]).sum())
+    ln, pn = o[n_mem:], po[n_mem:]
+    fpr = {"bits_per_key": 10.0, "model_bits": LB.model_bits(), "tau": tau, "backup_keys": lf.n_backup,
+           "learned": {"all": float(ln.mean()), "uniform": float(ln[~nr].mean()), "near": float(ln[nr].mean())},
+           "plain": {"all": float(pn.mean()), "uniform": float(pn[~nr].mean()), "near": float(pn[nr].mean())},
+           "false_negatives": {"learned": fn_learned, "plain": fn_plain}, "tau_curve": curve,
+           "non_member_queries": int(ln.size)}
+    # roofline of the model kernel: 2 * (64*128 + 128*64 + 64) algorithmic flops per key (tensor engine)
+    flops_key = 2 * (64 * 128 + 128 * 64 + 64)
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    with open(pk_path) as f:
+        pk = json.load(f)
+    tf = flops_key * nq / (score_ms * 1e-3) / 1e12
+    engine = "tensor (tcgen05 kind::f16, bf16 operands, fp32 accumulate; exact)" \
+        if model.engine == LB.BF_MLP_ENGINE_TENSOR else "dp4a (CUDA cores)"
+    roof = {"bound": "tensor", "achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": tf / pk["bf16_tflops"], "traffic": None, "kernel": f"bf_mlp_scores: {engine}",
+            "per": "one call", "peak_source": "measured bf16 dense burst (MEASURED_PEAKS.json)",
+            "algorithmic_flops_per_key": flops_key, "keys_per_call": nq, "ms_per_call": score_ms}
+    e2e = None
+    if not args.no_e2e:
+        e2e = learned_e2e(torch, lf, queries, args)
+    line = {
+        "metric": "learned prefilter: G lookups/s (model + backup) and FPR vs plain SBF at equal bits/key",
+        "value": nq / (look_ms * 1e-3) / 1e9, "unit": "G keys/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": look_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8 model (exact, bf16 MMA) / u32 words", "data": "synthetic",
+        "config": {"workload": "learned", "desc": LEARNED_DESC, "members": n_mem, "queries": nq,
+                   "intervals": d["n_intervals"], "plain_blocks": plain_blocks, "backup_blocks": backup_blocks,
+                   "l2": "inputs larger than L2 (no flush)", "host_data_s": t_gen},
+        "plain_lookup_gkeys_s": nq / (plain_ms * 1e-3) / 1e9, "model_scores_gkeys_s": nq / (score_ms * 1e-3) / 1e9,
+        "training": {"steps": steps, "batch": batch, "ms": train_ms, "ms_per_step": train_ms / steps,
+                     "first_loss": float(losses[:10].mean().item()), "last_loss": float(losses[-50:].mean().item())},
+        "engine": engine, "fpr": fpr, "roofline": roof, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": launches_per_lookup * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    lf.backup.close()
+    plain.close()
+    model.close()
+
+
+def learned_e2e(torch, lf, queries, args):
+    """Learned lookups from pinned host keys to a host result, chunked."""
+    n = queries.numel()
+    hk = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    hk.copy_(queries)
+    ho = torch.empty(n, dtype=torch.bool, pin_memory=True)
+    chunk = 1 << 24
+    dk = torch.empty(chunk, dtype=torch.int64, device=queries.device)
+    do = torch.empty(chunk, dtype=torch.bool, device=queries.device)
+
+    def go():
+        for lo in range(0, n, chunk):
+            c = min(chunk, n - lo)
+            dk[:c].copy_(hk[lo:lo + c], non_blocking=True)
+            lf.contains(dk[:c], out=do[:c])
+            ho[lo:lo + c].copy_(do[:c], non_blocking=True)
+        torch.cuda.synchronize()
+
+    go()
+    ts = []
+    for _ in range(max(1, args.steps // 2)):
+        t0 = time.perf_counter()
+        go()
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    return {"value": n / t / 1e9, "unit": "G keys/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": n,
+            "path": "pinned host keys -> device (16M-key chunks) -> bf_mlp_contains -> pinned host bytes"}
+
+
+def run_learned_reference(args):
+    """The oracle's integer model + backup lookups on a bounded sample (host cores)."""
+    import numpy as np
+    import oracle
+    from oracle import learned as OL
+    from synthkeys.mlp_params import init_params
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    d = learned_data(n_members=1 << 20, n_train=1 << 10, n_query_non=1 << 18, n_val=1 << 10)
+    m = OL.quantize(init_params(1, scale=1.0), d["members"][:4096])
+    sm = OL.int_scores(m, d["members"])
+    tau = int(np.quantile(sm, 0.5))
+    geom = oracle.Geometry(num_blocks=(10 * (1 << 26)) // 256, block_bits=256, word_bits=32, k=8, seed=0)
+    f = oracle.SBF(geom)
+    f.add(d["members"][sm < tau])
+    q = np.concatenate([d["members"][: 1 << 18], d["query_non"]])
+    vals = []
+    t_all = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        got = (OL.int_scores(m, q) >= tau) | (f.contains(q) != 0)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            vals.append(q.size / dt / 1e9)
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": "learned prefilter: G lookups/s (model + backup) and FPR vs plain SBF "
+            "at equal bits/key", "value": v, "unit": "G keys/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": q.size / v / 1e6, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64 numpy (integer model) / u32 words", "data": "synthetic",
+            "config": {"workload": "learned", "desc": LEARNED_DESC},
+            "cpu_baseline": {"value": v, "unit": "G keys/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{q.size:,} queries (2^18 members + 2^18 non-members) through the oracle's "
+                                       "integer model and its backup filter (full-size geometry), per step"},
+            "e2e": {"value": v, "unit": "G keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "positives": int(got.sum())}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="4GiB", choices=sorted(WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--workload", default="4GiB", choices=sorted(WORKLOADS) + ["batched", "serving", "learned"])
+    ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--frontier", action="store_true")
@@ -785,6 +1006,12 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "no CPU arm for the serving workload"}))
         else:
             run_serving(args)
+        return
+    if args.workload == "learned":
+        if args.impl == "reference":
+            run_learned_reference(args)
+        else:
+            run_learned(args)
         return
     if args.workload == "batched":
         if args.impl == "reference":

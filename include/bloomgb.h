@@ -343,6 +343,111 @@ bf_status bf_server_run_poisson(bf_server* s, double rate_per_s, double duration
 bf_status bf_add_noalloc(const bf_params* params, void* d_words, const uint64_t* d_keys, uint64_t n,
                          uint64_t* max_keys, bf_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+   Learned prefilter (an extension beside the paper's filters; the paper has no
+   learned component).  A small network over the 64 bits of a key -- inputs
+   x_i = (key >> i) & 1, layers 64 -> 128 -> 64 -> 1 with ReLU -- scores keys;
+   a key is reported present when its score reaches the threshold tau or when
+   a backup blocked filter (bf_create / bf_add), which holds the members the
+   network scores below tau, contains it.  No false negatives by
+   construction.
+   Training is in fp32 on the GPU (mean binary cross-entropy of the logit,
+   Adam), with the three weight matrices fake-quantized in the forward pass:
+   W -> s * clamp(round(W / s), -127, 127), s = max|W| / 127, rounding half
+   away from zero, the quotient and rounding taken in fp64; the gradient
+   passes straight through the rounding.
+   Parameter vector (BF_MLP_PARAMS fp32 values, device memory, caller-owned):
+   W1 [64][128] row-major (input-major), b1 [128], W2 [128][64], b2 [64],
+   W3 [64], b3.
+   The exported integer model computes exactly:
+     a1 = x . W1q + b1q,   h1 = min(max(a1, 0) >> sh1, 127)
+     a2 = h1 . W2q + b2q,  h2 = min(max(a2, 0) >> sh2, 127)
+     score = h2 . W3q + b3q, saturated to int32
+   with int8 weights Wq = clamp(round(W / s)), biases rounded to the units of
+   their layer's accumulator (s1; s1 2^sh1 s2; s1 2^sh1 s2 2^sh2 s3) and
+   saturated to int32, and sh1 / sh2 the smallest shifts that bring the
+   largest max(a, 0) of their layer over the calibration keys to <= 127.
+   ------------------------------------------------------------------------- */
+#define BF_MLP_PARAMS 16641
+
+typedef struct {
+    int8_t w1[64 * 128]; /* W1q[i][j] at i * 128 + j */
+    int8_t w2[128 * 64]; /* W2q[i][j] at i * 64 + j */
+    int8_t w3[64];
+    int32_t b1[128];
+    int32_t b2[64];
+    int32_t b3;
+    int32_t sh1, sh2;
+    double unit; /* value of one score unit in logit units */
+} bf_mlp_int8;
+
+typedef struct bf_mlp_model bf_mlp_model;
+
+/* Device workspace a training call needs for `batch` samples (bytes). */
+uint64_t bf_mlp_workspace_bytes(uint32_t batch);
+
+/* Gradient of the mean loss over one batch into d_grads (BF_MLP_PARAMS
+   floats) and the loss into *d_loss (if not NULL).  The training set is
+   d_keys / d_labels (n <= 2^32 - 1 entries, labels 0.0 or 1.0); sample i of
+   the batch is element ((first + i) mod n) * mult mod n, so with mult coprime
+   to n (1 <= mult < 2^32; else BF_EINVAL) n consecutive samples visit every
+   element once.  d_ws: bf_mlp_workspace_bytes(batch) bytes, 256-byte aligned. */
+bf_status bf_mlp_grad(const float* d_params, const uint64_t* d_keys, const float* d_labels, uint64_t n,
+                      uint64_t first, uint64_t mult, uint32_t batch, float* d_grads, float* d_loss, void* d_ws,
+                      uint64_t ws_bytes, bf_stream_t stream);
+
+/* One Adam step (step >= 1 counts from 1):  m = b1 m + (1-b1) g,
+   v = b2 v + (1-b2) g^2,  p -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps). */
+bf_status bf_mlp_adam(float* d_params, const float* d_grads, float* d_m, float* d_v, uint32_t step, float lr,
+                      float beta1, float beta2, float eps, bf_stream_t stream);
+
+/* `steps` training steps (gradient + Adam) numbered first_step, first_step+1,
+   ...; step t uses the batch that starts at sample (t-1)*batch.  Per-step
+   losses into d_loss[0..steps) if not NULL.  Enqueued only. */
+bf_status bf_mlp_train(float* d_params, float* d_m, float* d_v, const uint64_t* d_keys, const float* d_labels,
+                       uint64_t n, uint64_t mult, uint32_t batch, uint32_t first_step, uint32_t steps, float lr,
+                       float beta1, float beta2, float eps, float* d_loss, void* d_ws, uint64_t ws_bytes,
+                       bf_stream_t stream);
+
+/* Export the host parameter vector h_params to the integer model *out,
+   calibrating the shifts on the device keys d_calib[0..n_calib).
+   Synchronizes `stream`. */
+bf_status bf_mlp_export(const float* h_params, const uint64_t* d_calib, uint64_t n_calib, bf_mlp_int8* out,
+                        bf_stream_t stream);
+
+/* Copy an integer model to the current device (BF_EINVAL for shifts outside 0..62). */
+bf_status bf_mlp_load(const bf_mlp_int8* m, bf_mlp_model** out);
+bf_status bf_mlp_free(bf_mlp_model* m);
+
+/* Engines of the integer model.  TENSOR: tcgen05 MMAs in bf16 with fp32
+   accumulation on values for which that arithmetic is exact (models whose
+   shifts sh1, sh2 are <= 15); DP4A: CUDA-core int8 dot products.  Both give
+   the integer model's results bit for bit.  AUTO (default) takes TENSOR when
+   the model allows it. */
+#define BF_MLP_ENGINE_AUTO 0
+#define BF_MLP_ENGINE_TENSOR 1
+#define BF_MLP_ENGINE_DP4A 2
+/* BF_EUNSUPPORTED when TENSOR is asked of a model that does not allow it. */
+bf_status bf_mlp_set_engine(bf_mlp_model* m, int engine);
+/* The engine lookups of this model use (TENSOR or DP4A). */
+bf_status bf_mlp_get_engine(const bf_mlp_model* m, int* engine);
+/* Synchronizes the device; BF_ETIMEDOUT if a bounded wait of a tensor-core
+   launch of this model ran out (its results are then incomplete). */
+bf_status bf_mlp_check(const bf_mlp_model* m);
+
+/* Integer scores of n device keys into d_scores (int32). */
+bf_status bf_mlp_scores(const bf_mlp_model* m, const uint64_t* d_keys, uint64_t n, int32_t* d_scores,
+                        bf_stream_t stream);
+
+/* Compaction: the keys whose score is below tau, in no particular order, into
+   d_out_keys (room for n keys), their number into *d_count (device). */
+bf_status bf_mlp_select_below(const bf_mlp_model* m, int32_t tau, const uint64_t* d_keys, uint64_t n,
+                              uint64_t* d_out_keys, uint64_t* d_count, bf_stream_t stream);
+
+/* Learned-filter lookup: d_out[i] = (score(key_i) >= tau) || backup contains key_i. */
+bf_status bf_mlp_contains(const bf_mlp_model* m, int32_t tau, const bf_filter* backup, const uint64_t* d_keys,
+                          uint64_t n, uint8_t* d_out, bf_stream_t stream);
+
 const char* bf_status_str(bf_status s);
 
 /* Message of the last error on the calling host thread ("" if none). */

@@ -4,7 +4,7 @@ Network: the 64 bits of a key (bit i = (key >> i) & 1, as 0/1 features) ->
 128 ReLU units -> 64 ReLU units -> 1 logit.  Parameters: W1 [64][128],
 b1 [128], W2 [128][64], b2 [64], W3 [64], b3 (scalar).
 
-Training (fp64 here): weights are fake-quantized per layer, W_q = s * round(W / s)
+Training (fp64 here; Adam updates): weights are fake-quantized per layer, W_q = s * round(W / s)
 with s = max|W| / 127 (round half away from zero, clamp to +-127), and the
 gradient passes straight through the rounding (w.r.t. the float weights it
 equals the gradient w.r.t. W_q).  Loss: mean binary cross-entropy with logits.
@@ -72,6 +72,19 @@ def forward_backward(params: dict, keys, labels, quant: bool = True):
     g["W1"] = X.T @ dZ1
     g["b1"] = dZ1.sum(axis=0)
     return loss, g
+
+
+def adam_step(p, g, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """One Adam update (Kingma and Ba, 2015, Algorithm 1) in fp64: returns (p, m, v).
+
+    m and v are exponential moving averages of the gradient and its square;
+    they are divided by (1 - beta^t) to undo their bias toward zero."""
+    p, g, m, v = (np.asarray(a, dtype=np.float64) for a in (p, g, m, v))
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
 
 
 # ---------------------------------------------------------------------------

@@ -28,8 +28,13 @@ EXPORTED = (
     "bf_set_partition", "bf_get_partition", "bf_last_launches", "bf_add_noalloc", "bf_batch_create",
     "bf_batch_destroy", "bf_batch_set_layout", "bf_batch_get_layout", "bf_batch_add", "bf_batch_contains",
     "bf_batch_info", "bf_server_create", "bf_server_destroy", "bf_server_submit", "bf_server_wait",
-    "bf_server_get_stats", "bf_server_run_poisson", "bf_status_str", "bf_last_error", "bf_version",
+    "bf_server_get_stats", "bf_server_run_poisson", "bf_mlp_workspace_bytes", "bf_mlp_grad", "bf_mlp_adam",
+    "bf_mlp_train", "bf_mlp_export", "bf_mlp_load", "bf_mlp_free", "bf_mlp_scores", "bf_mlp_select_below",
+    "bf_mlp_contains", "bf_mlp_set_engine", "bf_mlp_get_engine", "bf_mlp_check", "bf_status_str", "bf_last_error", "bf_version",
 )
+
+BF_MLP_PARAMS = 16641
+BF_MLP_ENGINE_AUTO, BF_MLP_ENGINE_TENSOR, BF_MLP_ENGINE_DP4A = 0, 1, 2
 
 
 class BloomError(RuntimeError):
@@ -83,6 +88,12 @@ class bf_layout(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class bf_mlp_int8(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_int8 * (64 * 128)), ("w2", ctypes.c_int8 * (128 * 64)), ("w3", ctypes.c_int8 * 64),
+                ("b1", ctypes.c_int32 * 128), ("b2", ctypes.c_int32 * 64), ("b3", ctypes.c_int32),
+                ("sh1", ctypes.c_int32), ("sh2", ctypes.c_int32), ("unit", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -131,6 +142,21 @@ def lib():
         "bf_server_get_stats": (i32, [vp, i32, ctypes.POINTER(bf_server_stats_t)]),
         "bf_server_run_poisson": (i32, [vp, ctypes.c_double, ctypes.c_double, u64, u64, vp, u64, vp, u64,
                                         ctypes.POINTER(bf_server_stats_t)]),
+        "bf_mlp_workspace_bytes": (u64, [u32]),
+        "bf_mlp_grad": (i32, [vp, vp, vp, u64, u64, u64, u32, vp, vp, vp, u64, vp]),
+        "bf_mlp_adam": (i32, [vp, vp, vp, vp, u32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, vp]),
+        "bf_mlp_train": (i32, [vp, vp, vp, vp, vp, u64, u64, u32, u32, u32, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, ctypes.c_float, vp, vp, u64, vp]),
+        "bf_mlp_export": (i32, [vp, vp, u64, ctypes.POINTER(bf_mlp_int8), vp]),
+        "bf_mlp_load": (i32, [ctypes.POINTER(bf_mlp_int8), ctypes.POINTER(vp)]),
+        "bf_mlp_free": (i32, [vp]),
+        "bf_mlp_scores": (i32, [vp, vp, u64, vp, vp]),
+        "bf_mlp_select_below": (i32, [vp, i32, vp, u64, vp, vp, vp]),
+        "bf_mlp_contains": (i32, [vp, i32, vp, vp, u64, vp, vp]),
+        "bf_mlp_set_engine": (i32, [vp, i32]),
+        "bf_mlp_get_engine": (i32, [vp, ctypes.POINTER(i32)]),
+        "bf_mlp_check": (i32, [vp]),
         "bf_status_str": (ctypes.c_char_p, [i32]),
         "bf_last_error": (ctypes.c_char_p, []),
         "bf_version": (ctypes.c_char_p, []),
@@ -336,3 +362,69 @@ def bf_server_run_poisson(s: int, rate_per_s: float, duration_s: float, min_keys
     _check(lib().bf_server_run_poisson(s, rate_per_s, duration_s, min_keys, max_keys, h_key_pool, pool_keys,
                                        h_out_pool, seed, ctypes.byref(out)), "bf_server_run_poisson")
     return out.as_dict()
+
+
+def bf_mlp_workspace_bytes(batch: int) -> int:
+    return lib().bf_mlp_workspace_bytes(batch)
+
+
+def bf_mlp_grad(d_params: int, d_keys: int, d_labels: int, n: int, first: int, mult: int, batch: int,
+                d_grads: int, d_loss: int | None, d_ws: int, ws_bytes: int, stream=None) -> None:
+    _check(lib().bf_mlp_grad(d_params, d_keys, d_labels, n, first, mult, batch, d_grads, d_loss, d_ws, ws_bytes,
+                             _stream(stream)), "bf_mlp_grad")
+
+
+def bf_mlp_adam(d_params: int, d_grads: int, d_m: int, d_v: int, step: int, lr: float, beta1: float = 0.9,
+                beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
+    _check(lib().bf_mlp_adam(d_params, d_grads, d_m, d_v, step, lr, beta1, beta2, eps, _stream(stream)),
+           "bf_mlp_adam")
+
+
+def bf_mlp_train(d_params: int, d_m: int, d_v: int, d_keys: int, d_labels: int, n: int, mult: int, batch: int,
+                 first_step: int, steps: int, lr: float, beta1: float, beta2: float, eps: float,
+                 d_loss: int | None, d_ws: int, ws_bytes: int, stream=None) -> None:
+    _check(lib().bf_mlp_train(d_params, d_m, d_v, d_keys, d_labels, n, mult, batch, first_step, steps, lr, beta1,
+                              beta2, eps, d_loss, d_ws, ws_bytes, _stream(stream)), "bf_mlp_train")
+
+
+def bf_mlp_export(h_params: int, d_calib: int, n_calib: int, stream=None) -> bf_mlp_int8:
+    out = bf_mlp_int8()
+    _check(lib().bf_mlp_export(h_params, d_calib, n_calib, ctypes.byref(out), _stream(stream)), "bf_mlp_export")
+    return out
+
+
+def bf_mlp_load(m: bf_mlp_int8) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().bf_mlp_load(ctypes.byref(m), ctypes.byref(h)), "bf_mlp_load")
+    return h.value
+
+
+def bf_mlp_free(m: int) -> None:
+    _check(lib().bf_mlp_free(m), "bf_mlp_free")
+
+
+def bf_mlp_scores(m: int, d_keys: int, n: int, d_scores: int, stream=None) -> None:
+    _check(lib().bf_mlp_scores(m, d_keys, n, d_scores, _stream(stream)), "bf_mlp_scores")
+
+
+def bf_mlp_select_below(m: int, tau: int, d_keys: int, n: int, d_out_keys: int, d_count: int, stream=None) -> None:
+    _check(lib().bf_mlp_select_below(m, tau, d_keys, n, d_out_keys, d_count, _stream(stream)),
+           "bf_mlp_select_below")
+
+
+def bf_mlp_contains(m: int, tau: int, backup: int, d_keys: int, n: int, d_out: int, stream=None) -> None:
+    _check(lib().bf_mlp_contains(m, tau, backup, d_keys, n, d_out, _stream(stream)), "bf_mlp_contains")
+
+
+def bf_mlp_set_engine(m: int, engine: int) -> None:
+    _check(lib().bf_mlp_set_engine(m, engine), "bf_mlp_set_engine")
+
+
+def bf_mlp_get_engine(m: int) -> int:
+    e = ctypes.c_int()
+    _check(lib().bf_mlp_get_engine(m, ctypes.byref(e)), "bf_mlp_get_engine")
+    return e.value
+
+
+def bf_mlp_check(m: int) -> None:
+    _check(lib().bf_mlp_check(m), "bf_mlp_check")

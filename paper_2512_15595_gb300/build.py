@@ -39,7 +39,9 @@ def _units():
     units = [("bf_api", os.path.join(CSRC, "bf_api.cu"), []),
              ("gups", os.path.join(CSRC, "gups.cu"), []),
              ("sbf_expand", os.path.join(CSRC, "sbf_expand.cu"), []),
-             ("bf_server", os.path.join(CSRC, "bf_server.cu"), [])]
+             ("bf_server", os.path.join(CSRC, "bf_server.cu"), []),
+             ("lbf_kernels", os.path.join(CSRC, "lbf_kernels.cu"), []),
+             ("lbf_tc", os.path.join(CSRC, "lbf_tc.cu"), [])]
     for b, s in GEOMETRIES:
         units.append((f"sbf_B{b}_S{s}", os.path.join(CSRC, "sbf_geom.cu"), [f"-DSBF_B={b}", f"-DSBF_S={s}"]))
     return units

@@ -132,3 +132,52 @@ def test_csbf_params_and_layouts(L):
                 assert L.bf_layout_check(p, op, L.bf_layout(cg, 1, kpt, 256, 0, 0)) == L.BF_OK
     assert L.bf_layout_check(p, 0, L.bf_layout(8, 1, 1, 256, 0, 0)) == L.BF_EINVAL  # cg must divide groups
     assert L.bf_layout_check(p, 1, L.bf_layout(1, 2, 1, 256, 0, 0)) == L.BF_EINVAL  # phi must be 1
+
+
+def test_mlp_int8_struct_layout_matches_the_header(L, tmp_path):
+    """The ctypes mirror of bf_mlp_int8 has the C struct's size and offsets (gcc, host only)."""
+    import ctypes
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src = tmp_path / "lay.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "bloomgb.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bf_mlp_int8),'
+                   'offsetof(bf_mlp_int8,w2), offsetof(bf_mlp_int8,w3), offsetof(bf_mlp_int8,b1),'
+                   'offsetof(bf_mlp_int8,b2), offsetof(bf_mlp_int8,b3), offsetof(bf_mlp_int8,sh1),'
+                   'offsetof(bf_mlp_int8,sh2), offsetof(bf_mlp_int8,unit)); return 0;}\n')
+    exe = tmp_path / "lay"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    S = L.bf_mlp_int8
+    want = [ctypes.sizeof(S)] + [getattr(S, f).offset for f in ("w2", "w3", "b1", "b2", "b3", "sh1", "sh2", "unit")]
+    assert got == want
+
+
+def test_mlp_arguments_rejected_without_gpu(L):
+    lib = L.lib()
+    assert lib.bf_mlp_workspace_bytes(1024) >= 4 * (1024 * (2 * 128 + 2 * 64 + 2) + 2 * L.BF_MLP_PARAMS)
+    ws = lib.bf_mlp_workspace_bytes(64)
+    # null pointers, empty batch, unaligned workspace, n too large, multiplier not coprime to n
+    assert lib.bf_mlp_grad(None, 256, 256, 10, 0, 1, 64, 256, None, 256, ws, None) == L.BF_EINVAL
+    assert lib.bf_mlp_grad(256, 256, 256, 10, 0, 1, 0, 256, None, 256, ws, None) == L.BF_EINVAL
+    assert lib.bf_mlp_grad(256, 256, 256, 10, 0, 1, 64, 256, None, 128, ws, None) == L.BF_EINVAL
+    assert lib.bf_mlp_grad(256, 256, 256, 10, 0, 1, 64, 256, None, 256, ws - 4, None) == L.BF_EINVAL
+    assert lib.bf_mlp_grad(256, 256, 256, 1 << 32, 0, 1, 64, 256, None, 256, ws, None) == L.BF_EINVAL
+    assert lib.bf_mlp_grad(256, 256, 256, 10, 0, 4, 64, 256, None, 256, ws, None) == L.BF_EINVAL
+    assert lib.bf_mlp_grad(256, 256, 256, 10, 0, 0, 64, 256, None, 256, ws, None) == L.BF_EINVAL
+    assert lib.bf_mlp_train(256, 256, 256, 256, 256, 10, 3, 64, 0, 5, 1e-3, 0.9, 0.999, 1e-8, None, 256, ws,
+                            None) == L.BF_EINVAL
+    assert lib.bf_mlp_adam(256, 256, 256, 256, 0, 1e-3, 0.9, 0.999, 1e-8, None) == L.BF_EINVAL
+    assert lib.bf_mlp_load(None, None) == L.BF_EINVAL
+    bad = L.bf_mlp_int8()
+    bad.sh1 = 63
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.bf_mlp_load(ctypes.byref(bad), ctypes.byref(h)) == L.BF_EINVAL
+    assert lib.bf_mlp_free(None) == L.BF_EINVAL
+    assert lib.bf_mlp_scores(None, 256, 4, 256, None) == L.BF_EINVAL
+    assert lib.bf_mlp_contains(None, 0, None, 256, 4, 256, None) == L.BF_EINVAL
+    assert lib.bf_mlp_select_below(None, 0, 256, 4, 256, 256, None) == L.BF_EINVAL
+    assert lib.bf_mlp_export(None, None, 0, None, None) == L.BF_EINVAL

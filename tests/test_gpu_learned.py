@@ -1,0 +1,323 @@
+"""Learned prefilter on the GPU against the oracle.
+
+* one training gradient (fake-quantized forward, straight-through backward)
+  and the loss against the fp64 oracle, within a tolerance derived from fp32
+  accumulation; the batch's sample permutation reproduced on the host;
+* the Adam update against the oracle's, and the fused training loop against
+  gradient + Adam steps taken one by one (bit-exact: the same kernels);
+* one-step parity at several points of a training run (oracle fed the GPU's
+  fp32 parameters at each point);
+* export (int8 quantization + shift calibration) bit-exact against the
+  oracle's, including saturated biases;
+* integer scores bit-exact on ragged sizes, on models with saturating
+  accumulators, and for an oracle-made model loaded directly;
+* compaction of the members scored below tau (same set as the oracle's) and
+  the combined lookup (score >= tau or backup filter) element by element;
+  no member is ever rejected.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synthkeys
+from conftest import gpu_available
+from oracle import learned as OL
+from synthkeys import clustered
+from synthkeys.mlp_params import N_PARAMS, SHAPES, flatten, init_params, unflatten
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    from paper_2512_15595_gb300 import build
+    build.build()
+    return t
+
+
+@pytest.fixture(scope="module")
+def data():
+    s, w = clustered.intervals(n_intervals=400, n_clusters=8, seed=5)
+    mem = clustered.members(6000, s, w, seed=6)
+    non, _ = clustered.non_members(6000, s, w, seed=7)
+    keys = np.concatenate([mem, non])
+    labels = np.concatenate([np.ones(mem.size), np.zeros(non.size)]).astype(np.float32)
+    return mem, non, keys, labels
+
+
+def dev(torch, a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    return torch.from_numpy(a).cuda()
+
+
+def batch_indices(n, first, mult, batch):
+    return [((first + i) % n) * mult % n for i in range(batch)]
+
+
+# Tolerance of one fp32 gradient against fp64: every value is a sum of at
+# most a batch of products of fp32 terms computed through <= 3 layers of fp32
+# sums (64 or 128 terms); with unit roundoff 2^-24 the relative error of the
+# sums stays below ~1e-5 of the sum of magnitudes, itself within a small
+# factor of the largest gradient entry of each tensor.
+GRAD_TOL = 2e-5
+
+
+def compare_grads(g_dev, g_ref):
+    gd = unflatten(g_dev)
+    for k in g_ref:
+        ref = np.asarray(g_ref[k], dtype=np.float64).reshape(gd[k].shape)
+        scale = max(np.abs(ref).max(), 1e-30)
+        err = np.abs(gd[k].astype(np.float64) - ref).max()
+        assert err <= GRAD_TOL * scale, (k, err, scale)
+
+
+@pytest.mark.parametrize("batch,first,scale", [(512, 100, 1.0), (1000, 11_000, 0.5), (37, 0, 1.0)])
+def test_gradient_and_loss_match_oracle(torch, data, batch, first, scale):
+    from paper_2512_15595_gb300.learned import Trainer, coprime_multiplier
+    _, _, keys, labels = data
+    p = init_params(21 + batch, scale=scale)
+    n = keys.size
+    mult = coprime_multiplier(n)
+    t = Trainer(flatten(p), batch=batch)
+    g, loss = t.grad(dev(torch, keys), dev(torch, labels), first=first, mult=mult)
+    idx = batch_indices(n, first, mult, batch)
+    ref_loss, ref_g = OL.forward_backward(p, keys[idx], labels[idx].astype(np.float64), quant=True)
+    assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-5)
+    compare_grads(g.cpu().numpy(), ref_g)
+
+
+def test_adam_matches_oracle(torch):
+    from paper_2512_15595_gb300 import _lib
+    rng = np.random.default_rng(3)
+    p, g = rng.standard_normal(N_PARAMS).astype(np.float32), (rng.standard_normal(N_PARAMS) * 1e-2).astype(np.float32)
+    m, v = (rng.standard_normal(N_PARAMS) * 1e-3).astype(np.float32), (rng.random(N_PARAMS) * 1e-4).astype(np.float32)
+    dp, dg, dm, dv = (dev(torch, a) for a in (p, g, m, v))
+    _lib.bf_mlp_adam(dp.data_ptr(), dg.data_ptr(), dm.data_ptr(), dv.data_ptr(), 7, 1e-3, 0.9, 0.999, 1e-8)
+    # the kernel receives fp32 hyperparameters: the oracle takes the same values
+    f = lambda x: float(np.float32(x))
+    b1, b2 = f(0.9), f(0.999)
+    rp, rm, rv = OL.adam_step(p, g, m, v, 7, f(1e-3), b1, b2, f(1e-8))
+    torch.cuda.synchronize()
+    u = 2.0 ** -24
+    g64, m64, v64 = (x.astype(np.float64) for x in (g, m, v))
+    # fp32 rounding of each product and sum, relative to the magnitude of the terms
+    assert np.all(np.abs(dm.cpu().numpy() - rm) <= 4 * u * (np.abs(b1 * m64) + np.abs((1 - b1) * g64)))
+    assert np.all(np.abs(dv.cpu().numpy() - rv) <= 4 * u * (b2 * v64 + (1 - b2) * g64 * g64))
+    step = p.astype(np.float64) - rp
+    assert np.all(np.abs(dp.cpu().numpy() - rp) <= 1e-6 * np.abs(step) + 2 * u * np.abs(p))
+
+
+def test_fused_training_equals_step_by_step(torch, data):
+    from paper_2512_15595_gb300 import _lib
+    from paper_2512_15595_gb300.learned import Trainer
+    _, _, keys, labels = data
+    k, y = dev(torch, keys), dev(torch, labels)
+    a = Trainer(flatten(init_params(5, scale=1.0)), batch=256)
+    b = Trainer(flatten(init_params(5, scale=1.0)), batch=256)
+    losses = a.train(k, y, steps=6, lr=3e-3, mult=7)
+    ref_losses = []
+    for t in range(1, 7):
+        g, loss = b.grad(k, y, first=(t - 1) * 256 % keys.size, mult=7)
+        _lib.bf_mlp_adam(b.params.data_ptr(), g.data_ptr(), b.m.data_ptr(), b.v.data_ptr(), t, 3e-3)
+        ref_losses.append(float(loss.item()))
+    assert torch.equal(a.params, b.params)
+    # the loss is summed with atomics (order not fixed); the parameters do not depend on it
+    assert np.allclose(losses.cpu().numpy(), ref_losses, rtol=1e-6)
+
+
+def test_training_trajectory_one_step_parity(torch, data):
+    """At several points of a run: oracle gradient + Adam from the GPU's fp32 state."""
+    from paper_2512_15595_gb300.learned import Trainer, coprime_multiplier
+    _, _, keys, labels = data
+    n = keys.size
+    mult = coprime_multiplier(n)
+    t = Trainer(flatten(init_params(8, scale=1.0)), batch=512)
+    k, y = dev(torch, keys), dev(torch, labels)
+    first_loss = None
+    for stop in (1, 40, 120):
+        t.train(k, y, steps=stop - t.step, lr=2e-3, mult=mult)
+        p0, m0, v0 = (x.cpu().numpy() for x in (t.params, t.m, t.v))
+        step = t.step + 1
+        losses = t.train(k, y, steps=1, lr=2e-3, mult=mult)
+        idx = batch_indices(n, (step - 1) * 512 % n, mult, 512)
+        ref_loss, ref_g = OL.forward_backward(unflatten(p0), keys[idx], labels[idx].astype(np.float64), quant=True)
+        assert float(losses[0].item()) == pytest.approx(ref_loss, rel=1e-5)
+        g_flat = np.concatenate([np.asarray(ref_g[k_], dtype=np.float64).reshape(-1) for k_, _ in SHAPES])
+        f = lambda x: float(np.float32(x))
+        rp, _, _ = OL.adam_step(p0, g_flat, m0, v0, step, f(2e-3), f(0.9), f(0.999), f(1e-8))
+        moved = p0.astype(np.float64) - t.params.cpu().numpy()
+        want = p0.astype(np.float64) - rp
+        # Adam normalizes the step, so an element whose gradient is tiny next to
+        # its history is the most sensitive; compare against lr
+        assert np.abs(moved - want).max() <= 2e-3 * 1e-2, stop
+        first_loss = first_loss or ref_loss
+    assert ref_loss < first_loss  # it learns
+
+
+def make_int8(torch, m):
+    from paper_2512_15595_gb300._lib import bf_mlp_int8
+    out = bf_mlp_int8()
+    np.ctypeslib.as_array(out.w1)[:] = np.asarray(m["W1q"], dtype=np.int8).reshape(-1)
+    np.ctypeslib.as_array(out.w2)[:] = np.asarray(m["W2q"], dtype=np.int8).reshape(-1)
+    np.ctypeslib.as_array(out.w3)[:] = np.asarray(m["W3q"], dtype=np.int8)
+    np.ctypeslib.as_array(out.b1)[:] = np.asarray(m["b1q"], dtype=np.int32)
+    np.ctypeslib.as_array(out.b2)[:] = np.asarray(m["b2q"], dtype=np.int32)
+    out.b3, out.sh1, out.sh2, out.unit = int(m["b3q"]), int(m["sh1"]), int(m["sh2"]), float(m.get("unit", 1.0))
+    return out
+
+
+@pytest.mark.parametrize("seed,scale,ncal", [(30, 1.0, 5000), (31, 0.05, 3001), (32, 4.0, 1), (33, 1.0, 0)])
+def test_export_bit_exact(torch, data, seed, scale, ncal):
+    from paper_2512_15595_gb300.learned import Trainer, int_model_arrays
+    _, _, keys, _ = data
+    p = init_params(seed, scale=scale)
+    if seed == 32:
+        p["b3"][:] = 3.0e9  # saturates the int32 score bias
+        p["b1"][:5] = -1e6
+    calib = keys[:ncal]
+    t = Trainer(flatten(p), batch=64)
+    got = int_model_arrays(t.export(dev(torch, calib) if ncal else dev(torch, keys[:1])[:0]))
+    want = OL.quantize(p, calib)
+    for k_ in ("W1q", "b1q", "W2q", "b2q", "W3q"):
+        assert np.array_equal(got[k_], want[k_]), k_
+    for k_ in ("sh1", "sh2", "b3q"):
+        assert got[k_] == want[k_], (k_, got[k_], want[k_])
+    assert got["unit"] == want["unit"]
+
+
+def ragged_keys(n, seed):
+    return synthkeys.splitmix64(seed, 0, n)
+
+
+ENGINES = ["tensor", "dp4a"]
+
+
+def engine_id(name):
+    from paper_2512_15595_gb300.learned import BF_MLP_ENGINE_DP4A, BF_MLP_ENGINE_TENSOR
+    return BF_MLP_ENGINE_TENSOR if name == "tensor" else BF_MLP_ENGINE_DP4A
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("n", [0, 1, 127, 129, 511, 513, 100_003, 200_000])
+def test_scores_bit_exact_exported_model(torch, data, n, engine):
+    from paper_2512_15595_gb300.learned import IntModel, Trainer
+    _, _, keys, _ = data
+    p = init_params(40, scale=1.0)
+    t = Trainer(flatten(p), batch=64)
+    m = IntModel(t.export(dev(torch, keys)))
+    m.set_engine(engine_id(engine))
+    assert m.engine == engine_id(engine)
+    q = ragged_keys(n, 41)
+    got = m.scores(dev(torch, q)).cpu().numpy()
+    m.check()
+    want = OL.int_scores(OL.quantize(p, keys), q)
+    assert np.array_equal(got.astype(np.int64), want)
+
+
+def test_tensor_engine_is_the_default_when_exact(torch, data):
+    from paper_2512_15595_gb300.learned import BF_MLP_ENGINE_DP4A, BF_MLP_ENGINE_TENSOR, IntModel, Trainer
+    from paper_2512_15595_gb300 import BloomError
+    _, _, keys, _ = data
+    m = IntModel(Trainer(flatten(init_params(40, scale=1.0)), batch=64).export(dev(torch, keys)))
+    assert m.int8.sh1 <= 15 and m.int8.sh2 <= 15 and m.engine == BF_MLP_ENGINE_TENSOR
+    big = make_int8(torch, {"W1q": np.ones((64, 128)), "b1q": np.zeros(128), "sh1": 16, "W2q": np.ones((128, 64)),
+                            "b2q": np.zeros(64), "sh2": 0, "W3q": np.ones(64), "b3q": 0})
+    m2 = IntModel(big)
+    assert m2.engine == BF_MLP_ENGINE_DP4A
+    with pytest.raises(BloomError):
+        m2.set_engine(BF_MLP_ENGINE_TENSOR)
+
+
+def extreme_models():
+    """Integer models at the edges: weights at +-127, biases at and beyond the
+    clamps of the tensor engine, shifts at 0, 15 (the tensor engine's limit)
+    and beyond, scores that saturate int32 in both directions."""
+    rng = np.random.default_rng(9)
+    full = lambda shape, v: np.full(shape, v, dtype=np.int64)
+    out = []
+    out.append({"W1q": full((64, 128), 127), "b1q": full(128, 2**31 - 1 - 8128), "sh1": 0,
+                "W2q": full((128, 64), 127), "b2q": full(64, 0), "sh2": 0, "W3q": full(64, 127), "b3q": 2**31 - 1})
+    out.append({"W1q": full((64, 128), -127), "b1q": full(128, -(2**31)), "sh1": 15,
+                "W2q": full((128, 64), -127), "b2q": full(64, -(2**31)), "sh2": 15, "W3q": full(64, -127),
+                "b3q": -(2**31)})
+    for sh1, sh2 in ((0, 15), (15, 0), (7, 11), (3, 13), (15, 15)):
+        W1 = rng.integers(-127, 128, (64, 128))
+        W2 = rng.integers(-127, 128, (128, 64))
+        A1, A2 = 8128, 2064512
+        # biases spread across (and past) the range where they change the result
+        b1 = rng.integers(-(A1 + 50), 128 * 2**sh1 + A1 + 50, 128)
+        b1[:4] = [-(2**31), 2**31 - 1, -(A1 + 1), 128 * 2**sh1 + A1]
+        b2 = rng.integers(-(A2 + 50), 128 * 2**sh2 + A2 + 50, 64)
+        b2[:4] = [-(2**31), 2**31 - 1, -(A2 + 1), 128 * 2**sh2 + A2]
+        out.append({"W1q": W1, "b1q": b1, "sh1": sh1, "W2q": W2, "b2q": b2, "sh2": sh2,
+                    "W3q": rng.integers(-127, 128, 64), "b3q": int(rng.integers(-2**31, 2**31 - 1))})
+    out.append({"W1q": rng.integers(-127, 128, (64, 128)), "b1q": rng.integers(-3000, 3000, 128), "sh1": 5,
+                "W2q": rng.integers(-127, 128, (128, 64)), "b2q": rng.integers(-2**31, 2**31 - 1, 64), "sh2": 62,
+                "W3q": rng.integers(-127, 128, 64), "b3q": -(2**31)})
+    out.append({"W1q": rng.integers(-127, 128, (64, 128)), "b1q": rng.integers(-200, 200, 128), "sh1": 3,
+                "W2q": rng.integers(-127, 128, (128, 64)), "b2q": rng.integers(-20000, 20000, 64), "sh2": 7,
+                "W3q": -np.abs(rng.integers(-127, 128, 64)), "b3q": -(2**31) + 5})
+    return out
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_scores_saturation_and_extremes(torch, engine):
+    from paper_2512_15595_gb300.learned import IntModel
+    q = ragged_keys(20_011, 42)
+    q[:3] = [0, 2**64 - 1, 0x5555555555555555]
+    ran = 0
+    for c in extreme_models():
+        mm = IntModel(make_int8(torch, c))
+        if engine == "tensor" and not (c["sh1"] <= 15 and c["sh2"] <= 15):
+            continue
+        mm.set_engine(engine_id(engine))
+        got = mm.scores(dev(torch, q)).cpu().numpy().astype(np.int64)
+        mm.check()
+        assert np.array_equal(got, OL.int_scores(c, q)), (c["sh1"], c["sh2"])
+        ran += 1
+    assert ran >= 7
+
+
+@pytest.fixture(scope="module")
+def small_learned(torch, data):
+    from paper_2512_15595_gb300.learned import IntModel, Trainer, coprime_multiplier
+    mem, non, keys, labels = data
+    t = Trainer(flatten(init_params(50, scale=1.0)), batch=512)
+    t.train(dev(torch, keys), dev(torch, labels), steps=300, lr=3e-3, mult=coprime_multiplier(keys.size))
+    p = unflatten(t.params.cpu().numpy())
+    m = IntModel(t.export(dev(torch, keys)))
+    ref = OL.quantize(p, keys)
+    return m, ref
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("quantile", [0.0, 0.3, 0.9, 1.0])
+def test_learned_lookup_matches_oracle(torch, data, small_learned, quantile, engine):
+    from paper_2512_15595_gb300.learned import LearnedFilter
+    mem, non, _, _ = data
+    m, ref = small_learned
+    m.set_engine(engine_id(engine))
+    sm = OL.int_scores(ref, mem)
+    tau = int(np.quantile(sm, quantile)) + (1 if quantile == 1.0 else 0)
+    fn_ref = mem[sm < tau]
+    blocks = 37
+    lf = LearnedFilter(m, tau, dev(torch, mem), backup_blocks=blocks, seed=3)
+    assert lf.n_backup == fn_ref.size
+    # compaction: the same set of keys
+    out, cnt = m.select_below(tau, dev(torch, mem))
+    assert np.array_equal(np.sort(out[:cnt].cpu().numpy().view(np.uint64)), np.sort(fn_ref))
+    # backup filter: identical bit array to the oracle's built from the same keys
+    geom = oracle.Geometry(num_blocks=blocks, block_bits=256, word_bits=32, k=8, seed=3)
+    ob = oracle.SBF(geom)
+    ob.add(fn_ref)
+    assert np.array_equal(lf.backup.words.cpu().numpy(), ob.as_bytes())
+    q = np.concatenate([mem, non, ragged_keys(3001, 43)])
+    got = lf.contains(dev(torch, q)).cpu().numpy().astype(np.uint8)
+    want = ((OL.int_scores(ref, q) >= tau) | (ob.contains(q) != 0)).astype(np.uint8)
+    assert np.array_equal(got, want)
+    assert got[:mem.size].all()  # no false negatives

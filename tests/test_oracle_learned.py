@@ -118,3 +118,23 @@ def test_clustered_generator():
     k, f = clustered.non_members(10_000, s, w, seed=5)
     assert not clustered.inside(k, s, w).any()
     assert f.sum() == 5000
+
+
+def test_adam_first_step_is_a_signed_step():
+    # after one step m_hat = g and v_hat = g^2, so every parameter moves by lr * g / (|g| + eps)
+    rng = np.random.default_rng(1)
+    p, g = rng.standard_normal(50), rng.standard_normal(50) * 1e-3
+    q, m, v = L.adam_step(p, g, np.zeros(50), np.zeros(50), 1, lr=0.01)
+    assert np.allclose(p - q, 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_adam_constant_gradient_bias_correction():
+    # with a constant gradient the bias-corrected moments equal g and g^2 at every step t
+    g = np.array([0.3, -2.0, 1e-4])
+    p = np.zeros(3)
+    m = v = np.zeros(3)
+    for t in range(1, 8):
+        q, m, v = L.adam_step(p, g, m, v, t, lr=0.05, beta1=0.8, beta2=0.95, eps=0.0)
+        assert np.allclose(p - q, 0.05 * np.sign(g), rtol=1e-12, atol=0), t
+        p = q
