@@ -818,16 +818,19 @@ def run_learned(args):
     val_scores = model.scores(val).cpu().numpy()
     cands = sorted(set(int(x) for x in np.quantile(val_scores, [0.5, 0.8, 0.9, 0.95, 0.99, 0.999])) |
                    {int(val_scores.max()) + 1})
-    curve = []
-    best = None
-    for tau in cands:
-        lf = LB.LearnedFilter(model, tau, members, backup_blocks, B, S, K, 0)
-        fp = lf.contains(val).float().mean().item()
-        curve.append({"tau": tau, "backup_keys": lf.n_backup, "val_fpr": fp})
-        if best is None or fp < best[1]:
-            best = (tau, fp)
-        lf.backup.close()
-    tau = best[0]
+
+    def pick_tau(backup_blocks):
+        curve, best = [], None
+        for t in cands:
+            f_ = LB.LearnedFilter(model, t, members, backup_blocks, B, S, K, 0)
+            fp = f_.contains(val).float().mean().item()
+            curve.append({"tau": t, "backup_keys": f_.n_backup, "val_fpr": fp})
+            if best is None or fp < best[1]:
+                best = (t, fp)
+            f_.backup.close()
+        return best[0], curve
+
+    tau, curve = pick_tau(backup_blocks)
     lf = LB.LearnedFilter(model, tau, members, backup_blocks, B, S, K, 0)
     plain = Filter(plain_blocks, B, S, K, 0, device=device)
     plain.add(members)
@@ -876,6 +879,27 @@ def run_learned(args):
            "plain": {"all": float(pn.mean()), "uniform": float(pn[~nr].mean()), "near": float(pn[nr].mean())},
            "false_negatives": {"learned": fn_learned, "plain": fn_plain}, "tau_curve": curve,
            "non_member_queries": int(ln.size)}
+    # the same comparison at other budgets (tau re-chosen on the validation set for each)
+    by_bits = []
+    qn_near = torch.from_numpy(nr).to(device)
+    for bpk in [int(x) for x in args.learned_bits.split(",") if x]:
+        tb = bpk * n_mem
+        pb, bb = tb // B, max(1, (tb - LB.model_bits()) // B)
+        t_b, _ = pick_tau(bb)
+        lb = LB.LearnedFilter(model, t_b, members, bb, B, S, K, 0)
+        pf = Filter(pb, B, S, K, 0, device=device)
+        pf.add(members)
+        lo_ = lb.contains(qn)
+        po_ = pf.contains(qn)
+        by_bits.append({"bits_per_key": bpk, "tau": t_b, "backup_keys": lb.n_backup,
+                        "learned": {"all": lo_.float().mean().item(), "uniform": lo_[~qn_near].float().mean().item(),
+                                    "near": lo_[qn_near].float().mean().item()},
+                        "plain": {"all": po_.float().mean().item(), "uniform": po_[~qn_near].float().mean().item(),
+                                  "near": po_[qn_near].float().mean().item()}})
+        print(json.dumps(by_bits[-1]), file=sys.stderr, flush=True)
+        lb.backup.close()
+        pf.close()
+    fpr["by_bits_per_key"] = by_bits
     # roofline of the model kernel: 2 * (64*128 + 128*64 + 64) algorithmic flops per key (tensor engine)
     flops_key = 2 * (64 * 128 + 128 * 64 + 64)
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -912,21 +936,15 @@ def run_learned(args):
 
 
 def learned_e2e(torch, lf, queries, args):
-    """Learned lookups from pinned host keys to a host result, chunked."""
+    """Learned lookups from pinned host keys to a pinned host result through
+    bf_mlp_contains_host (staged copies overlapped with the lookups)."""
     n = queries.numel()
     hk = torch.empty(n, dtype=torch.int64, pin_memory=True)
     hk.copy_(queries)
     ho = torch.empty(n, dtype=torch.bool, pin_memory=True)
-    chunk = 1 << 24
-    dk = torch.empty(chunk, dtype=torch.int64, device=queries.device)
-    do = torch.empty(chunk, dtype=torch.bool, device=queries.device)
 
     def go():
-        for lo in range(0, n, chunk):
-            c = min(chunk, n - lo)
-            dk[:c].copy_(hk[lo:lo + c], non_blocking=True)
-            lf.contains(dk[:c], out=do[:c])
-            ho[lo:lo + c].copy_(do[:c], non_blocking=True)
+        lf.contains_host(hk, ho)
         torch.cuda.synchronize()
 
     go()
@@ -937,7 +955,8 @@ def learned_e2e(torch, lf, queries, args):
         ts.append(time.perf_counter() - t0)
     t = statistics.median(ts)
     return {"value": n / t / 1e9, "unit": "G keys/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": n,
-            "path": "pinned host keys -> device (16M-key chunks) -> bf_mlp_contains -> pinned host bytes"}
+            "path": "bf_mlp_contains_host: pinned host keys -> device staging (2^24-key chunks, 3 streams) -> "
+                    "backup lookup + model -> pinned host bytes"}
 
 
 def run_learned_reference(args):
@@ -987,6 +1006,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="4GiB", choices=sorted(WORKLOADS) + ["batched", "serving", "learned"])
     ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--learned-bits", default="2,4,6,8", help="other bits/key budgets for the FPR comparison")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--frontier", action="store_true")

@@ -448,6 +448,14 @@ bf_status bf_mlp_select_below(const bf_mlp_model* m, int32_t tau, const uint64_t
 bf_status bf_mlp_contains(const bf_mlp_model* m, int32_t tau, const bf_filter* backup, const uint64_t* d_keys,
                           uint64_t n, uint8_t* d_out, bf_stream_t stream);
 
+/* The same from host buffers (pinned for overlap): chunks of 2^24 keys are
+   copied in, looked up and copied out on three internal streams that follow
+   `stream` and are joined back into it.  The model keeps the staging
+   buffers (3 x 144 MiB of device memory) from the first call until
+   bf_mlp_free.  Calls on one model must not overlap. */
+bf_status bf_mlp_contains_host(bf_mlp_model* m, int32_t tau, const bf_filter* backup, const uint64_t* h_keys,
+                               uint64_t n, uint8_t* h_out, bf_stream_t stream);
+
 const char* bf_status_str(bf_status s);
 
 /* Message of the last error on the calling host thread ("" if none). */

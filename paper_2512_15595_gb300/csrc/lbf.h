@@ -20,11 +20,10 @@ constexpr int kImgW1 = 0, kImgW2 = kImgW1 + kH1 * kIn, kImgW3 = kImgW2 + kH2 * k
 void image_of(const bf_mlp_int8* m, std::vector<unsigned char>& img);
 
 // Tensor-core form of a model (see lbf_tc.cu): the operand image copied to
-// shared memory and the per-column constants of the two requantizations.
+// shared memory (weights, bias pieces, constant columns, bit table) and the
+// score offset.
 struct TcModel {
   std::vector<uint8_t> image;
-  float c1[128];
-  float c2[64];
   long long s3;
 };
 
@@ -40,10 +39,17 @@ cudaError_t tc_run(const uint8_t* d_image, const TcModel& tm, const uint64_t* d_
 }  // namespace lbf
 
 struct bf_mlp_model {
+  static constexpr int kDepth = 3;  // host pipeline: chunks in flight
   unsigned char* d_img = nullptr;  // CUDA-core image
   uint8_t* d_tc = nullptr;         // tensor-core operand image (null when not eligible)
   unsigned int* d_err = nullptr;   // device error word (bounded waits that ran out)
   lbf::TcModel tc;
   int engine = BF_MLP_ENGINE_AUTO;
   int device = 0;
+  // host pipeline (created on first use): staging slots of chunk keys + results
+  void* staging = nullptr;
+  uint64_t chunk = 0;
+  cudaStream_t pipe[kDepth] = {};
+  cudaEvent_t ev_done[kDepth] = {};
+  cudaEvent_t ev_start = nullptr;
 };

@@ -544,6 +544,12 @@ bf_status bf_mlp_load(const bf_mlp_int8* m, bf_mlp_model** out) {
 
 bf_status bf_mlp_free(bf_mlp_model* m) {
   if (!m) return BF_EINVAL;
+  for (int i = 0; i < bf_mlp_model::kDepth; ++i) {
+    if (m->pipe[i]) cudaStreamDestroy(m->pipe[i]);
+    if (m->ev_done[i]) cudaEventDestroy(m->ev_done[i]);
+  }
+  if (m->ev_start) cudaEventDestroy(m->ev_start);
+  if (m->staging) cudaFree(m->staging);
   if (m->d_img) cudaFree(m->d_img);
   if (m->d_tc) cudaFree(m->d_tc);
   if (m->d_err) cudaFree(m->d_err);
@@ -614,6 +620,49 @@ bf_status bf_mlp_contains(const bf_mlp_model* m, int32_t tau, const bf_filter* b
   const bf_status s = bf_contains(backup, d_keys, n, d_out, stream);
   if (s != BF_OK) return s;
   return run_model(m, d_keys, n, 1, tau, nullptr, d_out, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+bf_status bf_mlp_contains_host(bf_mlp_model* m, int32_t tau, const bf_filter* backup, const uint64_t* h_keys,
+                               uint64_t n, uint8_t* h_out, bf_stream_t stream) {
+  if (!m || !backup || (n && (!h_keys || !h_out))) return BF_EINVAL;
+  if (n == 0) return BF_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  constexpr uint64_t kChunk = 1ull << 24;
+  const uint64_t keys_bytes = kChunk * 8, slot = keys_bytes + kChunk;  // both multiples of 256
+  cudaError_t e = cudaSuccess;
+  if (!m->staging) {
+    if (cudaMalloc(&m->staging, slot * bf_mlp_model::kDepth) != cudaSuccess) {
+      cudaGetLastError();
+      m->staging = nullptr;
+      return BF_ENOMEM;
+    }
+    m->chunk = kChunk;
+    for (int i = 0; i < bf_mlp_model::kDepth; ++i)
+      if (cudaStreamCreateWithFlags(&m->pipe[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&m->ev_done[i], cudaEventDisableTiming) != cudaSuccess)
+        return BF_ECUDA;
+    if (cudaEventCreateWithFlags(&m->ev_start, cudaEventDisableTiming) != cudaSuccess) return BF_ECUDA;
+  }
+  if ((e = cudaEventRecord(m->ev_start, st)) != cudaSuccess) return BF_ECUDA;
+  for (int i = 0; i < bf_mlp_model::kDepth; ++i)
+    if (cudaStreamWaitEvent(m->pipe[i], m->ev_start, 0) != cudaSuccess) return BF_ECUDA;
+  uint64_t c = 0;
+  for (uint64_t lo = 0; lo < n; lo += kChunk, ++c) {
+    const uint64_t cnt = std::min(kChunk, n - lo);
+    const int k = static_cast<int>(c % bf_mlp_model::kDepth);
+    cudaStream_t ps = m->pipe[k];
+    char* base = static_cast<char*>(m->staging) + k * slot;
+    uint64_t* d_keys = reinterpret_cast<uint64_t*>(base);
+    uint8_t* d_out = reinterpret_cast<uint8_t*>(base + keys_bytes);
+    if (cudaMemcpyAsync(d_keys, h_keys + lo, cnt * 8, cudaMemcpyHostToDevice, ps) != cudaSuccess) return BF_ECUDA;
+    const bf_status s = bf_mlp_contains(m, tau, backup, d_keys, cnt, d_out, reinterpret_cast<bf_stream_t>(ps));
+    if (s != BF_OK) return s;
+    if (cudaMemcpyAsync(h_out + lo, d_out, cnt, cudaMemcpyDeviceToHost, ps) != cudaSuccess) return BF_ECUDA;
+  }
+  for (int i = 0; i < bf_mlp_model::kDepth; ++i)
+    if (cudaEventRecord(m->ev_done[i], m->pipe[i]) != cudaSuccess || cudaStreamWaitEvent(st, m->ev_done[i], 0) != cudaSuccess)
+      return BF_ECUDA;
+  return BF_OK;
 }
 
 }  // extern "C"

@@ -7,11 +7,13 @@
 // an exactly representable integer multiple of a power of two:
 //   * A1 = the key bits (0/1), B1 = W1q * 2^-sh1 (int8 times a power of two:
 //     exact in bf16); |sum x W1q| <= 64 * 127.
-//   * the epilogue adds a per-column constant c1 = (b1' + 128 * 2^sh1) 2^-sh1,
-//     so y1 = 128 + a1 / 2^sh1 exactly (b1' = b1q clamped to the range where
-//     it still changes the result), converts to bf16 rounding toward zero
-//     (the bf16 spacing on [128, 256) is 1, so this is the floor) and clamps
-//     to [128, 255]: A2 = 128 + h1, exact in bf16.
+//   * a per-column constant c1 = (b1' + 128 * 2^sh1) 2^-sh1 enters through a
+//     16-wide extra k-block (three constant-one columns of A times c1 split
+//     into three bf16 pieces), so y1 = 128 + a1 / 2^sh1 exactly (b1' = b1q
+//     clamped to the range where it still changes the result); the epilogue
+//     converts to bf16 rounding toward zero (the bf16 spacing on [128, 256)
+//     is 1, so this is the floor) and clamps to [128, 255]: A2 = 128 + h1,
+//     exact in bf16.
 //   * B2 = W2q * 2^-sh2; the offset 128 * colsum(W2q) is folded into c2, and
 //     likewise A3 = 128 + h2, B3 = W3q, score = acc3 + (b3q - 128 sum W3q).
 // Every magnitude stays below 2^24 when sh1, sh2 <= 15 (checked on the host;
@@ -19,13 +21,21 @@
 // model's bit for bit.
 //
 // Kernel shape: persistent, one CTA per SM, four warpgroups.  Each warpgroup
-// owns a 32 KiB shared-memory slot and 128 TMEM columns and runs its tiles of
-// 128 keys through build A1 -> MMA L1 -> epilogue -> MMA L2 -> epilogue ->
-// MMA L3 -> score on its own; one elected thread issues its MMAs and commits
-// them to the warpgroup's mbarrier.  Four independent pipelines keep the
-// tensor core busy while the other warpgroups run their epilogues.  Operands
-// use the K-major 128-byte-swizzled layout (8-row groups of 128-byte rows,
-// 16-byte chunks XOR-permuted by row), written by the threads themselves.
+// owns 16 KiB of shared memory (A1) and 128 TMEM columns and runs its tiles of
+// 128 keys through MMA L1 -> epilogue -> MMA L2 -> epilogue -> MMA L3 -> score
+// on its own; one elected thread issues its MMAs and commits them to the
+// warpgroup's mbarriers.  Four independent pipelines keep the tensor core
+// busy while the other warpgroups run their epilogues.  The activations stay
+// in tensor memory: each epilogue reads its fp32 accumulator row, packs the
+// requantized bf16 pairs and stores them back into columns already consumed,
+// and the next MMA takes its A operand from there (so L2 and L3 read only B
+// from shared memory).  TMEM columns of a warpgroup over one tile:
+//   L1: D1 -> 0..127;  E1: A2 (128 bf16 = 64 columns) -> 0..63;
+//   L2: A = 0..63, D2 -> 64..127;  E2: A3 (64 bf16) -> 0..31;
+//   L3: A = 0..31, D3 -> 64..79;  E3: column 64.
+// Shared-memory operands (A1, weights, bias pieces) use the K-major
+// 128-byte-swizzled layout (8-row groups of 128-byte rows, 16-byte chunks
+// XOR-permuted by row); the next tile's A1 is written while L2 runs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -43,14 +53,19 @@ namespace {
 constexpr uint32_t kB1 = 0;                     // 128 rows (unit j) x 64 bf16 (input i)
 constexpr uint32_t kB2 = kB1 + 128 * 128;       // 2 k-blocks x 64 rows x 64 bf16
 constexpr uint32_t kB3 = kB2 + 2 * 64 * 128;    // 16 rows x 64 bf16 (row 0 = W3q)
-constexpr uint32_t kLut = kB3 + 16 * 128;       // 256 x 8 bf16: bits of a byte as 0/1
+constexpr uint32_t kB1b = kB3 + 16 * 128;       // 128 rows: the three bf16 pieces of c1 (k = 0..2)
+constexpr uint32_t kB2b = kB1b + 128 * 128;     // 64 rows: the pieces of c2
+constexpr uint32_t kAc = kB2b + 64 * 128;       // 128 rows: ones at k = 0..2
+constexpr uint32_t kLut = kAc + 128 * 128;      // 256 x 8 bf16: bits of a byte as 0/1
 constexpr uint32_t kImage = kLut + 256 * 16;    // bytes copied from the device image
-constexpr uint32_t kSlots = kImage;             // 4 slots of 32 KiB
-constexpr uint32_t kSlotBytes = 32768;
+constexpr uint32_t kSlots = kImage;             // 4 slots of 16 KiB (A1)
+constexpr uint32_t kSlotBytes = 16384;
 constexpr int kWG = 4;
-constexpr uint32_t kBar = kSlots + kWG * kSlotBytes;  // 4 mbarriers, TMEM base, flags
-constexpr uint32_t kSmemBytes = kBar + 64 + 1024;     // + alignment slack
-static_assert(kSlots % 1024 == 0, "slots must be 1024-byte aligned");
+constexpr uint32_t kBar = kSlots + kWG * kSlotBytes;  // 4 mbarriers per warpgroup, TMEM base, flags
+constexpr uint32_t kSmemBytes = kBar + 256 + 1024;    // + alignment slack
+static_assert(kSlots % 1024 == 0 && kB1b % 1024 == 0 && kB2b % 1024 == 0 && kAc % 1024 == 0,
+              "swizzled operands must be 1024-byte aligned");
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 constexpr int kThreads = 128 * kWG;
 constexpr uint32_t kTmemCols = 512;
 
@@ -71,8 +86,6 @@ struct TcArgs {
   uint64_t* out_keys;
   unsigned int* err;
   long long s3;
-  float c1[128];
-  float c2[64];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -93,6 +106,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(id), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t id,
+                                            uint32_t accum) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(id), "r"(accum));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -136,22 +157,6 @@ __device__ __forceinline__ uint4 lds128(uint32_t a) {
   return v;
 }
 
-// 32 consecutive fp32 columns of this thread's TMEM row
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
   uint32_t r;
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
@@ -173,6 +178,57 @@ __device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t chunk) {
   return row * 128u + (((chunk ^ (row & 7u)) & 7u) << 4);
 }
 
+#define LBF_LD32(dst, addr)                                                                                        \
+  asm volatile(                                                                                                    \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "   \
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"                \
+      : "=r"(dst[0]), "=r"(dst[1]), "=r"(dst[2]), "=r"(dst[3]), "=r"(dst[4]), "=r"(dst[5]), "=r"(dst[6]),           \
+        "=r"(dst[7]), "=r"(dst[8]), "=r"(dst[9]), "=r"(dst[10]), "=r"(dst[11]), "=r"(dst[12]), "=r"(dst[13]),       \
+        "=r"(dst[14]), "=r"(dst[15]), "=r"(dst[16]), "=r"(dst[17]), "=r"(dst[18]), "=r"(dst[19]), "=r"(dst[20]),    \
+        "=r"(dst[21]), "=r"(dst[22]), "=r"(dst[23]), "=r"(dst[24]), "=r"(dst[25]), "=r"(dst[26]), "=r"(dst[27]),    \
+        "=r"(dst[28]), "=r"(dst[29]), "=r"(dst[30]), "=r"(dst[31])                                                  \
+      : "r"(addr))
+
+#define LBF_ST16(addr, src)                                                                                        \
+  asm volatile(                                                                                                    \
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "  \
+      "%15, %16};" ::"r"(addr),                                                                                     \
+      "r"(src[0]), "r"(src[1]), "r"(src[2]), "r"(src[3]), "r"(src[4]), "r"(src[5]), "r"(src[6]), "r"(src[7]),       \
+      "r"(src[8]), "r"(src[9]), "r"(src[10]), "r"(src[11]), "r"(src[12]), "r"(src[13]), "r"(src[14]), "r"(src[15])  \
+      : "memory")
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 32 loaded accumulator columns -> 16 columns of packed bf16 (128 + h) at `to`
+__device__ __forceinline__ void requant_store(const uint32_t (&a)[32], uint32_t to) {
+  uint32_t w[16];
+#pragma unroll
+  for (int p = 0; p < 16; ++p) w[p] = requant2(__uint_as_float(a[2 * p]), __uint_as_float(a[2 * p + 1]));
+  LBF_ST16(to, w);
+}
+
+// Accumulator columns from[0 .. 32 NC) -> packed bf16 columns to[0 .. 16 NC),
+// in chunks of 32 columns with the next chunk's load in flight while the
+// current one is converted.  Chunk c is stored over columns that chunk c/2
+// already loaded (to <= from), so no store overwrites an unread column.
+template <int NC>
+__device__ __forceinline__ void requant_run(uint32_t from, uint32_t to) {
+  uint32_t a[32], b[32];
+  LBF_LD32(a, from);
+  tmem_wait_ld();
+#pragma unroll
+  for (int c = 0; c < NC; c += 2) {
+    if (c + 1 < NC) LBF_LD32(b, from + 32 * (c + 1));
+    requant_store(a, to + 16 * c);
+    if (c + 1 < NC) {
+      tmem_wait_ld();
+      if (c + 2 < NC) LBF_LD32(a, from + 32 * (c + 2));
+      requant_store(b, to + 16 * (c + 1));
+      if (c + 2 < NC) tmem_wait_ld();
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ TcArgs P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -182,10 +238,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ 
 
   for (uint32_t i = tid; i < kImage / 16; i += kThreads)
     reinterpret_cast<uint4*>(smem)[i] = reinterpret_cast<const uint4*>(P.image)[i];
-  uint32_t* holder = reinterpret_cast<uint32_t*>(smem + kBar + 32);
-  volatile int* flag = reinterpret_cast<volatile int*>(smem + kBar + 48);
+  uint32_t* holder = reinterpret_cast<uint32_t*>(smem + kBar + 128);
+  volatile int* flag = reinterpret_cast<volatile int*>(smem + kBar + 144);
   if (tid == 0) {
-    for (int s = 0; s < kWG; ++s)
+    for (int s = 0; s < 4 * kWG; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sb + kBar + 8 * s) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -203,93 +259,96 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ 
 
   const int wg = tid >> 7;
   const uint32_t r = tid & 127;
-  const uint32_t slot = sb + kSlots + wg * kSlotBytes;
-  const uint32_t bar = sb + kBar + 8 * wg;
-  const uint32_t tm = tmem + wg * 128;                      // this warpgroup's columns
-  const uint32_t tm_row = tm + ((r & ~31u) << 16);          // this warp's lane quarter
+  const uint32_t a1 = sb + kSlots + wg * kSlotBytes;   // this warpgroup's A1 (shared memory)
+  const uint32_t bars = sb + kBar + 32 * wg;           // commits of L1, L2, L3
+  const uint32_t tm = tmem + wg * 128;                  // this warpgroup's columns
+  const uint32_t tm_row = tm + ((r & ~31u) << 16);      // this warp's lane quarter
   const uint64_t ntiles = (P.n + 127) / 128;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWG;
   const uint64_t limit = 2000000000ull;
-  uint32_t phase = 0;
-  bool failed = false;
+  uint32_t phase = 0;  // each barrier completes once per tile
+  int failed = -1;
 
-  // one elected thread waits (bounded) on the MMA commit; the warpgroup then
-  // agrees on the outcome through a named barrier
-  auto wait_mma = [&]() -> bool {
-    if (r == 0) flag[wg] = mbar_wait(bar, phase, limit) ? 0 : 1;
+  // one elected thread waits (bounded) on a commit; the warpgroup then agrees
+  // on the outcome through a named barrier (a flag slot per barrier)
+  auto wait_on = [&](int which) -> bool {
+    if (r == 0) flag[4 * wg + which] = mbar_wait(bars + 8 * which, phase, limit) ? 0 : 1;
     wg_bar(1 + wg);
-    phase ^= 1;
     fence_after();
-    return flag[wg] == 0;
+    return flag[4 * wg + which] == 0;
   };
-
-  for (uint64_t tile = static_cast<uint64_t>(blockIdx.x) * kWG + wg; tile < ntiles;
-       tile += static_cast<uint64_t>(gridDim.x) * kWG) {
-    const uint64_t i = tile * 128 + r;
-    const bool live = i < P.n;
-    const uint64_t key = live ? __ldg(P.keys + i) : 0;
-    // A1: row r = the 64 key bits as bf16 0 / 1
+  // A1 of a tile: row r = the 64 key bits as bf16 0 / 1
+  auto build_a1 = [&](uint64_t key) {
 #pragma unroll
     for (uint32_t c = 0; c < 8; ++c) {
       const uint4 v = lds128(sb + kLut + ((static_cast<uint32_t>(key >> (8 * c)) & 0xFFu) << 4));
-      sts128(slot + swz(r, c), v.x, v.y, v.z, v.w);
+      sts128(a1 + swz(r, c), v.x, v.y, v.z, v.w);
     }
     fence_async_smem();
+  };
+  // make this thread's TMEM stores visible to the MMA issued after the barrier
+  auto tmem_stores_done = [&]() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    fence_before();
     wg_bar(1 + wg);
+  };
+
+  uint64_t tile = static_cast<uint64_t>(blockIdx.x) * kWG + wg;
+  uint64_t key = 0;
+  if (tile < ntiles) {
+    const uint64_t i0 = tile * 128 + r;
+    key = i0 < P.n ? __ldg(P.keys + i0) : 0;
+    build_a1(key);
+    wg_bar(1 + wg);
+  }
+  for (; tile < ntiles; tile += stride) {
+    const uint64_t i = tile * 128 + r;
+    const bool live = i < P.n;
     if (r == 0) {
       fence_after();
 #pragma unroll
-      for (uint32_t s = 0; s < 4; ++s) mma_bf16(tm, sdesc(slot + s * 32), sdesc(sb + kB1 + s * 32), idesc(128), s);
-      mma_commit(bar);
+      for (uint32_t s = 0; s < 4; ++s) mma_bf16(tm, sdesc(a1 + s * 32), sdesc(sb + kB1 + s * 32), idesc(128), s);
+      mma_bf16(tm, sdesc(sb + kAc), sdesc(sb + kB1b), idesc(128), 1);
+      mma_commit(bars);
     }
-    if (!wait_mma()) { failed = true; break; }
-    // epilogue 1: 128 columns -> A2 = 128 + h1 (two k-blocks)
-#pragma unroll
-    for (uint32_t q = 0; q < 4; ++q) {
-      float v[32];
-      tmem_ld32(tm_row + q * 32, v);
-      uint32_t w[16];
-#pragma unroll
-      for (int p = 0; p < 16; ++p) w[p] = requant2(v[2 * p] + P.c1[q * 32 + 2 * p], v[2 * p + 1] + P.c1[q * 32 + 2 * p + 1]);
-      const uint32_t kb = slot + (q >> 1) * 16384u;
-#pragma unroll
-      for (uint32_t t = 0; t < 4; ++t) sts128(kb + swz(r, (q & 1) * 4 + t), w[4 * t], w[4 * t + 1], w[4 * t + 2], w[4 * t + 3]);
-    }
-    fence_before();
-    fence_async_smem();
-    wg_bar(1 + wg);
+    // the next tile's keys, loaded early
+    const uint64_t ntile = tile + stride;
+    const uint64_t ni = ntile * 128 + r;
+    const uint64_t nkey = (ntile < ntiles && ni < P.n) ? __ldg(P.keys + ni) : 0;
+    // epilogue 1: D1 (columns 0..127) -> A2 = 128 + h1 packed in columns 0..63
+    if (!wait_on(0)) { failed = 0; break; }
+    requant_run<4>(tm_row, tm_row);
+    tmem_stores_done();
     if (r == 0) {
       fence_after();
 #pragma unroll
       for (uint32_t s = 0; s < 8; ++s)
-        mma_bf16(tm, sdesc(slot + (s >> 2) * 16384u + (s & 3) * 32), sdesc(sb + kB2 + (s >> 2) * 8192u + (s & 3) * 32),
-                 idesc(64), s);
-      mma_commit(bar);
+        mma_bf16_ta(tm + 64, tm + 8 * s, sdesc(sb + kB2 + (s >> 2) * 8192u + (s & 3) * 32), idesc(64), s);
+      mma_bf16(tm + 64, sdesc(sb + kAc), sdesc(sb + kB2b), idesc(64), 1);
+      mma_commit(bars + 8);
     }
-    if (!wait_mma()) { failed = true; break; }
-    // epilogue 2: 64 columns -> A3 = 128 + h2 (one k-block)
-#pragma unroll
-    for (uint32_t q = 0; q < 2; ++q) {
-      float v[32];
-      tmem_ld32(tm_row + q * 32, v);
-      uint32_t w[16];
-#pragma unroll
-      for (int p = 0; p < 16; ++p) w[p] = requant2(v[2 * p] + P.c2[q * 32 + 2 * p], v[2 * p + 1] + P.c2[q * 32 + 2 * p + 1]);
-#pragma unroll
-      for (uint32_t t = 0; t < 4; ++t) sts128(slot + swz(r, q * 4 + t), w[4 * t], w[4 * t + 1], w[4 * t + 2], w[4 * t + 3]);
-    }
-    fence_before();
-    fence_async_smem();
-    wg_bar(1 + wg);
+    // the next tile's A1 while L2 runs (L1, its only reader, is complete)
+    if (ntile < ntiles) build_a1(nkey);
+    // epilogue 2: D2 (columns 64..127) -> A3 = 128 + h2 packed in columns 0..31
+    if (!wait_on(1)) { failed = 1; break; }
+    requant_run<2>(tm_row + 64, tm_row);
+    tmem_stores_done();
     if (r == 0) {
       fence_after();
 #pragma unroll
-      for (uint32_t s = 0; s < 4; ++s) mma_bf16(tm, sdesc(slot + s * 32), sdesc(sb + kB3 + s * 32), idesc(16), s);
-      mma_commit(bar);
+      for (uint32_t s = 0; s < 4; ++s) mma_bf16_ta(tm + 64, tm + 8 * s, sdesc(sb + kB3 + s * 32), idesc(16), s);
+      mma_commit(bars + 16);
     }
-    if (!wait_mma()) { failed = true; break; }
-    // score: column 0
-    const float acc3 = tmem_ld1(tm_row);
+    if (!wait_on(2)) { failed = 2; break; }
+    // score: column 64
+    const float acc3 = tmem_ld1(tm_row + 64);
     fence_before();
+    // the next L1 overwrites these columns: warp 0 waits for every warp's load
+    if ((r >> 5) == 0)
+      asm volatile("bar.sync %0, 128;" ::"r"(5 + wg) : "memory");
+    else
+      asm volatile("bar.arrive %0, 128;" ::"r"(5 + wg) : "memory");
+    phase ^= 1;
     long long sc = static_cast<long long>(__float2int_rn(acc3)) + P.s3;
     sc = sc < INT32_MIN ? INT32_MIN : (sc > INT32_MAX ? INT32_MAX : sc);
     if (P.mode == 0) {
@@ -305,10 +364,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ 
       base = __shfl_sync(0xFFFFFFFFu, base, 0);
       if (take) P.out_keys[base + __popc(vote & ((1u << lane) - 1u))] = key;
     }
+    key = nkey;
   }
-  if (failed && r == 0) {
+  if (failed >= 0 && r == 0) {
     atomicOr(P.err, 1u);
-    mbar_wait(bar, phase ^ 1, limit);  // the MMAs still in flight, once more (bounded)
+    // the MMAs still in flight, once more (bounded)
+    mbar_wait(bars + 8 * failed, phase, limit / 4);
   }
   fence_before();
   __syncthreads();
@@ -334,6 +395,24 @@ uint32_t swz_host(uint32_t row, uint32_t k) {  // element k (< 64) of a 128-byte
   return row * 128u + ((((k >> 3) ^ (row & 7u)) & 7u) << 4) + (k & 7u) * 2u;
 }
 
+// c (an fp32 value with at most 24 significant bits) as three bf16 pieces
+// whose sum is c exactly; false if that does not hold
+bool split3(float c, uint16_t (&p)[3]) {
+  float rest = c;
+  double exact = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    uint32_t u;
+    std::memcpy(&u, &rest, 4);
+    p[i] = static_cast<uint16_t>(u >> 16);  // truncation keeps the top 8 significant bits
+    const uint32_t t = static_cast<uint32_t>(p[i]) << 16;
+    float v;
+    std::memcpy(&v, &t, 4);
+    rest = rest - v;  // exact: v is a prefix of rest's bits
+    exact += static_cast<double>(v);
+  }
+  return rest == 0.f && exact == static_cast<double>(c);
+}
+
 }  // namespace
 
 bool tc_eligible(const bf_mlp_int8* m) { return m->sh1 >= 0 && m->sh1 <= 15 && m->sh2 >= 0 && m->sh2 <= 15; }
@@ -354,17 +433,23 @@ bool tc_prepare(const bf_mlp_int8* m, TcModel* out) {
   }
   for (uint32_t b = 0; b < 256; ++b)
     for (uint32_t e = 0; e < 8; ++e) put16(img, kLut + b * 16 + e * 2, ((b >> e) & 1u) ? 0x3F80 : 0);
+  for (uint32_t r = 0; r < 128; ++r)
+    for (uint32_t k = 0; k < 3; ++k) put16(img, kAc + swz_host(r, k), 0x3F80);
   const long long A1 = 64LL * 127, A2 = 128LL * 127 * 127;
   const long long p1 = 1LL << m->sh1, p2 = 1LL << m->sh2;
-  for (int j = 0; j < 128; ++j) {
+  for (uint32_t j = 0; j < 128; ++j) {
     const long long b = std::min(std::max<long long>(m->b1[j], -(A1 + 1)), 128 * p1 + A1);
-    out->c1[j] = static_cast<float>(static_cast<double>(b + 128 * p1) * s1);
+    uint16_t pc[3];
+    if (!split3(static_cast<float>(static_cast<double>(b + 128 * p1) * s1), pc)) return false;
+    for (uint32_t k = 0; k < 3; ++k) put16(img, kB1b + swz_host(j, k), pc[k]);
   }
-  for (int j = 0; j < 64; ++j) {
+  for (uint32_t j = 0; j < 64; ++j) {
     long long col = 0;
     for (int i = 0; i < 128; ++i) col += m->w2[i * 64 + j];
     const long long b = std::min(std::max<long long>(m->b2[j], -(A2 + 1)), 128 * p2 + A2);
-    out->c2[j] = static_cast<float>(static_cast<double>(b - 128 * col + 128 * p2) * s2);
+    uint16_t pc[3];
+    if (!split3(static_cast<float>(static_cast<double>(b - 128 * col + 128 * p2) * s2), pc)) return false;
+    for (uint32_t k = 0; k < 3; ++k) put16(img, kB2b + swz_host(j, k), pc[k]);
   }
   out->s3 = static_cast<long long>(m->b3) - 128 * sum3;
   out->image = std::move(img);
@@ -400,8 +485,6 @@ cudaError_t tc_run(const uint8_t* d_image, const TcModel& tm, const uint64_t* d_
   a.out_keys = out_keys;
   a.err = err;
   a.s3 = tm.s3;
-  std::memcpy(a.c1, tm.c1, sizeof(a.c1));
-  std::memcpy(a.c2, tm.c2, sizeof(a.c2));
   k_tc_mlp<<<grid, kThreads, kSmemBytes, st>>>(a);
   return cudaGetLastError();
 }

@@ -157,3 +157,10 @@ class LearnedFilter:
         _lib.bf_mlp_contains(self.model.handle, self.tau, self.backup.handle, keys.data_ptr(), keys.numel(),
                              out.data_ptr(), stream)
         return out
+
+    def contains_host(self, keys, out, stream=None) -> None:
+        """Lookups from a host tensor (pinned for overlap) into a host bool/uint8 tensor."""
+        if keys.is_cuda or out.is_cuda or out.numel() != keys.numel() or out.element_size() != 1:
+            raise ValueError("host keys and a host 1-byte output of the same length")
+        _lib.bf_mlp_contains_host(self.model.handle, self.tau, self.backup.handle, keys.data_ptr(), keys.numel(),
+                                  out.data_ptr(), stream)

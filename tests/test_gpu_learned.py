@@ -321,3 +321,31 @@ def test_learned_lookup_matches_oracle(torch, data, small_learned, quantile, eng
     want = ((OL.int_scores(ref, q) >= tau) | (ob.contains(q) != 0)).astype(np.uint8)
     assert np.array_equal(got, want)
     assert got[:mem.size].all()  # no false negatives
+
+
+def test_learned_lookup_from_host_buffers(torch, data, small_learned):
+    """bf_mlp_contains_host over two ragged chunks equals the device path, and
+    a sample of positions equals the oracle."""
+    from paper_2512_15595_gb300.learned import LearnedFilter
+    mem, non, _, _ = data
+    m, ref = small_learned
+    tau = int(np.quantile(OL.int_scores(ref, mem), 0.5))
+    lf = LearnedFilter(m, tau, dev(torch, mem), backup_blocks=301, seed=4)
+    n = (1 << 24) + 12_345
+    q = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    q.copy_(synthkeys.splitmix64_torch(44, 0, n, "cuda"))
+    q[:mem.size] = torch.from_numpy(mem.view(np.int64))
+    out = torch.zeros(n, dtype=torch.bool, pin_memory=True)
+    lf.contains_host(q, out)
+    torch.cuda.synchronize()
+    dq = q.cuda()
+    want_dev = lf.contains(dq).cpu()
+    assert torch.equal(out, want_dev)
+    assert out[:mem.size].all()
+    idx = np.random.default_rng(5).choice(n, 20_000, replace=False)
+    keys = q.numpy()[idx].view(np.uint64)
+    fn_ref = mem[OL.int_scores(ref, mem) < tau]
+    ob = oracle.SBF(oracle.Geometry(num_blocks=301, block_bits=256, word_bits=32, k=8, seed=4))
+    ob.add(fn_ref)
+    want = (OL.int_scores(ref, keys) >= tau) | (ob.contains(keys) != 0)
+    assert np.array_equal(out.numpy()[idx], want)
