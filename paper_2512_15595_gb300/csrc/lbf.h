@@ -25,16 +25,26 @@ void image_of(const bf_mlp_int8* m, std::vector<unsigned char>& img);
 struct TcModel {
   std::vector<uint8_t> image;
   long long s3;
+  float w3[64];
+};
+
+// A backup filter the tensor-core kernel can probe itself (256-bit blocks,
+// S = 32, K = 8, sectorized).
+struct TcBackup {
+  const uint32_t* words;
+  uint64_t num_blocks;
+  uint64_t seed;
 };
 
 bool tc_eligible(const bf_mlp_int8* m);
 bool tc_prepare(const bf_mlp_int8* m, TcModel* out);
 uint32_t tc_image_bytes();
 // modes: 0 scores to out32, 1 out8[i] = 1 where score >= tau, 4 keys scoring
-// below tau appended to out_keys (number in *count)
+// below tau appended to out_keys (number in *count), 5 out8[i] = score >= tau
+// or `backup` contains key i
 cudaError_t tc_run(const uint8_t* d_image, const TcModel& tm, const uint64_t* d_keys, uint64_t n, int mode, int tau,
                    int32_t* out32, uint8_t* out8, unsigned long long* count, uint64_t* out_keys, unsigned int* err,
-                   cudaStream_t st);
+                   cudaStream_t st, const TcBackup* backup = nullptr);
 
 }  // namespace lbf
 

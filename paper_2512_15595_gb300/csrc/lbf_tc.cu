@@ -15,24 +15,25 @@
 //     is 1, so this is the floor) and clamps to [128, 255]: A2 = 128 + h1,
 //     exact in bf16.
 //   * B2 = W2q * 2^-sh2; the offset 128 * colsum(W2q) is folded into c2, and
-//     likewise A3 = 128 + h2, B3 = W3q, score = acc3 + (b3q - 128 sum W3q).
+//     likewise 128 + h2 (exact in bf16 and fp32) is dotted with W3q on the
+//     CUDA cores in fp32 (integer partial sums below 2^24), score = acc3 +
+//     (b3q - 128 sum W3q).
 // Every magnitude stays below 2^24 when sh1, sh2 <= 15 (checked on the host;
 // other models use the dp4a kernel), so the results equal the integer
 // model's bit for bit.
 //
 // Kernel shape: persistent, one CTA per SM, four warpgroups.  Each warpgroup
 // owns 16 KiB of shared memory (A1) and 128 TMEM columns and runs its tiles of
-// 128 keys through MMA L1 -> epilogue -> MMA L2 -> epilogue -> MMA L3 -> score
-// on its own; one elected thread issues its MMAs and commits them to the
+// 128 keys through MMA L1 -> epilogue -> MMA L2 -> epilogue with layer 3 ->
+// score on its own; one elected thread issues its MMAs and commits them to the
 // warpgroup's mbarriers.  Four independent pipelines keep the tensor core
 // busy while the other warpgroups run their epilogues.  The activations stay
 // in tensor memory: each epilogue reads its fp32 accumulator row, packs the
 // requantized bf16 pairs and stores them back into columns already consumed,
-// and the next MMA takes its A operand from there (so L2 and L3 read only B
-// from shared memory).  TMEM columns of a warpgroup over one tile:
+// and the next MMA takes its A operand from there (so L2 reads only B from
+// shared memory).  TMEM columns of a warpgroup over one tile:
 //   L1: D1 -> 0..127;  E1: A2 (128 bf16 = 64 columns) -> 0..63;
-//   L2: A = 0..63, D2 -> 64..127;  E2: A3 (64 bf16) -> 0..31;
-//   L3: A = 0..31, D3 -> 64..79;  E3: column 64.
+//   L2: A = 0..63, D2 -> 64..127;  E2: reads 64..127.
 // Shared-memory operands (A1, weights, bias pieces) use the K-major
 // 128-byte-swizzled layout (8-row groups of 128-byte rows, 16-byte chunks
 // XOR-permuted by row); the next tile's A1 is written while L2 runs.
@@ -45,6 +46,7 @@
 
 #include "bloomgb.h"
 #include "lbf.h"
+#include "sbf_device.cuh"
 
 namespace lbf {
 namespace {
@@ -52,8 +54,7 @@ namespace {
 // shared-memory map (offsets from a 1024-byte aligned base)
 constexpr uint32_t kB1 = 0;                     // 128 rows (unit j) x 64 bf16 (input i)
 constexpr uint32_t kB2 = kB1 + 128 * 128;       // 2 k-blocks x 64 rows x 64 bf16
-constexpr uint32_t kB3 = kB2 + 2 * 64 * 128;    // 16 rows x 64 bf16 (row 0 = W3q)
-constexpr uint32_t kB1b = kB3 + 16 * 128;       // 128 rows: the three bf16 pieces of c1 (k = 0..2)
+constexpr uint32_t kB1b = kB2 + 2 * 64 * 128;   // 128 rows: the three bf16 pieces of c1 (k = 0..2)
 constexpr uint32_t kB2b = kB1b + 128 * 128;     // 64 rows: the pieces of c2
 constexpr uint32_t kAc = kB2b + 64 * 128;       // 128 rows: ones at k = 0..2
 constexpr uint32_t kLut = kAc + 128 * 128;      // 256 x 8 bf16: bits of a byte as 0/1
@@ -78,7 +79,8 @@ struct TcArgs {
   const uint64_t* keys;
   uint64_t n;
   const uint8_t* image;  // kImage bytes, laid out as in shared memory
-  int mode;              // 0 scores, 1 out8 |= score >= tau, 4 compaction below tau
+  int mode;              // 0 scores, 1 out8 |= score >= tau, 4 compaction below tau,
+                         // 5 out8 = score >= tau || backup filter (fused lookup)
   int tau;
   int32_t* out32;
   uint8_t* out8;
@@ -86,7 +88,33 @@ struct TcArgs {
   uint64_t* out_keys;
   unsigned int* err;
   long long s3;
+  float w3[64];  // W3q as fp32 (layer 3 runs on the CUDA cores)
+  // mode 5: the backup filter (256-bit blocks, S = 32, K = 8, sectorized)
+  const uint32_t* bk_words;
+  uint64_t bk_blocks;
+  uint64_t bk_acc0;
+  int bk_mode;
 };
+
+// Backup-filter membership of one key (sectorized filter, 256-bit blocks,
+// S = 32, K = 8: one bit in each of the block's eight words; Sec. II-A and
+// Sec. IV-B): the block's 32 bytes are loaded here, tested by backup_test.
+__device__ __forceinline__ void backup_load(const TcArgs& P, uint64_t key, uint32_t& hlo, uint32_t (&w)[8]) {
+  const uint64_t h = bloomgb::xxh64_key(key, P.bk_acc0);
+  const uint64_t j = bloomgb::block_of(h, P.bk_blocks, P.bk_mode);
+  hlo = static_cast<uint32_t>(h);
+  bloomgb::ld_words<8>(P.bk_words + j * 8, bloomgb::policy_evict_normal(), w);
+}
+
+__device__ __forceinline__ bool backup_test(uint32_t hlo, const uint32_t (&w)[8]) {
+  bool in = true;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const uint32_t bit = bloomgb::pattern_bit(hlo, bloomgb::salt_at<32>(t));
+    in = in && ((w[t] & bit) != 0);
+  }
+  return in;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -157,12 +185,6 @@ __device__ __forceinline__ uint4 lds128(uint32_t a) {
   return v;
 }
 
-__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
-  uint32_t r;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-  return __uint_as_float(r);
-}
 
 // bf16 pair: floor of (lo, hi) on [128, 256) by conversion toward zero, then clamped to [128, 255]
 __device__ __forceinline__ uint32_t requant2(float lo, float hi) {
@@ -260,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ 
   const int wg = tid >> 7;
   const uint32_t r = tid & 127;
   const uint32_t a1 = sb + kSlots + wg * kSlotBytes;   // this warpgroup's A1 (shared memory)
-  const uint32_t bars = sb + kBar + 32 * wg;           // commits of L1, L2, L3
+  const uint32_t bars = sb + kBar + 32 * wg;           // commits of L1, L2
   const uint32_t tm = tmem + wg * 128;                  // this warpgroup's columns
   const uint32_t tm_row = tm + ((r & ~31u) << 16);      // this warp's lane quarter
   const uint64_t ntiles = (P.n + 127) / 128;
@@ -315,6 +337,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ 
     const uint64_t ntile = tile + stride;
     const uint64_t ni = ntile * 128 + r;
     const uint64_t nkey = (ntile < ntiles && ni < P.n) ? __ldg(P.keys + ni) : 0;
+    // fused lookup: the backup filter's block is fetched while L1 runs
+    bool in_backup = false;
+    if (P.mode == 5) {
+      uint32_t hlo, bw[8];
+      backup_load(P, key, hlo, bw);
+      in_backup = backup_test(hlo, bw);
+    }
     // epilogue 1: D1 (columns 0..127) -> A2 = 128 + h1 packed in columns 0..63
     if (!wait_on(0)) { failed = 0; break; }
     requant_run<4>(tm_row, tm_row);
@@ -329,19 +358,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ 
     }
     // the next tile's A1 while L2 runs (L1, its only reader, is complete)
     if (ntile < ntiles) build_a1(nkey);
-    // epilogue 2: D2 (columns 64..127) -> A3 = 128 + h2 packed in columns 0..31
+    // epilogue 2 and layer 3: D2 (columns 64..127) -> 128 + h2 (bf16, exact) ->
+    // dot product with W3q in fp32 (integer partial sums below 2^24: exact)
     if (!wait_on(1)) { failed = 1; break; }
-    requant_run<2>(tm_row + 64, tm_row);
-    tmem_stores_done();
-    if (r == 0) {
-      fence_after();
+    float acc3 = 0.f;
+    {
+      uint32_t a[32], b[32];
+      LBF_LD32(a, tm_row + 64);
+      LBF_LD32(b, tm_row + 96);
+      tmem_wait_ld();
 #pragma unroll
-      for (uint32_t s = 0; s < 4; ++s) mma_bf16_ta(tm + 64, tm + 8 * s, sdesc(sb + kB3 + s * 32), idesc(16), s);
-      mma_commit(bars + 16);
+      for (int p = 0; p < 16; ++p) {
+        const uint32_t w = requant2(__uint_as_float(a[2 * p]), __uint_as_float(a[2 * p + 1]));
+        acc3 = fmaf(__uint_as_float(w << 16), P.w3[2 * p], acc3);
+        acc3 = fmaf(__uint_as_float(w & 0xFFFF0000u), P.w3[2 * p + 1], acc3);
+      }
+#pragma unroll
+      for (int p = 0; p < 16; ++p) {
+        const uint32_t w = requant2(__uint_as_float(b[2 * p]), __uint_as_float(b[2 * p + 1]));
+        acc3 = fmaf(__uint_as_float(w << 16), P.w3[32 + 2 * p], acc3);
+        acc3 = fmaf(__uint_as_float(w & 0xFFFF0000u), P.w3[32 + 2 * p + 1], acc3);
+      }
     }
-    if (!wait_on(2)) { failed = 2; break; }
-    // score: column 64
-    const float acc3 = tmem_ld1(tm_row + 64);
     fence_before();
     // the next L1 overwrites these columns: warp 0 waits for every warp's load
     if ((r >> 5) == 0)
@@ -355,6 +393,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ 
       if (live) P.out32[i] = static_cast<int32_t>(sc);
     } else if (P.mode == 1) {
       if (live && sc >= P.tau) P.out8[i] = 1;
+    } else if (P.mode == 5) {
+      if (live) P.out8[i] = (sc >= P.tau || in_backup) ? 1 : 0;
     } else {
       const bool take = live && sc < P.tau;
       const unsigned vote = __ballot_sync(0xFFFFFFFFu, take);
@@ -427,10 +467,7 @@ bool tc_prepare(const bf_mlp_int8* m, TcModel* out) {
     for (uint32_t i = 0; i < 128; ++i)
       put16(img, kB2 + (i >> 6) * 8192u + swz_host(j, i & 63u), bf16_of(m->w2[i * 64 + j] * s2));
   long long sum3 = 0;
-  for (uint32_t i = 0; i < 64; ++i) {
-    put16(img, kB3 + swz_host(0, i), bf16_of(m->w3[i]));
-    sum3 += m->w3[i];
-  }
+  for (uint32_t i = 0; i < 64; ++i) sum3 += m->w3[i];
   for (uint32_t b = 0; b < 256; ++b)
     for (uint32_t e = 0; e < 8; ++e) put16(img, kLut + b * 16 + e * 2, ((b >> e) & 1u) ? 0x3F80 : 0);
   for (uint32_t r = 0; r < 128; ++r)
@@ -452,6 +489,7 @@ bool tc_prepare(const bf_mlp_int8* m, TcModel* out) {
     for (uint32_t k = 0; k < 3; ++k) put16(img, kB2b + swz_host(j, k), pc[k]);
   }
   out->s3 = static_cast<long long>(m->b3) - 128 * sum3;
+  for (int i = 0; i < 64; ++i) out->w3[i] = static_cast<float>(m->w3[i]);
   out->image = std::move(img);
   return true;
 }
@@ -460,7 +498,7 @@ uint32_t tc_image_bytes() { return kImage; }
 
 cudaError_t tc_run(const uint8_t* d_image, const TcModel& tm, const uint64_t* d_keys, uint64_t n, int mode, int tau,
                    int32_t* out32, uint8_t* out8, unsigned long long* count, uint64_t* out_keys, unsigned int* err,
-                   cudaStream_t st) {
+                   cudaStream_t st, const TcBackup* backup) {
   if (n == 0) return cudaSuccess;
   static thread_local int configured_device = -1;
   int dev = 0, sms = 0;
@@ -485,6 +523,12 @@ cudaError_t tc_run(const uint8_t* d_image, const TcModel& tm, const uint64_t* d_
   a.out_keys = out_keys;
   a.err = err;
   a.s3 = tm.s3;
+  std::memcpy(a.w3, tm.w3, sizeof(a.w3));
+  a.bk_words = backup ? backup->words : nullptr;
+  a.bk_blocks = backup ? backup->num_blocks : 0;
+  a.bk_acc0 = backup ? bloomgb::xxh64_acc0(backup->seed) : 0;
+  a.bk_mode = backup ? bloomgb::block_mode(backup->num_blocks) : 0;
+  if (mode == 5 && !backup) return cudaErrorInvalidValue;
   k_tc_mlp<<<grid, kThreads, kSmemBytes, st>>>(a);
   return cudaGetLastError();
 }

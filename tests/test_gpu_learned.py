@@ -295,25 +295,28 @@ def small_learned(torch, data):
     return m, ref
 
 
+@pytest.mark.parametrize("geom", [(256, 32, 8), (512, 64, 16)])
 @pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("quantile", [0.0, 0.3, 0.9, 1.0])
-def test_learned_lookup_matches_oracle(torch, data, small_learned, quantile, engine):
+def test_learned_lookup_matches_oracle(torch, data, small_learned, quantile, engine, geom):
+    """(256, 32, 8) with the tensor engine is the fused kernel (model and backup
+    probe in one launch); the other cases run the backup lookup first."""
     from paper_2512_15595_gb300.learned import LearnedFilter
     mem, non, _, _ = data
     m, ref = small_learned
     m.set_engine(engine_id(engine))
+    B, S, K = geom
     sm = OL.int_scores(ref, mem)
     tau = int(np.quantile(sm, quantile)) + (1 if quantile == 1.0 else 0)
     fn_ref = mem[sm < tau]
     blocks = 37
-    lf = LearnedFilter(m, tau, dev(torch, mem), backup_blocks=blocks, seed=3)
+    lf = LearnedFilter(m, tau, dev(torch, mem), backup_blocks=blocks, block_bits=B, word_bits=S, k=K, seed=3)
     assert lf.n_backup == fn_ref.size
     # compaction: the same set of keys
     out, cnt = m.select_below(tau, dev(torch, mem))
     assert np.array_equal(np.sort(out[:cnt].cpu().numpy().view(np.uint64)), np.sort(fn_ref))
     # backup filter: identical bit array to the oracle's built from the same keys
-    geom = oracle.Geometry(num_blocks=blocks, block_bits=256, word_bits=32, k=8, seed=3)
-    ob = oracle.SBF(geom)
+    ob = oracle.SBF(oracle.Geometry(num_blocks=blocks, block_bits=B, word_bits=S, k=K, seed=3))
     ob.add(fn_ref)
     assert np.array_equal(lf.backup.words.cpu().numpy(), ob.as_bytes())
     q = np.concatenate([mem, non, ragged_keys(3001, 43)])
