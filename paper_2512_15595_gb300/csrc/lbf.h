@@ -20,11 +20,13 @@ constexpr int kImgW1 = 0, kImgW2 = kImgW1 + kH1 * kIn, kImgW3 = kImgW2 + kH2 * k
 void image_of(const bf_mlp_int8* m, std::vector<unsigned char>& img);
 
 // Tensor-core form of a model (see lbf_tc.cu): the operand image copied to
-// shared memory (weights, bias pieces, constant columns, bit table) and the
-// score offset.
+// shared memory (weights, bit table), the per-unit requantization constants,
+// W3q and the score offset.
 struct TcModel {
   std::vector<uint8_t> image;
   long long s3;
+  float c1[128];
+  float c2[64];
   float w3[64];
 };
 

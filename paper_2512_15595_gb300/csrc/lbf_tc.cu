@@ -1,19 +1,17 @@
 // Learned prefilter, integer model on the 5th-generation tensor cores.
 //
 // The exported model is integer arithmetic (int8 weights, ReLU + shift +
-// saturation, int32 score).  sm_103a has no int8 tensor-core MMA, so the
-// three products run as bf16 MMAs with fp32 accumulation (tcgen05.mma
+// saturation, int32 score).  sm_103a has no int8 tensor-core MMA, so the two
+// matrix products run as bf16 MMAs with fp32 accumulation (tcgen05.mma
 // kind::f16) on values chosen so that every product and every partial sum is
 // an exactly representable integer multiple of a power of two:
 //   * A1 = the key bits (0/1), B1 = W1q * 2^-sh1 (int8 times a power of two:
 //     exact in bf16); |sum x W1q| <= 64 * 127.
-//   * a per-column constant c1 = (b1' + 128 * 2^sh1) 2^-sh1 enters through a
-//     16-wide extra k-block (three constant-one columns of A times c1 split
-//     into three bf16 pieces), so y1 = 128 + a1 / 2^sh1 exactly (b1' = b1q
-//     clamped to the range where it still changes the result); the epilogue
-//     converts to bf16 rounding toward zero (the bf16 spacing on [128, 256)
-//     is 1, so this is the floor) and clamps to [128, 255]: A2 = 128 + h1,
-//     exact in bf16.
+//   * the epilogue adds a per-unit fp32 constant c1 = (b1' + 128 * 2^sh1)
+//     2^-sh1 (b1' = b1q clamped to the range where it still changes the
+//     result), so y1 = 128 + a1 / 2^sh1 exactly, converts to bf16 rounding
+//     toward zero (the bf16 spacing on [128, 256) is 1, so this is the floor)
+//     and clamps to [128, 255]: A2 = 128 + h1, exact in bf16.
 //   * B2 = W2q * 2^-sh2; the offset 128 * colsum(W2q) is folded into c2, and
 //     likewise 128 + h2 (exact in bf16 and fp32) is dotted with W3q on the
 //     CUDA cores in fp32 (integer partial sums below 2^24), score = acc3 +
@@ -22,21 +20,22 @@
 // other models use the dp4a kernel), so the results equal the integer
 // model's bit for bit.
 //
-// Kernel shape: persistent, one CTA per SM, four warpgroups.  Each warpgroup
-// owns 16 KiB of shared memory (A1) and 128 TMEM columns and runs its tiles of
-// 128 keys through MMA L1 -> epilogue -> MMA L2 -> epilogue with layer 3 ->
-// score on its own; one elected thread issues its MMAs and commits them to the
-// warpgroup's mbarriers.  Four independent pipelines keep the tensor core
-// busy while the other warpgroups run their epilogues.  The activations stay
-// in tensor memory: each epilogue reads its fp32 accumulator row, packs the
-// requantized bf16 pairs and stores them back into columns already consumed,
-// and the next MMA takes its A operand from there (so L2 reads only B from
-// shared memory).  TMEM columns of a warpgroup over one tile:
+// Kernel shape: persistent, one CTA per SM, warp-specialized: four epilogue
+// warpgroups and one MMA warp.  Each warpgroup owns 16 KiB of shared memory
+// (A1) and 128 TMEM columns and walks its tiles of 128 keys (one key per
+// thread, one TMEM lane per key): it writes A1 and signals the MMA warp,
+// waits for L1, requantizes (TMEM -> registers -> TMEM), signals, writes the
+// next tile's A1 while L2 runs, waits for L2, finishes layer 3 and the score,
+// and releases its TMEM columns to the next L1.  The MMA warp's elected thread
+// issues every product (L1 of each warpgroup, then L2 of each, in turn) and
+// commits it to that warpgroup's mbarrier, so no epilogue thread ever blocks
+// on issuing MMAs.
+// All waits are bounded (2 s); a time-out sets the model's error word.
+// TMEM columns of a warpgroup over one tile:
 //   L1: D1 -> 0..127;  E1: A2 (128 bf16 = 64 columns) -> 0..63;
-//   L2: A = 0..63, D2 -> 64..127;  E2: reads 64..127.
-// Shared-memory operands (A1, weights, bias pieces) use the K-major
-// 128-byte-swizzled layout (8-row groups of 128-byte rows, 16-byte chunks
-// XOR-permuted by row); the next tile's A1 is written while L2 runs.
+//   L2: A = 0..63 (A from tensor memory), D2 -> 64..127;  E2: reads 64..127.
+// Shared-memory operands (A1, B1, B2) use the K-major 128-byte-swizzled
+// layout (8-row groups of 128-byte rows, 16-byte chunks XOR-permuted by row).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,21 +53,22 @@ namespace {
 // shared-memory map (offsets from a 1024-byte aligned base)
 constexpr uint32_t kB1 = 0;                     // 128 rows (unit j) x 64 bf16 (input i)
 constexpr uint32_t kB2 = kB1 + 128 * 128;       // 2 k-blocks x 64 rows x 64 bf16
-constexpr uint32_t kB1b = kB2 + 2 * 64 * 128;   // 128 rows: the three bf16 pieces of c1 (k = 0..2)
-constexpr uint32_t kB2b = kB1b + 128 * 128;     // 64 rows: the pieces of c2
-constexpr uint32_t kAc = kB2b + 64 * 128;       // 128 rows: ones at k = 0..2
-constexpr uint32_t kLut = kAc + 128 * 128;      // 256 x 8 bf16: bits of a byte as 0/1
-constexpr uint32_t kImage = kLut + 256 * 16;    // bytes copied from the device image
-constexpr uint32_t kSlots = kImage;             // 4 slots of 16 KiB (A1)
+constexpr uint32_t kImage = kB2 + 2 * 64 * 128;  // bytes copied from the device image
+constexpr uint32_t kSlots = (kImage + 1023) / 1024 * 1024;  // 4 slots of 16 KiB (A1)
 constexpr uint32_t kSlotBytes = 16384;
 constexpr int kWG = 4;
 constexpr uint32_t kBar = kSlots + kWG * kSlotBytes;  // 4 mbarriers per warpgroup, TMEM base, flags
-constexpr uint32_t kSmemBytes = kBar + 256 + 1024;    // + alignment slack
-static_assert(kSlots % 1024 == 0 && kB1b % 1024 == 0 && kB2b % 1024 == 0 && kAc % 1024 == 0,
-              "swizzled operands must be 1024-byte aligned");
+// + alignment slack; at least 120 KiB so that no second CTA (which would
+// wait for this one's tensor memory) is ever placed on the same SM
+constexpr uint32_t kSmemBytes = kBar + 256 + 1024 > 120 * 1024 ? kBar + 256 + 1024 : 120 * 1024;
+static_assert(kSlots % 1024 == 0 && kB2 % 1024 == 0, "swizzled operands must be 1024-byte aligned");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
-constexpr int kThreads = 128 * kWG;
+constexpr int kEpiThreads = 128 * kWG;
+constexpr int kThreads = kEpiThreads + 32;  // + the MMA warp
 constexpr uint32_t kTmemCols = 512;
+// mbarriers of a warpgroup: A1 ready (128 arrivals), A2 ready (128), D1 full
+// and D2 full (one tcgen05.commit each)
+constexpr int kBarA1 = 0, kBarA2 = 1, kBarD1 = 2, kBarD2 = 3;
 
 // instruction descriptor, kind::f16: fp32 D, bf16 A and B, both K-major, M = 128
 __host__ __device__ constexpr uint32_t idesc(uint32_t n) {
@@ -88,7 +88,9 @@ struct TcArgs {
   uint64_t* out_keys;
   unsigned int* err;
   long long s3;
-  float w3[64];  // W3q as fp32 (layer 3 runs on the CUDA cores)
+  float c1[128];  // per-unit constants of the two requantizations
+  float c2[64];
+  float w3[64];   // W3q as fp32 (layer 3 runs on the CUDA cores)
   // mode 5: the backup filter (256-bit blocks, S = 32, K = 8, sectorized)
   const uint32_t* bk_words;
   uint64_t bk_blocks;
@@ -179,11 +181,6 @@ __device__ __forceinline__ void sts128(uint32_t a, uint32_t x, uint32_t y, uint3
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
 }
 
-__device__ __forceinline__ uint4 lds128(uint32_t a) {
-  uint4 v;
-  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
-  return v;
-}
 
 
 // bf16 pair: floor of (lo, hi) on [128, 256) by conversion toward zero, then clamped to [128, 255]
@@ -221,34 +218,136 @@ __device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t chunk) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// 32 loaded accumulator columns -> 16 columns of packed bf16 (128 + h) at `to`
-__device__ __forceinline__ void requant_store(const uint32_t (&a)[32], uint32_t to) {
+// two fp32 lanes in one 64-bit register pair (sm_100 f32x2 arithmetic)
+__device__ __forceinline__ uint64_t pack2(uint32_t lo, uint32_t hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+  return r;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ float lo_of(uint64_t v) { return __uint_as_float(static_cast<uint32_t>(v)); }
+__device__ __forceinline__ float hi_of(uint64_t v) { return __uint_as_float(static_cast<uint32_t>(v >> 32)); }
+
+// 32 loaded accumulator columns of layer L (first unit u0) -> 16 columns of
+// packed bf16 (128 + h) at `to`
+template <int L>
+__device__ __forceinline__ void requant_store(const TcArgs& P, const uint32_t (&a)[32], int u0, uint32_t to) {
+  const float* c = L == 1 ? P.c1 : P.c2;
   uint32_t w[16];
 #pragma unroll
-  for (int p = 0; p < 16; ++p) w[p] = requant2(__uint_as_float(a[2 * p]), __uint_as_float(a[2 * p + 1]));
+  for (int p = 0; p < 16; ++p) {
+    const uint64_t y = add2(pack2(a[2 * p], a[2 * p + 1]),
+                            pack2(__float_as_uint(c[u0 + 2 * p]), __float_as_uint(c[u0 + 2 * p + 1])));
+    w[p] = requant2(lo_of(y), hi_of(y));
+  }
   LBF_ST16(to, w);
 }
 
-// Accumulator columns from[0 .. 32 NC) -> packed bf16 columns to[0 .. 16 NC),
-// in chunks of 32 columns with the next chunk's load in flight while the
-// current one is converted.  Chunk c is stored over columns that chunk c/2
-// already loaded (to <= from), so no store overwrites an unread column.
-template <int NC>
-__device__ __forceinline__ void requant_run(uint32_t from, uint32_t to) {
+// Layer-1 accumulators (columns from[0..128)) -> packed bf16 at to[0..64), in
+// chunks of 32 columns with the next chunk's load in flight while the current
+// one is converted; chunk c is stored over columns that chunk c/2 already
+// loaded (to <= from), so no store overwrites an unread column.
+__device__ __forceinline__ void epilogue1(const TcArgs& P, uint32_t from, uint32_t to) {
   uint32_t a[32], b[32];
   LBF_LD32(a, from);
   tmem_wait_ld();
+  LBF_LD32(b, from + 32);
+  requant_store<1>(P, a, 0, to);
+  tmem_wait_ld();
+  LBF_LD32(a, from + 64);
+  requant_store<1>(P, b, 32, to + 16);
+  tmem_wait_ld();
+  LBF_LD32(b, from + 96);
+  requant_store<1>(P, a, 64, to + 32);
+  tmem_wait_ld();
+  requant_store<1>(P, b, 96, to + 48);
+}
+
+// Layer-2 accumulators (64 columns at `from`) -> 128 + h2 -> dot with W3q
+// (fp32, even and odd units in the two lanes; every partial sum is an integer
+// below 2^24, so exact)
+__device__ __forceinline__ float epilogue2(const TcArgs& P, uint32_t from) {
+  uint32_t a[32], b[32];
+  LBF_LD32(a, from);
+  LBF_LD32(b, from + 32);
+  tmem_wait_ld();
+  auto cp = [&](int u) { return pack2(__float_as_uint(P.c2[u]), __float_as_uint(P.c2[u + 1])); };
+  auto wp = [&](int u) { return pack2(__float_as_uint(P.w3[u]), __float_as_uint(P.w3[u + 1])); };
+  uint64_t acc = 0;
 #pragma unroll
-  for (int c = 0; c < NC; c += 2) {
-    if (c + 1 < NC) LBF_LD32(b, from + 32 * (c + 1));
-    requant_store(a, to + 16 * c);
-    if (c + 1 < NC) {
-      tmem_wait_ld();
-      if (c + 2 < NC) LBF_LD32(a, from + 32 * (c + 2));
-      requant_store(b, to + 16 * (c + 1));
-      if (c + 2 < NC) tmem_wait_ld();
+  for (int p = 0; p < 16; ++p) {
+    const uint64_t y = add2(pack2(a[2 * p], a[2 * p + 1]), cp(2 * p));
+    const uint32_t w = requant2(lo_of(y), hi_of(y));
+    acc = fma2(pack2(w << 16, w & 0xFFFF0000u), wp(2 * p), acc);
+  }
+#pragma unroll
+  for (int p = 0; p < 16; ++p) {
+    const uint64_t y = add2(pack2(b[2 * p], b[2 * p + 1]), cp(32 + 2 * p));
+    const uint32_t w = requant2(lo_of(y), hi_of(y));
+    acc = fma2(pack2(w << 16, w & 0xFFFF0000u), wp(32 + 2 * p), acc);
+  }
+  return lo_of(acc) + hi_of(acc);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ uint64_t tiles_of(uint64_t ntiles, uint64_t first, uint64_t stride) {
+  return first < ntiles ? (ntiles - first + stride - 1) / stride : 0;
+}
+
+// The MMA warp's elected thread issues the warpgroups' products in a fixed
+// round: L1 of every warpgroup, then L2 of every warpgroup, and so on (the
+// warpgroups run the same work, so they become ready in about this order).
+// Each wait is a blocking try_wait (the thread sleeps in hardware).  Returns
+// false when a request did not come within 2 s.
+__device__ bool mma_issuer(uint32_t sb, uint32_t tmem, uint64_t ntiles) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWG;
+  uint64_t left[kWG];
+  uint64_t most = 0;
+  for (int w = 0; w < kWG; ++w) {
+    left[w] = tiles_of(ntiles, static_cast<uint64_t>(blockIdx.x) * kWG + w, stride);
+    most = left[w] > most ? left[w] : most;
+  }
+  const uint64_t limit = 2000000000ull;
+  for (uint64_t t = 0; t < most; ++t) {
+    const uint32_t ph = static_cast<uint32_t>(t & 1);
+#pragma unroll
+    for (int w = 0; w < kWG; ++w) {
+      if (t >= left[w]) continue;
+      const uint32_t bars = sb + kBar + 32 * w;
+      if (!mbar_wait(bars + 8 * kBarA1, ph, limit)) return false;
+      fence_after();
+      const uint32_t a1 = sb + kSlots + w * kSlotBytes;
+      const uint32_t tm = tmem + 128 * w;
+#pragma unroll
+      for (uint32_t s = 0; s < 4; ++s) mma_bf16(tm, sdesc(a1 + s * 32), sdesc(sb + kB1 + s * 32), idesc(128), s);
+      mma_commit(bars + 8 * kBarD1);
+    }
+#pragma unroll
+    for (int w = 0; w < kWG; ++w) {
+      if (t >= left[w]) continue;
+      const uint32_t bars = sb + kBar + 32 * w;
+      if (!mbar_wait(bars + 8 * kBarA2, ph, limit)) return false;
+      fence_after();
+      const uint32_t tm = tmem + 128 * w;
+#pragma unroll
+      for (uint32_t s = 0; s < 8; ++s)
+        mma_bf16_ta(tm + 64, tm + 8 * s, sdesc(sb + kB2 + (s >> 2) * 8192u + (s & 3) * 32), idesc(64), s);
+      mma_commit(bars + 8 * kBarD2);
     }
   }
+  return true;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ TcArgs P) {
@@ -263,11 +362,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ 
   uint32_t* holder = reinterpret_cast<uint32_t*>(smem + kBar + 128);
   volatile int* flag = reinterpret_cast<volatile int*>(smem + kBar + 144);
   if (tid == 0) {
-    for (int s = 0; s < 4 * kWG; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sb + kBar + 8 * s) : "memory");
+    for (int w = 0; w < kWG; ++w) {
+      const uint32_t bars = sb + kBar + 32 * w;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(bars + 8 * kBarA1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(bars + 8 * kBarA2) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars + 8 * kBarD1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars + 8 * kBarD2) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  const int mma_warp = kEpiThreads / 32;
+  if (warp == mma_warp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
                  "r"(kTmemCols)
                  : "memory");
@@ -278,142 +383,109 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ 
   __syncthreads();
   fence_after();
   const uint32_t tmem = *holder;
-
-  const int wg = tid >> 7;
-  const uint32_t r = tid & 127;
-  const uint32_t a1 = sb + kSlots + wg * kSlotBytes;   // this warpgroup's A1 (shared memory)
-  const uint32_t bars = sb + kBar + 32 * wg;           // commits of L1, L2
-  const uint32_t tm = tmem + wg * 128;                  // this warpgroup's columns
-  const uint32_t tm_row = tm + ((r & ~31u) << 16);      // this warp's lane quarter
   const uint64_t ntiles = (P.n + 127) / 128;
-  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWG;
   const uint64_t limit = 2000000000ull;
-  uint32_t phase = 0;  // each barrier completes once per tile
-  int failed = -1;
 
-  // one elected thread waits (bounded) on a commit; the warpgroup then agrees
-  // on the outcome through a named barrier (a flag slot per barrier)
-  auto wait_on = [&](int which) -> bool {
-    if (r == 0) flag[4 * wg + which] = mbar_wait(bars + 8 * which, phase, limit) ? 0 : 1;
-    wg_bar(1 + wg);
-    fence_after();
-    return flag[4 * wg + which] == 0;
-  };
-  // A1 of a tile: row r = the 64 key bits as bf16 0 / 1
-  auto build_a1 = [&](uint64_t key) {
-#pragma unroll
-    for (uint32_t c = 0; c < 8; ++c) {
-      const uint4 v = lds128(sb + kLut + ((static_cast<uint32_t>(key >> (8 * c)) & 0xFFu) << 4));
-      sts128(a1 + swz(r, c), v.x, v.y, v.z, v.w);
-    }
-    fence_async_smem();
-  };
-  // make this thread's TMEM stores visible to the MMA issued after the barrier
-  auto tmem_stores_done = [&]() {
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    fence_before();
-    wg_bar(1 + wg);
-  };
+  if (warp == mma_warp) {
+    if ((tid & 31) == 0 && !mma_issuer(sb, tmem, ntiles)) atomicOr(P.err, 1u);
+  } else {
+    const int wg = tid >> 7;
+    const uint32_t r = tid & 127;
+    const uint32_t a1 = sb + kSlots + wg * kSlotBytes;  // this warpgroup's A1 (shared memory)
+    const uint32_t bars = sb + kBar + 32 * wg;
+    const uint32_t tm = tmem + wg * 128;                 // this warpgroup's columns
+    const uint32_t tm_row = tm + ((r & ~31u) << 16);     // this warp's lane quarter
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWG;
+    uint32_t phase = 0;  // each barrier completes once per tile
+    bool failed = false;
 
-  uint64_t tile = static_cast<uint64_t>(blockIdx.x) * kWG + wg;
-  uint64_t key = 0;
-  if (tile < ntiles) {
-    const uint64_t i0 = tile * 128 + r;
-    key = i0 < P.n ? __ldg(P.keys + i0) : 0;
-    build_a1(key);
-    wg_bar(1 + wg);
-  }
-  for (; tile < ntiles; tile += stride) {
-    const uint64_t i = tile * 128 + r;
-    const bool live = i < P.n;
-    if (r == 0) {
+    // one elected thread waits (bounded) on a commit; the warpgroup then
+    // agrees on the outcome through a named barrier (a flag slot per barrier)
+    auto wait_on = [&](int which) -> bool {
+      if (r == 0) flag[4 * wg + which] = mbar_wait(bars + 8 * which, phase, limit) ? 0 : 1;
+      wg_bar(1 + wg);
       fence_after();
+      return flag[4 * wg + which] == 0;
+    };
+    // A1 of a tile: row r = the 64 key bits as bf16 0 / 1.  For 16 bits x,
+    // X = (even bits of x) | (odd bits of x) << 16 puts bits 2j and 2j+1 at
+    // positions 2j and 16 + 2j, so ((X >> 2j) & 0x10001) * 0x3F80 is the bf16
+    // pair (bit 2j, bit 2j+1) with 1.0 = 0x3F80.
+    auto build_a1 = [&](uint64_t key) {
 #pragma unroll
-      for (uint32_t s = 0; s < 4; ++s) mma_bf16(tm, sdesc(a1 + s * 32), sdesc(sb + kB1 + s * 32), idesc(128), s);
-      mma_bf16(tm, sdesc(sb + kAc), sdesc(sb + kB1b), idesc(128), 1);
-      mma_commit(bars);
-    }
-    // the next tile's keys, loaded early
-    const uint64_t ntile = tile + stride;
-    const uint64_t ni = ntile * 128 + r;
-    const uint64_t nkey = (ntile < ntiles && ni < P.n) ? __ldg(P.keys + ni) : 0;
-    // fused lookup: the backup filter's block is fetched while L1 runs
-    bool in_backup = false;
-    if (P.mode == 5) {
-      uint32_t hlo, bw[8];
-      backup_load(P, key, hlo, bw);
-      in_backup = backup_test(hlo, bw);
-    }
-    // epilogue 1: D1 (columns 0..127) -> A2 = 128 + h1 packed in columns 0..63
-    if (!wait_on(0)) { failed = 0; break; }
-    requant_run<4>(tm_row, tm_row);
-    tmem_stores_done();
-    if (r == 0) {
-      fence_after();
+      for (uint32_t g = 0; g < 4; ++g) {
+        const uint32_t x = static_cast<uint32_t>(key >> (16 * g)) & 0xFFFFu;
+        const uint32_t X = (x & 0x5555u) | (((x >> 1) & 0x5555u) << 16);
+        uint32_t w[8];
 #pragma unroll
-      for (uint32_t s = 0; s < 8; ++s)
-        mma_bf16_ta(tm + 64, tm + 8 * s, sdesc(sb + kB2 + (s >> 2) * 8192u + (s & 3) * 32), idesc(64), s);
-      mma_bf16(tm + 64, sdesc(sb + kAc), sdesc(sb + kB2b), idesc(64), 1);
-      mma_commit(bars + 8);
-    }
-    // the next tile's A1 while L2 runs (L1, its only reader, is complete)
-    if (ntile < ntiles) build_a1(nkey);
-    // epilogue 2 and layer 3: D2 (columns 64..127) -> 128 + h2 (bf16, exact) ->
-    // dot product with W3q in fp32 (integer partial sums below 2^24: exact)
-    if (!wait_on(1)) { failed = 1; break; }
-    float acc3 = 0.f;
-    {
-      uint32_t a[32], b[32];
-      LBF_LD32(a, tm_row + 64);
-      LBF_LD32(b, tm_row + 96);
-      tmem_wait_ld();
-#pragma unroll
-      for (int p = 0; p < 16; ++p) {
-        const uint32_t w = requant2(__uint_as_float(a[2 * p]), __uint_as_float(a[2 * p + 1]));
-        acc3 = fmaf(__uint_as_float(w << 16), P.w3[2 * p], acc3);
-        acc3 = fmaf(__uint_as_float(w & 0xFFFF0000u), P.w3[2 * p + 1], acc3);
+        for (uint32_t j = 0; j < 8; ++j) w[j] = ((X >> (2 * j)) & 0x00010001u) * 0x3F80u;
+        sts128(a1 + swz(r, 2 * g), w[0], w[1], w[2], w[3]);
+        sts128(a1 + swz(r, 2 * g + 1), w[4], w[5], w[6], w[7]);
       }
-#pragma unroll
-      for (int p = 0; p < 16; ++p) {
-        const uint32_t w = requant2(__uint_as_float(b[2 * p]), __uint_as_float(b[2 * p + 1]));
-        acc3 = fmaf(__uint_as_float(w << 16), P.w3[32 + 2 * p], acc3);
-        acc3 = fmaf(__uint_as_float(w & 0xFFFF0000u), P.w3[32 + 2 * p + 1], acc3);
+      fence_async_smem();
+    };
+
+    uint64_t tile = static_cast<uint64_t>(blockIdx.x) * kWG + wg;
+    uint64_t key = 0;
+    if (tile < ntiles) {
+      const uint64_t i0 = tile * 128 + r;
+      key = i0 < P.n ? __ldg(P.keys + i0) : 0;
+      build_a1(key);
+      mbar_arrive(bars + 8 * kBarA1);
+    }
+    for (; tile < ntiles; tile += stride) {
+      const uint64_t i = tile * 128 + r;
+      const bool live = i < P.n;
+      // the next tile's keys, loaded early
+      const uint64_t ntile = tile + stride;
+      const uint64_t ni = ntile * 128 + r;
+      const uint64_t nkey = (ntile < ntiles && ni < P.n) ? __ldg(P.keys + ni) : 0;
+      // fused lookup: the backup filter's block is fetched while L1 runs
+      bool in_backup = false;
+      if (P.mode == 5) {
+        uint32_t hlo, bw[8];
+        backup_load(P, key, hlo, bw);
+        in_backup = backup_test(hlo, bw);
       }
+      // epilogue 1: D1 (columns 0..127) + c1 -> A2 = 128 + h1 packed in columns 0..63
+      if (!wait_on(kBarD1)) { failed = true; break; }
+      epilogue1(P, tm_row, tm_row);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      fence_before();
+      mbar_arrive(bars + 8 * kBarA2);
+      // the next tile's A1 while L2 runs (L1, its only reader, is complete)
+      if (ntile < ntiles) build_a1(nkey);
+      // epilogue 2 and layer 3: D2 (columns 64..127)
+      if (!wait_on(kBarD2)) { failed = true; break; }
+      const float acc3 = epilogue2(P, tm_row + 64);
+      fence_before();
+      // TMEM and the next A1 are ready for the next L1
+      if (ntile < ntiles) mbar_arrive(bars + 8 * kBarA1);
+      phase ^= 1;
+      long long sc = static_cast<long long>(__float2int_rn(acc3)) + P.s3;
+      sc = sc < INT32_MIN ? INT32_MIN : (sc > INT32_MAX ? INT32_MAX : sc);
+      if (P.mode == 0) {
+        if (live) P.out32[i] = static_cast<int32_t>(sc);
+      } else if (P.mode == 1) {
+        if (live && sc >= P.tau) P.out8[i] = 1;
+      } else if (P.mode == 5) {
+        if (live) P.out8[i] = (sc >= P.tau || in_backup) ? 1 : 0;
+      } else {
+        const bool take = live && sc < P.tau;
+        const unsigned vote = __ballot_sync(0xFFFFFFFFu, take);
+        const uint32_t lane = r & 31u;
+        unsigned long long base = 0;
+        if (lane == 0 && vote) base = atomicAdd(P.count, static_cast<unsigned long long>(__popc(vote)));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (take) P.out_keys[base + __popc(vote & ((1u << lane) - 1u))] = key;
+      }
+      key = nkey;
     }
-    fence_before();
-    // the next L1 overwrites these columns: warp 0 waits for every warp's load
-    if ((r >> 5) == 0)
-      asm volatile("bar.sync %0, 128;" ::"r"(5 + wg) : "memory");
-    else
-      asm volatile("bar.arrive %0, 128;" ::"r"(5 + wg) : "memory");
-    phase ^= 1;
-    long long sc = static_cast<long long>(__float2int_rn(acc3)) + P.s3;
-    sc = sc < INT32_MIN ? INT32_MIN : (sc > INT32_MAX ? INT32_MAX : sc);
-    if (P.mode == 0) {
-      if (live) P.out32[i] = static_cast<int32_t>(sc);
-    } else if (P.mode == 1) {
-      if (live && sc >= P.tau) P.out8[i] = 1;
-    } else if (P.mode == 5) {
-      if (live) P.out8[i] = (sc >= P.tau || in_backup) ? 1 : 0;
-    } else {
-      const bool take = live && sc < P.tau;
-      const unsigned vote = __ballot_sync(0xFFFFFFFFu, take);
-      const uint32_t lane = r & 31u;
-      unsigned long long base = 0;
-      if (lane == 0 && vote) base = atomicAdd(P.count, static_cast<unsigned long long>(__popc(vote)));
-      base = __shfl_sync(0xFFFFFFFFu, base, 0);
-      if (take) P.out_keys[base + __popc(vote & ((1u << lane) - 1u))] = key;
-    }
-    key = nkey;
-  }
-  if (failed >= 0 && r == 0) {
-    atomicOr(P.err, 1u);
-    // the MMAs still in flight, once more (bounded)
-    mbar_wait(bars + 8 * failed, phase, limit / 4);
+    if (failed && r == 0) atomicOr(P.err, 1u);
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == mma_warp) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
@@ -435,24 +507,6 @@ uint32_t swz_host(uint32_t row, uint32_t k) {  // element k (< 64) of a 128-byte
   return row * 128u + ((((k >> 3) ^ (row & 7u)) & 7u) << 4) + (k & 7u) * 2u;
 }
 
-// c (an fp32 value with at most 24 significant bits) as three bf16 pieces
-// whose sum is c exactly; false if that does not hold
-bool split3(float c, uint16_t (&p)[3]) {
-  float rest = c;
-  double exact = 0.0;
-  for (int i = 0; i < 3; ++i) {
-    uint32_t u;
-    std::memcpy(&u, &rest, 4);
-    p[i] = static_cast<uint16_t>(u >> 16);  // truncation keeps the top 8 significant bits
-    const uint32_t t = static_cast<uint32_t>(p[i]) << 16;
-    float v;
-    std::memcpy(&v, &t, 4);
-    rest = rest - v;  // exact: v is a prefix of rest's bits
-    exact += static_cast<double>(v);
-  }
-  return rest == 0.f && exact == static_cast<double>(c);
-}
-
 }  // namespace
 
 bool tc_eligible(const bf_mlp_int8* m) { return m->sh1 >= 0 && m->sh1 <= 15 && m->sh2 >= 0 && m->sh2 <= 15; }
@@ -468,25 +522,22 @@ bool tc_prepare(const bf_mlp_int8* m, TcModel* out) {
       put16(img, kB2 + (i >> 6) * 8192u + swz_host(j, i & 63u), bf16_of(m->w2[i * 64 + j] * s2));
   long long sum3 = 0;
   for (uint32_t i = 0; i < 64; ++i) sum3 += m->w3[i];
-  for (uint32_t b = 0; b < 256; ++b)
-    for (uint32_t e = 0; e < 8; ++e) put16(img, kLut + b * 16 + e * 2, ((b >> e) & 1u) ? 0x3F80 : 0);
-  for (uint32_t r = 0; r < 128; ++r)
-    for (uint32_t k = 0; k < 3; ++k) put16(img, kAc + swz_host(r, k), 0x3F80);
+  // per-unit constants: integers below 2^24 times 2^-sh, exact in fp32
   const long long A1 = 64LL * 127, A2 = 128LL * 127 * 127;
   const long long p1 = 1LL << m->sh1, p2 = 1LL << m->sh2;
   for (uint32_t j = 0; j < 128; ++j) {
     const long long b = std::min(std::max<long long>(m->b1[j], -(A1 + 1)), 128 * p1 + A1);
-    uint16_t pc[3];
-    if (!split3(static_cast<float>(static_cast<double>(b + 128 * p1) * s1), pc)) return false;
-    for (uint32_t k = 0; k < 3; ++k) put16(img, kB1b + swz_host(j, k), pc[k]);
+    const double c = static_cast<double>(b + 128 * p1) * s1;
+    out->c1[j] = static_cast<float>(c);
+    if (static_cast<double>(out->c1[j]) != c) return false;
   }
   for (uint32_t j = 0; j < 64; ++j) {
     long long col = 0;
     for (int i = 0; i < 128; ++i) col += m->w2[i * 64 + j];
     const long long b = std::min(std::max<long long>(m->b2[j], -(A2 + 1)), 128 * p2 + A2);
-    uint16_t pc[3];
-    if (!split3(static_cast<float>(static_cast<double>(b - 128 * col + 128 * p2) * s2), pc)) return false;
-    for (uint32_t k = 0; k < 3; ++k) put16(img, kB2b + swz_host(j, k), pc[k]);
+    const double c = static_cast<double>(b - 128 * col + 128 * p2) * s2;
+    out->c2[j] = static_cast<float>(c);
+    if (static_cast<double>(out->c2[j]) != c) return false;
   }
   out->s3 = static_cast<long long>(m->b3) - 128 * sum3;
   for (int i = 0; i < 64; ++i) out->w3[i] = static_cast<float>(m->w3[i]);
@@ -523,6 +574,8 @@ cudaError_t tc_run(const uint8_t* d_image, const TcModel& tm, const uint64_t* d_
   a.out_keys = out_keys;
   a.err = err;
   a.s3 = tm.s3;
+  std::memcpy(a.c1, tm.c1, sizeof(a.c1));
+  std::memcpy(a.c2, tm.c2, sizeof(a.c2));
   std::memcpy(a.w3, tm.w3, sizeof(a.w3));
   a.bk_words = backup ? backup->words : nullptr;
   a.bk_blocks = backup ? backup->num_blocks : 0;
