@@ -162,15 +162,17 @@ __device__ __forceinline__ uint64_t globaltimer() {
   return t;
 }
 
-// bounded wait on an mbarrier phase (2 s): false when it did not complete
+// bounded wait on an mbarrier phase: false when it did not complete within
+// limit_ns.  Each try_wait may sleep in hardware (suspend-time hint 20 us)
+// until the phase completes, so a waiting thread takes almost no issue slots.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, uint64_t limit_ns) {
   const uint64_t t0 = globaltimer();
   while (true) {
     uint32_t done;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(bar), "r"(phase)
+        : "r"(bar), "r"(phase), "r"(20000u)
         : "memory");
     if (done) return true;
     if (globaltimer() - t0 > limit_ns) return false;
