@@ -217,15 +217,15 @@ def run_reference(args, w, wname):
 KERNEL_SOURCES = ("sbf_kernels.cuh", "sbf_device.cuh", "salts.cuh", "sbf_partition.cuh", "sbf_expand.cu")
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2512_15595_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic(op: str, wname: str):
+def measured_traffic(op: str, wname: str, sources=KERNEL_SOURCES):
     """DRAM bytes of one call of `op` from the committed ncu summary, if the
     kernel sources have not changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -234,7 +234,7 @@ def measured_traffic(op: str, wname: str):
     with open(path) as f:
         t = json.load(f)
     e = t.get(f"{op}/{wname}")
-    if not e or e.get("kernel_source_hash") != kernel_source_hash():
+    if not e or e.get("kernel_source_hash") != kernel_source_hash(sources):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -790,7 +790,7 @@ def run_learned(args):
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
     t_gen = time.perf_counter()
-    d = learned_data()
+    d = learned_data(n_members=args.learned_members, n_query_non=args.learned_members)
     t_gen = time.perf_counter() - t_gen
     n_mem = d["members"].size
     to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(device)
@@ -908,10 +908,23 @@ def run_learned(args):
     tf = flops_key * nq / (score_ms * 1e-3) / 1e12
     engine = "tensor (tcgen05 kind::f16, bf16 operands, fp32 accumulate; exact)" \
         if model.engine == LB.BF_MLP_ENGINE_TENSOR else "dp4a (CUDA cores)"
+    traffic = measured_traffic("scores", "learned", ("lbf_tc.cu", "lbf.h")) if nq == 1 << 27 else None
     roof = {"bound": "tensor", "achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-            "frac": tf / pk["bf16_tflops"], "traffic": None, "kernel": f"bf_mlp_scores: {engine}",
+            "frac": tf / pk["bf16_tflops"], "traffic": traffic, "kernel": f"bf_mlp_scores: {engine}",
             "per": "one call", "peak_source": "measured bf16 dense burst (MEASURED_PEAKS.json)",
             "algorithmic_flops_per_key": flops_key, "keys_per_call": nq, "ms_per_call": score_ms}
+    # the tensor-instruction bound: one tile of 128 keys is 4 MMAs (N = 128, A
+    # in shared memory) + 8 MMAs (N = 64, A in tensor memory); their measured
+    # per-instruction cost at the sampled SM clock
+    from paper_2512_15595_gb300 import _lib as LL
+    c128, c64 = LL.bf_mma_cost(128, False), LL.bf_mma_cost(64, True)
+    tile_cycles = 4 * c128 + 8 * c64
+    f_hz = (clocks or {}).get("sm_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    bound = 128 * sms * f_hz * 1e6 / tile_cycles / 1e9
+    tib = {"cycles_per_mma_n128_smem": c128, "cycles_per_mma_n64_tmem": c64, "cycles_per_tile": tile_cycles,
+           "sm_mhz": f_hz, "gkeys_s": bound, "model_frac": (nq / (score_ms * 1e-3) / 1e9) / bound,
+           "how": "bf_mma_cost: back-to-back tcgen05.mma kind::f16, M=128, K=16, one issuing thread per SM"}
     e2e = None
     if not args.no_e2e:
         e2e = learned_e2e(torch, lf, queries, args)
@@ -926,7 +939,8 @@ def run_learned(args):
         "plain_lookup_gkeys_s": nq / (plain_ms * 1e-3) / 1e9, "model_scores_gkeys_s": nq / (score_ms * 1e-3) / 1e9,
         "training": {"steps": steps, "batch": batch, "ms": train_ms, "ms_per_step": train_ms / steps,
                      "first_loss": float(losses[:10].mean().item()), "last_loss": float(losses[-50:].mean().item())},
-        "engine": engine, "fpr": fpr, "roofline": roof, "e2e": e2e, "clocks": clocks,
+        "engine": engine, "fpr": fpr, "roofline": roof, "tensor_instruction_bound": tib, "e2e": e2e,
+        "clocks": clocks,
         "gpu_launches": launches_per_lookup * args.steps,
     }
     print(json.dumps(line), flush=True)
@@ -1007,6 +1021,8 @@ def main():
     ap.add_argument("--workload", default="4GiB", choices=sorted(WORKLOADS) + ["batched", "serving", "learned"])
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--learned-bits", default="2,4,6,8", help="other bits/key budgets for the FPR comparison")
+    ap.add_argument("--learned-members", type=int, default=1 << 26,
+                    help="member keys of the learned workload (queries: as many non-members again)")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--frontier", action="store_true")

@@ -456,6 +456,17 @@ bf_status bf_mlp_contains(const bf_mlp_model* m, int32_t tau, const bf_filter* b
 bf_status bf_mlp_contains_host(bf_mlp_model* m, int32_t tau, const bf_filter* backup, const uint64_t* h_keys,
                                uint64_t n, uint8_t* h_out, bf_stream_t stream);
 
+/* Measured cost of back-to-back 5th-generation tensor-core MMAs (tcgen05.mma
+   kind::f16, M = 128, K = 16, bf16 operands, fp32 accumulation) with n
+   columns (16, 32, 64, 128 or 256), A from shared memory (a_tmem = 0) or
+   tensor memory (1): one issuing thread per SM on every SM issues `reps`
+   instructions (1 <= reps <= 2^24); *cycles = SM clock cycles per
+   instruction.  The learned prefilter's tile is a fixed set of such
+   instructions, so this bounds its throughput (as bf_gups bounds the
+   filters').  Synchronizes the device; BF_ETIMEDOUT if the instructions did
+   not complete within 2 s. */
+bf_status bf_mma_cost(uint32_t n, int a_tmem, uint32_t reps, double* cycles);
+
 const char* bf_status_str(bf_status s);
 
 /* Message of the last error on the calling host thread ("" if none). */

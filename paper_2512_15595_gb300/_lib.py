@@ -30,7 +30,7 @@ EXPORTED = (
     "bf_batch_info", "bf_server_create", "bf_server_destroy", "bf_server_submit", "bf_server_wait",
     "bf_server_get_stats", "bf_server_run_poisson", "bf_mlp_workspace_bytes", "bf_mlp_grad", "bf_mlp_adam",
     "bf_mlp_train", "bf_mlp_export", "bf_mlp_load", "bf_mlp_free", "bf_mlp_scores", "bf_mlp_select_below",
-    "bf_mlp_contains", "bf_mlp_contains_host", "bf_mlp_set_engine", "bf_mlp_get_engine", "bf_mlp_check", "bf_status_str", "bf_last_error", "bf_version",
+    "bf_mlp_contains", "bf_mlp_contains_host", "bf_mlp_set_engine", "bf_mlp_get_engine", "bf_mlp_check", "bf_mma_cost", "bf_status_str", "bf_last_error", "bf_version",
 )
 
 BF_MLP_PARAMS = 16641
@@ -158,6 +158,7 @@ def lib():
         "bf_mlp_set_engine": (i32, [vp, i32]),
         "bf_mlp_get_engine": (i32, [vp, ctypes.POINTER(i32)]),
         "bf_mlp_check": (i32, [vp]),
+        "bf_mma_cost": (i32, [u32, i32, u32, ctypes.POINTER(ctypes.c_double)]),
         "bf_status_str": (ctypes.c_char_p, [i32]),
         "bf_last_error": (ctypes.c_char_p, []),
         "bf_version": (ctypes.c_char_p, []),
@@ -433,3 +434,9 @@ def bf_mlp_check(m: int) -> None:
 
 def bf_mlp_contains_host(m: int, tau: int, backup: int, h_keys: int, n: int, h_out: int, stream=None) -> None:
     _check(lib().bf_mlp_contains_host(m, tau, backup, h_keys, n, h_out, _stream(stream)), "bf_mlp_contains_host")
+
+
+def bf_mma_cost(n: int, a_tmem: bool, reps: int = 4096) -> float:
+    c = ctypes.c_double()
+    _check(lib().bf_mma_cost(n, int(a_tmem), reps, ctypes.byref(c)), "bf_mma_cost")
+    return c.value

@@ -41,7 +41,8 @@ def _units():
              ("sbf_expand", os.path.join(CSRC, "sbf_expand.cu"), []),
              ("bf_server", os.path.join(CSRC, "bf_server.cu"), []),
              ("lbf_kernels", os.path.join(CSRC, "lbf_kernels.cu"), []),
-             ("lbf_tc", os.path.join(CSRC, "lbf_tc.cu"), [])]
+             ("lbf_tc", os.path.join(CSRC, "lbf_tc.cu"), []),
+             ("tc_cost", os.path.join(CSRC, "tc_cost.cu"), [])]
     for b, s in GEOMETRIES:
         units.append((f"sbf_B{b}_S{s}", os.path.join(CSRC, "sbf_geom.cu"), [f"-DSBF_B={b}", f"-DSBF_S={s}"]))
     return units

@@ -181,3 +181,13 @@ def test_mlp_arguments_rejected_without_gpu(L):
     assert lib.bf_mlp_contains(None, 0, None, 256, 4, 256, None) == L.BF_EINVAL
     assert lib.bf_mlp_select_below(None, 0, 256, 4, 256, 256, None) == L.BF_EINVAL
     assert lib.bf_mlp_export(None, None, 0, None, None) == L.BF_EINVAL
+
+
+def test_mma_cost_arguments_rejected_without_gpu(L):
+    import ctypes
+    lib = L.lib()
+    c = ctypes.c_double()
+    assert lib.bf_mma_cost(48, 0, 10, ctypes.byref(c)) == L.BF_EINVAL
+    assert lib.bf_mma_cost(64, 0, 0, ctypes.byref(c)) == L.BF_EINVAL
+    assert lib.bf_mma_cost(64, 0, 1 << 25, ctypes.byref(c)) == L.BF_EINVAL
+    assert lib.bf_mma_cost(64, 1, 10, None) == L.BF_EINVAL

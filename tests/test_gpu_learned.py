@@ -352,3 +352,15 @@ def test_learned_lookup_from_host_buffers(torch, data, small_learned):
     ob.add(fn_ref)
     want = (OL.int_scores(ref, keys) >= tau) | (ob.contains(keys) != 0)
     assert np.array_equal(out.numpy()[idx], want)
+
+
+def test_mma_cost_microbenchmark(torch):
+    """bf_mma_cost reports plausible per-instruction costs: no faster than the
+    tensor cores' nominal rate (8192 bf16 flops per SM per cycle) and growing
+    with N from N = 128 on."""
+    from paper_2512_15595_gb300 import _lib
+    costs = {(n, ta): _lib.bf_mma_cost(n, ta, 2048) for n in (64, 128, 256) for ta in (False, True)}
+    for (n, ta), c in costs.items():
+        assert c >= 0.9 * 128 * n * 16 * 2 / 8192, (n, ta, c)
+        assert c < 2000
+    assert costs[(256, False)] > costs[(128, False)] >= costs[(64, False)] * 0.9
