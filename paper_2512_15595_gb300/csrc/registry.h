@@ -41,9 +41,8 @@ constexpr uint64_t kRecTile = 128;  // slice buffer capacity granule: the larges
 // lookup flavour also keeps each record's query index)
 constexpr size_t partition_smem_bytes(int nparts, bool lookup = false) {
   return static_cast<size_t>(kPartTile) * 8        // records of the tile, sorted by slice
-         + static_cast<size_t>(kPartTile) * 2      // slice of each sorted record
          + static_cast<size_t>(nparts) * 4 * 2     // per-slice count and start in the tile
-         + static_cast<size_t>(nparts) * 8         // per-slice reserved global position
+         + static_cast<size_t>(nparts) * 8         // per-slice global offset
          + 64 * 4                                  // scan scratch (one entry per warp)
          + (lookup ? static_cast<size_t>(kPartTile) * 4 : 0);  // query index of each sorted record
 }

@@ -64,11 +64,12 @@ template <int B, int S, int K, bool LOOKUP>
 __global__ void __launch_bounds__(kPartThreads, 3) sbf_partition_kernel(const PartArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* tile_rec = reinterpret_cast<uint64_t*>(smem);
-  uint16_t* tile_part = reinterpret_cast<uint16_t*>(tile_rec + kPartTile);
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(tile_part + kPartTile);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(tile_rec + kPartTile);
   uint32_t* start = cnt + a.nparts;
-  unsigned long long* gpos = reinterpret_cast<unsigned long long*>(start + a.nparts);
-  uint32_t* warp_sum = reinterpret_cast<uint32_t*>(gpos + a.nparts);
+  // per slice: reserved global position minus the slice's first position in
+  // the tile (modulo 2^64), so that sorted position i goes to off[p] + i
+  unsigned long long* off = reinterpret_cast<unsigned long long*>(start + a.nparts);
+  uint32_t* warp_sum = reinterpret_cast<uint32_t*>(off + a.nparts);
   uint32_t* tile_idx = warp_sum + 64;  // lookup only (kPartTile entries)
 
   using W = typename WordOf<S>::type;
@@ -138,25 +139,26 @@ __global__ void __launch_bounds__(kPartThreads, 3) sbf_partition_kernel(const Pa
 
     // reserve space in each slice's buffer, and scatter into shared memory
     for (uint32_t p = tid; p < a.nparts; p += kPartThreads)
-      gpos[p] = cnt[p] ? atomicAdd(a.counts + p, static_cast<unsigned long long>(cnt[p])) : 0ull;
+      off[p] = (cnt[p] ? atomicAdd(a.counts + p, static_cast<unsigned long long>(cnt[p])) : 0ull) -
+               static_cast<unsigned long long>(start[p]);
 #pragma unroll
     for (int u = 0; u < kPartKeysPerThread; ++u) {
       if (pr[u] != 0xFFFFFFFFu) {
         const uint32_t part = pr[u] >> 12;
         const uint32_t pos = start[part] + (pr[u] & 0xFFFu);
         tile_rec[pos] = rec[u];
-        tile_part[pos] = static_cast<uint16_t>(part);
         if constexpr (LOOKUP) tile_idx[pos] = static_cast<uint32_t>(base) + u * kPartThreads + tid;
       }
     }
     __syncthreads();
 
     // coalesced write-out: consecutive positions of one slice go to
-    // consecutive addresses of that slice's buffer
+    // consecutive addresses of that slice's buffer (the slice is read back
+    // from the record's block index)
     for (uint32_t i = tid; i < tile_n; i += kPartThreads) {
-      const uint32_t p = tile_part[i];
-      const uint64_t dst = gpos[p] + (i - start[p]);
       const uint64_t r = tile_rec[i];
+      const uint32_t p = static_cast<uint32_t>((r >> 32) >> a.shift);
+      const uint64_t dst = off[p] + i;
       if constexpr (LOOKUP) {
         const uint32_t q = tile_idx[i];
         if (dst < a.cap) {
