@@ -76,6 +76,12 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def whole_job_rate(world: int, keys_per_step: int, steps: int, total_ms: float) -> float:
+    """G keys/s of the whole job: every rank processes keys_per_step per step;
+    total_ms is the slowest rank's time for all timed steps."""
+    return world * keys_per_step * steps / (total_ms * 1e-3) / 1e9
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -374,7 +380,7 @@ def run_ours(args, w, wname):
     add_ms = statistics.median(e[0].elapsed_time(e[1]) for e in evs)
     con_ms = statistics.median(e[1].elapsed_time(e[2]) for e in evs)
     keys_per_step = n_ins + n_q
-    value = world * keys_per_step * args.steps / (total_ms * 1e-3) / 1e9
+    value = whole_job_rate(world, keys_per_step, args.steps, total_ms)
     ins_g = n_ins / (add_ms * 1e-3) / 1e9
     look_g = n_q / (con_ms * 1e-3) / 1e9
 
