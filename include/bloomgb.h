@@ -248,8 +248,8 @@ bf_status bf_gups(int mode, void* d_table, uint64_t table_bytes, uint32_t unit_b
                   const uint64_t* d_keys, uint64_t n, uint8_t* d_out, const bf_layout* layout,
                   bf_stream_t stream);
 
-/* Batched filters (SURVEY-level extension of the paper's bulk operations to
-   many independent filters): one launch builds, or probes, every filter of
+/* Batched filters (an extension of the paper's bulk operations to many
+   independent filters): one launch builds, or probes, every filter of
    a batch.  All filters share params->block_bits / word_bits / k / seed
    (params->num_blocks is ignored); each has its own bit array and its own
    run [key_offset, key_offset + key_count) of one key array, and lookup
