@@ -384,7 +384,7 @@ def run_ours(args, w, wname):
     ins_g = n_ins / (add_ms * 1e-3) / 1e9
     look_g = n_q / (con_ms * 1e-3) / 1e9
 
-    # accuracy of this build: FPR of the fresh queries at 10 bits/key
+    # accuracy of the constructed filter: FPR of the fresh queries at 10 bits/key
     fresh = flags == 0
     n_fresh = int(fresh.sum().item())
     measured_fpr = float(out[fresh].float().sum().item()) / max(1, n_fresh)

@@ -61,7 +61,7 @@ typedef enum {
     BF_EINVAL = 1,         /* bad argument: null pointer, misalignment, bad geometry */
     BF_ENOMEM = 2,         /* device or pinned-host allocation failed */
     BF_ECUDA = 3,          /* a CUDA call failed; see bf_last_error() */
-    BF_EUNSUPPORTED = 4,   /* valid by the definition, but not compiled into this build */
+    BF_EUNSUPPORTED = 4,   /* valid by the definition, but not compiled into this library */
     BF_ETIMEDOUT = 5       /* a wait ran out of time (bf_server_wait) */
 } bf_status;
 
