@@ -52,7 +52,8 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("num_blocks", ctypes.c_uint64), ("block_bits", ctypes.c_uint32),
                 ("word_bits", ctypes.c_uint32), ("k", ctypes.c_uint32),
-                ("groups", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+                ("groups", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("salts", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 def lib():
@@ -66,6 +67,7 @@ def lib():
             "orc_key_hash": (u64, [u64, u64]),
             "orc_salt64": (u64, [u32]),
             "orc_salt32": (u32, [u32]),
+            "orc_parquet_salt32": (u32, [u32]),
             "orc_block_index": (u64, [u64, u64]),
             "orc_bit_position": (u32, [u64, u32, u32]),
             "orc_check": (i32, [P]),
@@ -120,6 +122,11 @@ def block_indices(keys, num_blocks: int, seed: int = 0) -> np.ndarray:
     return out
 
 
+def parquet_salts() -> list[int]:
+    """Salt set 1: the Parquet split-block filter's eight multipliers."""
+    return [lib().orc_parquet_salt32(i) for i in range(8)]
+
+
 def salts(word_bits: int, count: int = 64) -> list[int]:
     L = lib()
     return [L.orc_salt32(i) if word_bits == 32 else L.orc_salt64(i) for i in range(count)]
@@ -146,6 +153,7 @@ class Geometry:
     k: int = 8
     seed: int = 0
     groups: int = 0
+    salts: int = 0  # 0: SplitMix64 salts; 1: the Parquet split-block salts (256/32/8 only)
 
     @property
     def s(self) -> int:
@@ -173,7 +181,7 @@ class Geometry:
         return np.uint32 if self.word_bits == 32 else np.uint64
 
     def cparams(self) -> _Params:
-        return _Params(self.num_blocks, self.block_bits, self.word_bits, self.k, self.groups, self.seed)
+        return _Params(self.num_blocks, self.block_bits, self.word_bits, self.k, self.groups, self.seed, self.salts, 0)
 
     def valid(self) -> bool:
         p = self.cparams()

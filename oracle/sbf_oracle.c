@@ -42,6 +42,12 @@
  *     this is the sectorized rule, and the two forms coincide);
  *   - k must be a multiple of z and k + z <= 64 (the pattern and selection
  *     multipliers then never share a table entry).
+ *
+ * Salt set 1 (salts = 1, only B = 256, S = 32, k = 8, sectorized): the
+ * multipliers are those of the Apache Parquet split-block Bloom filter, so
+ * the bit array is the one a Parquet writer stores for the same keys and
+ * block count (the paper's compatibility claim, Sec. VI); everything else
+ * above is unchanged.
  */
 #include <stddef.h>
 #include <stdint.h>
@@ -187,6 +193,22 @@ uint32_t orc_salt32(uint32_t i)
     return (uint32_t)(orc_salt64(i) >> 32) | 1u;
 }
 
+/* Salt set 1: the eight odd multipliers of the Apache Parquet split-block
+   filter (256-bit blocks of eight 32-bit words, one bit per word), which the
+   paper's filter with B = 256, S = 32, k = 8 reproduces bit for bit (Sec. VI).
+   The values are not in the paper; they were recovered from the bit arrays
+   pyarrow's Parquet writer produces (tests/test_oracle_hash_pins.py recovers
+   them again on every run and compares). */
+static const uint32_t parquet_salt32[8] = {
+    0x47B6137Bu, 0x44974D91u, 0x8824AD5Bu, 0xA2B7289Du,
+    0x705495C7u, 0x2DF1424Bu, 0x9EFC4947u, 0x5C6BFB31u,
+};
+
+uint32_t orc_parquet_salt32(uint32_t i)
+{
+    return i < 8 ? parquet_salt32[i] : 0u;
+}
+
 /* ---------------------------------------------------------------------- */
 /* block selection and bit positions                                        */
 /* ---------------------------------------------------------------------- */
@@ -216,7 +238,19 @@ typedef struct {
     uint32_t k;
     uint32_t groups;    /* z: 0 (or s) = sectorized; 0 < z < s = cache-sectorized */
     uint64_t seed;
+    uint32_t salts;     /* 0: SplitMix64 salts; 1: the Parquet split-block salts */
+    uint32_t reserved;
 } orc_params;
+
+/* bit position of salt index i under the geometry's salt set */
+static uint32_t bit_position_p(const orc_params* p, uint64_t h, uint32_t salt_index)
+{
+    if (p->salts == 1) {
+        uint64_t h_lo = h & 0xFFFFFFFFULL;
+        return (uint32_t)(h_lo * (uint64_t)orc_parquet_salt32(salt_index)) >> 27;
+    }
+    return orc_bit_position(h, salt_index, p->word_bits);
+}
 
 static uint32_t effective_groups(const orc_params* p)
 {
@@ -238,6 +272,8 @@ int orc_check(const orc_params* p)
     if (p->k < z || p->k % z != 0) return -1;
     if (p->k > ORC_MAX_SALTS) return -1;
     if (z < s && p->k + z > ORC_MAX_SALTS) return -1;
+    if (p->salts > 1) return -1;
+    if (p->salts == 1 && !(p->block_bits == 256 && p->word_bits == 32 && p->k == 8 && z == s)) return -1;
     return 0;
 }
 
@@ -267,7 +303,7 @@ uint64_t orc_group_pattern(const orc_params* p, uint64_t h, uint32_t q)
     uint32_t z = effective_groups(p);
     uint32_t kz = p->k / z;
     uint64_t pattern = 0;
-    for (uint32_t t = 0; t < kz; ++t) pattern |= 1ULL << orc_bit_position(h, q + z * t, p->word_bits);
+    for (uint32_t t = 0; t < kz; ++t) pattern |= 1ULL << bit_position_p(p, h, q + z * t);
     return pattern;
 }
 
@@ -290,7 +326,7 @@ uint64_t orc_word_pattern(const orc_params* p, uint64_t h, uint32_t w)
     uint32_t kp = p->k / s;
     uint64_t pattern = 0;
     for (uint32_t t = 0; t < kp; ++t) {
-        uint32_t bit = orc_bit_position(h, w + s * t, p->word_bits);
+        uint32_t bit = bit_position_p(p, h, w + s * t);
         pattern |= 1ULL << bit;
     }
     return pattern;

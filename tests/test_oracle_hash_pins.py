@@ -126,3 +126,36 @@ def test_xxh64_high_half_and_block_rule_consistent_with_parquet(recovered_multip
     # negative control: the neighbouring block holds the pattern only rarely
     hits = sum(_predicted_block_ok(words, nb, h, mult, shift_block=1) for h in hs)
     assert hits < 0.2 * len(hs)
+
+
+def test_oracle_parquet_salt_set_is_the_recovered_one(recovered_multipliers):
+    # the oracle's salt set 1 equals what pyarrow's writer output determines
+    assert oracle.parquet_salts() == [m[0] for m in recovered_multipliers]
+
+
+@pytest.mark.parametrize("n", [1, 37, 3000, 20_000])
+def test_oracle_parquet_mode_reproduces_pyarrow_bitsets(n):
+    """With salt set 1 the oracle's whole bit array is the one pyarrow stores
+    (same keys, same number of blocks): the filter is Parquet-compatible."""
+    keys = np.arange(n, dtype=np.int64) * 2654435761 - 987654321
+    words = parquet_bitset(keys)
+    nb = words.size // 8
+    geom = oracle.Geometry(num_blocks=nb, block_bits=256, word_bits=32, k=8, seed=0, salts=1)
+    assert geom.valid()
+    f = oracle.SBF(geom)
+    f.add(keys.view(np.uint64))
+    assert np.array_equal(f.words, words)
+    # the default salt set does not reproduce it (negative control)
+    g = oracle.SBF(oracle.Geometry(num_blocks=nb, block_bits=256, word_bits=32, k=8, seed=0))
+    g.add(keys.view(np.uint64))
+    assert not np.array_equal(g.words, words)
+
+
+def test_parquet_salt_set_geometry_rules():
+    ok = oracle.Geometry(num_blocks=10, block_bits=256, word_bits=32, k=8, salts=1)
+    assert ok.valid()
+    for kw in ({"k": 16}, {"block_bits": 512}, {"word_bits": 64, "block_bits": 512}, {"groups": 2}):
+        args = dict(num_blocks=10, block_bits=256, word_bits=32, k=8, salts=1)
+        args.update(kw)
+        assert not oracle.Geometry(**args).valid(), kw
+    assert not oracle.Geometry(num_blocks=10, salts=2).valid()
