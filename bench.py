@@ -159,7 +159,8 @@ def cpu_oracle_rate(w, budget_s: float):
     import oracle
     import synthkeys
     b, n_ins, n_q = wl_sizes(w)
-    geom = oracle.Geometry(num_blocks=b, block_bits=w["block_bits"], word_bits=w["word_bits"], k=w["k"], seed=0)
+    geom = oracle.Geometry(num_blocks=b, block_bits=w["block_bits"], word_bits=w["word_bits"], k=w["k"], seed=0,
+                           salts=w.get("salts", 0))
     f = oracle.SBF(geom)
     chunk = 1 << 20
     done_i, t_i = 0, 0.0
@@ -334,7 +335,7 @@ def run_ours(args, w, wname):
     regime = autotune.regime_of(w["nbytes"], props.L2_cache_size)
 
     ins, qd, flags = gen_inputs(torch, w, device)
-    f = Filter(b, w["block_bits"], w["word_bits"], w["k"], 0, device=device)
+    f = Filter(b, w["block_bits"], w["word_bits"], w["k"], 0, device=device, salts=w.get("salts", 0))
     layouts = autotune.apply_tuned(f, regime)
     out = torch.empty(n_q, dtype=torch.uint8, device=device)
     stream = torch.cuda.current_stream()
@@ -444,6 +445,7 @@ def run_ours(args, w, wname):
             "data": "synthetic (SplitMix64 key streams generated on the device)",
             "config": {"workload": wname, "desc": w["desc"], "num_blocks": b, "block_bits": w["block_bits"],
                        "word_bits": w["word_bits"], "k": w["k"], "n_insert": n_ins, "n_lookup": n_q,
+                       "salts": "parquet split-block" if w.get("salts") else "splitmix64",
                        "regime": regime, "layouts": layouts, "partition": f.partition(),
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (no flush)" if n_ins * 8 > props.L2_cache_size
@@ -1027,6 +1029,8 @@ def main():
     ap.add_argument("--workload", default="4GiB", choices=sorted(WORKLOADS) + ["batched", "serving", "learned"])
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--learned-bits", default="2,4,6,8", help="other bits/key budgets for the FPR comparison")
+    ap.add_argument("--salts", default="default", choices=["default", "parquet"],
+                    help="salt set of the filter (parquet: the Parquet split-block multipliers; 256/32/8 only)")
     ap.add_argument("--learned-members", type=int, default=1 << 26,
                     help="member keys of the learned workload (queries: as many non-members again)")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
@@ -1061,7 +1065,12 @@ def main():
         else:
             run_batched(args)
         return
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.salts == "parquet":
+        if (w["block_bits"], w["word_bits"], w["k"]) != (256, 32, 8):
+            ap.error("the Parquet salt set exists for 256-bit blocks, S = 32, K = 8 only")
+        w["salts"] = 1
+        w["desc"] = w["desc"] + "; Parquet split-block salt set (bit-compatible with Parquet/Arrow filters)"
     if args.impl == "reference":
         run_reference(args, w, args.workload)
     elif args.sweep:

@@ -77,7 +77,13 @@ typedef enum {
    read or updated.
    Builds compile k in {4,8,16} and, for the CSBF, z in {1,2,4,8}; other
    admissible values return BF_EUNSUPPORTED.  The slice-partitioned paths,
-   batches and bf_add_noalloc serve sectorized filters only. */
+   batches and bf_add_noalloc serve sectorized filters only.
+   salts: the odd multipliers of the bit positions (Sec. IV-B).  0 (default):
+   the library's SplitMix64 tables.  1: the Apache Parquet split-block Bloom
+   filter's eight multipliers, for block_bits = 256, word_bits = 32, k = 8,
+   sectorized only (else BF_EINVAL); with seed 0 the bit array is then the one
+   a Parquet writer stores for the same keys and block count (Sec. VI), so
+   such filters can be read from or written into Parquet files as they are. */
 typedef struct {
     uint64_t num_blocks;
     uint32_t block_bits;
@@ -85,6 +91,8 @@ typedef struct {
     uint32_t k;
     uint32_t groups;        /* z; 0 = sectorized */
     uint64_t seed;
+    uint32_t salts;         /* salt set: 0 default, 1 Parquet split-block */
+    uint32_t reserved;      /* 0 */
 } bf_params;
 
 typedef enum { BF_OP_ADD = 0, BF_OP_CONTAINS = 1 } bf_op;

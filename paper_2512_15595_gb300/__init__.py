@@ -57,9 +57,11 @@ class Filter:
     """A filter whose bit array is a torch tensor (adopted by the library)."""
 
     def __init__(self, num_blocks: int, block_bits: int = 256, word_bits: int = 32, k: int = 8,
-                 seed: int = 0, device=None, words=None, groups: int = 0):
+                 seed: int = 0, device=None, words=None, groups: int = 0, salts: int = 0):
+        """salts = 1: the Parquet split-block salt set (256/32/8 only; with seed
+        0 the bit array is the one a Parquet writer stores)."""
         import torch
-        self.params = bf_params(num_blocks, block_bits, word_bits, k, groups, seed)
+        self.params = bf_params(num_blocks, block_bits, word_bits, k, groups, seed, salts, 0)
         self.nbytes = num_blocks * block_bits // 8
         if words is None:
             device = torch.device(device or "cuda")
@@ -146,8 +148,9 @@ class Batch:
     indexed by each filter's key run.
     """
 
-    def __init__(self, filters, block_bits: int = 256, word_bits: int = 32, k: int = 8, seed: int = 0):
-        self.params = bf_params(1, block_bits, word_bits, k, 0, seed)
+    def __init__(self, filters, block_bits: int = 256, word_bits: int = 32, k: int = 8, seed: int = 0,
+                 salts: int = 0):
+        self.params = bf_params(1, block_bits, word_bits, k, 0, seed, salts, 0)
         self._keep = [f[0] for f in filters]
         descs = [(f[0].data_ptr(), f[1], f[2], f[3]) for f in filters]
         self.handle = _lib.bf_batch_create(self.params, descs)

@@ -46,10 +46,14 @@ class BloomError(RuntimeError):
 _STATUS = {0: "BF_OK", 1: "BF_EINVAL", 2: "BF_ENOMEM", 3: "BF_ECUDA", 4: "BF_EUNSUPPORTED", 5: "BF_ETIMEDOUT"}
 
 
+BF_SALTS_DEFAULT, BF_SALTS_PARQUET = 0, 1
+
+
 class bf_params(ctypes.Structure):
     _fields_ = [("num_blocks", ctypes.c_uint64), ("block_bits", ctypes.c_uint32),
                 ("word_bits", ctypes.c_uint32), ("k", ctypes.c_uint32),
-                ("groups", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+                ("groups", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("salts", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 BF_PART_OFF, BF_PART_ON, BF_PART_AUTO = 0, 1, 2

@@ -59,7 +59,8 @@ const KernelEntry* find_sbf(int op, const bf_params& p, const bf_layout& l) {
   for (const auto& e : registry().sbf) {
     if (e.op == op && e.B == static_cast<int>(p.block_bits) && e.S == static_cast<int>(p.word_bits) &&
         e.K == static_cast<int>(p.k) && e.theta == static_cast<int>(l.cg) &&
-        e.phi == static_cast<int>(l.phi) && e.kpt == static_cast<int>(l.kpt))
+        e.phi == static_cast<int>(l.phi) && e.kpt == static_cast<int>(l.kpt) && e.z == 0 &&
+        e.salts == static_cast<int>(p.salts))
       return &e;
   }
   return nullptr;
@@ -135,10 +136,11 @@ bf_status resolve_grid(const void* fn, int device, uint32_t threads, uint32_t gr
 }  // namespace
 
 namespace bloomgb {
-const KernelEntry* find_kernel(int op, int block_bits, int word_bits, int k, int theta, int phi, int kpt, int z) {
+const KernelEntry* find_kernel(int op, int block_bits, int word_bits, int k, int theta, int phi, int kpt, int z,
+                               int salts) {
   for (const auto& e : registry().sbf)
     if (e.op == op && e.B == block_bits && e.S == word_bits && e.K == k && e.theta == theta && e.phi == phi &&
-        e.kpt == kpt && e.z == z)
+        e.kpt == kpt && e.z == z && e.salts == salts)
       return &e;
   return nullptr;
 }
@@ -223,6 +225,9 @@ bf_status check_params(const bf_params* p) {
       return fail(BF_EINVAL, "cache-sectorized: k must be a multiple of groups and k + groups <= 64");
   }
   if (p->num_blocks > (~0ull) / 128) return fail(BF_EINVAL, "num_blocks too large");
+  if (p->salts > 1) return fail(BF_EINVAL, "salts must be 0 (default) or 1 (Parquet split-block)");
+  if (p->salts == 1 && !(p->block_bits == 256 && p->word_bits == 32 && p->k == 8 && z == 0))
+    return fail(BF_EINVAL, "the Parquet salt set needs block_bits 256, word_bits 32, k 8, a sectorized filter");
   return BF_OK;
 }
 
@@ -943,12 +948,15 @@ extern "C" bf_status bf_add_noalloc(const bf_params* params, void* d_words, cons
     return BF_EINVAL;
   const uint32_t s = params->block_bits / params->word_bits;
   if (params->k < s || params->k % s != 0 || params->k > 64) return BF_EINVAL;
+  if (params->salts > 1 ||
+      (params->salts == 1 && !(params->block_bits == 256 && params->word_bits == 32 && params->k == 8)))
+    return BF_EINVAL;
   if (reinterpret_cast<uintptr_t>(d_words) % std::max<uint32_t>(32, params->block_bits / 8) != 0) return BF_EINVAL;
   const KernelEntry* pe = nullptr;
   const KernelEntry* re = nullptr;
   for (const auto& e : registry().sbf) {
     if (e.B != static_cast<int>(params->block_bits) || e.S != static_cast<int>(params->word_bits) ||
-        e.K != static_cast<int>(params->k))
+        e.K != static_cast<int>(params->k) || e.z != 0 || e.salts != static_cast<int>(params->salts))
       continue;
     if (e.op == 3) pe = &e;
     if (e.op == 2 && e.theta == static_cast<int>(s) && e.phi == 1 && e.kpt == 1) re = &e;

@@ -301,7 +301,7 @@ bf_status bf_server_create(const bf_params* params, const bf_batch_filter* filte
     if (!filters[i].d_words || reinterpret_cast<uintptr_t>(filters[i].d_words) % align || filters[i].num_blocks == 0)
       return BF_EINVAL;
   // lookup layout: one thread per key, the whole block in one step, 4 keys per thread
-  const KernelEntry* k = find_kernel(8, p.block_bits, p.word_bits, p.k, 1, s_words, 4, 0);
+  const KernelEntry* k = find_kernel(8, p.block_bits, p.word_bits, p.k, 1, s_words, 4, 0, static_cast<int>(p.salts));
   if (!k) return BF_EUNSUPPORTED;
   bf_server* s = new (std::nothrow) bf_server();
   if (!s) return BF_ENOMEM;

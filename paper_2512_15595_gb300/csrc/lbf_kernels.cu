@@ -624,7 +624,7 @@ bf_status bf_mlp_contains(const bf_mlp_model* m, int32_t tau, const bf_filter* b
   uint64_t nbytes = 0;
   if (engine == BF_MLP_ENGINE_TENSOR && bf_get_params(backup, &bp) == BF_OK &&
       bf_words(backup, &words, &nbytes) == BF_OK && bp.block_bits == 256 && bp.word_bits == 32 && bp.k == 8 &&
-      (bp.groups == 0 || bp.groups == 8) && reinterpret_cast<uintptr_t>(d_keys) % 8 == 0) {
+      (bp.groups == 0 || bp.groups == 8) && bp.salts == 0 && reinterpret_cast<uintptr_t>(d_keys) % 8 == 0) {
     // one fused launch: model and backup probe per key
     const lbf::TcBackup tb{static_cast<const uint32_t*>(words), bp.num_blocks, bp.seed};
     return lbf::tc_run(m->d_tc, m->tc, d_keys, n, 5, tau, nullptr, d_out, nullptr, nullptr, m->d_err,

@@ -129,7 +129,8 @@ struct KernelEntry {
   int op;
   int B, S, K, theta, phi, kpt;
   const void* fn;
-  int z = 0;  // groups of a cache-sectorized kernel; 0 = sectorized
+  int z = 0;      // groups of a cache-sectorized kernel; 0 = sectorized
+  int salts = 0;  // salt set (bf_params.salts)
 };
 
 struct GupsEntry {
@@ -139,7 +140,8 @@ struct GupsEntry {
 };
 
 // Lookup of a compiled kernel (implemented with the registry in bf_api.cu).
-const KernelEntry* find_kernel(int op, int block_bits, int word_bits, int k, int theta, int phi, int kpt, int z);
+const KernelEntry* find_kernel(int op, int block_bits, int word_bits, int k, int theta, int phi, int kpt, int z,
+                               int salts = 0);
 // Resident CTAs per SM of a kernel at a CTA size (cached).
 int kernel_resident_ctas(const void* fn, int threads, int device);
 

@@ -7,6 +7,7 @@
 #include <type_traits>
 #include <utility>
 
+#include "parquet_salts.cuh"
 #include "salts.cuh"
 
 namespace bloomgb {
@@ -67,21 +68,24 @@ __device__ __forceinline__ uint64_t pattern_bit(uint32_t hlo, uint64_t salt) {
   return (1ull << ((static_cast<uint64_t>(hlo) * salt) >> 58));
 }
 
-template <int S> __host__ __device__ constexpr typename WordOf<S>::type salt_at(int i);
-template <> __host__ __device__ constexpr uint32_t salt_at<32>(int i) { return salt32_at(i); }
-template <> __host__ __device__ constexpr uint64_t salt_at<64>(int i) { return salt64_at(i); }
+// salt i of salt set SET (0: the SplitMix64 tables; 1: the Parquet
+// split-block multipliers, 32-bit words only)
+template <int S, int SET = 0> __host__ __device__ constexpr typename WordOf<S>::type salt_at(int i);
+template <> __host__ __device__ constexpr uint32_t salt_at<32, 0>(int i) { return salt32_at(i); }
+template <> __host__ __device__ constexpr uint64_t salt_at<64, 0>(int i) { return salt64_at(i); }
+template <> __host__ __device__ constexpr uint32_t salt_at<32, 1>(int i) { return parquet_salt32_at(i); }
 
 // Compile-time binary decision tree (Sec. IV-B, "mapping thread indices to
 // salt indices"): returns salt_at(BASE + r * STRIDE) for a runtime r in
 // [0, N) with log2(N) selects, every leaf a literal.
-template <int S, int BASE, int STRIDE, int N>
+template <int S, int BASE, int STRIDE, int N, int SET = 0>
 __device__ __forceinline__ typename WordOf<S>::type salt_select(uint32_t r) {
   if constexpr (N == 1) {
-    return salt_at<S>(BASE);
+    return salt_at<S, SET>(BASE);
   } else {
     constexpr int H = N / 2;
-    const auto lo = salt_select<S, BASE, STRIDE, H>(r);
-    const auto hi = salt_select<S, BASE + H * STRIDE, STRIDE, N - H>(r - H);
+    const auto lo = salt_select<S, BASE, STRIDE, H, SET>(r);
+    const auto hi = salt_select<S, BASE + H * STRIDE, STRIDE, N - H, SET>(r - H);
     return r < static_cast<uint32_t>(H) ? lo : hi;
   }
 }

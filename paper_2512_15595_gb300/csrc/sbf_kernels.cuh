@@ -24,9 +24,11 @@ namespace bloomgb {
 
 enum : uint32_t { kHintFilterEvictLast = 1u << 0, kHintKeysEvictNormal = 1u << 1 };
 
-template <int B_, int S_, int K_, int THETA_, int PHI_, int KPT_>
+// SALTS_: the salt set (0: SplitMix64 tables; 1: the Parquet split-block
+// multipliers, valid for B = 256, S = 32, K = 8 only)
+template <int B_, int S_, int K_, int THETA_, int PHI_, int KPT_, int SALTS_ = 0>
 struct Cfg {
-  static constexpr int B = B_, S = S_, K = K_, THETA = THETA_, PHI = PHI_, KPT = KPT_;
+  static constexpr int B = B_, S = S_, K = K_, THETA = THETA_, PHI = PHI_, KPT = KPT_, SALTS = SALTS_;
   using word_t = typename WordOf<S>::type;
   static constexpr int s = B / S;            // words per block
   static constexpr int kp = K / s;           // pattern bits per word
@@ -37,6 +39,7 @@ struct Cfg {
   static_assert(THETA >= 1 && THETA <= 32 && (THETA & (THETA - 1)) == 0, "THETA");
   static_assert(PHI >= 1 && (PHI & (PHI - 1)) == 0 && chunk <= s, "PHI");
   static_assert(KPT == 1 || KPT == 2 || KPT == 4, "KPT");
+  static_assert(SALTS == 0 || (SALTS == 1 && B == 256 && S == 32 && K == 8), "salt set");
 };
 
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
@@ -58,7 +61,7 @@ struct LaneSalts {
       static_for<C::PHI>([&](auto p) {
         static_for<C::kp>([&](auto t) {
           constexpr int Q = decltype(q)::value, P = decltype(p)::value, T = decltype(t)::value;
-          v[Q][P][T] = salt_select<C::S, Q * C::chunk + P + C::s * T, C::PHI, C::THETA>(r);
+          v[Q][P][T] = salt_select<C::S, Q * C::chunk + P + C::s * T, C::PHI, C::THETA, C::SALTS>(r);
         });
       });
     });

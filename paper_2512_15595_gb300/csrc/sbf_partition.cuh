@@ -24,26 +24,26 @@ namespace bloomgb {
 
 // OR a record's pattern into its block with one thread (Theta = 1, Phi = s):
 // the overflow path of the partition kernel.
-template <int B, int S, int K>
+template <int B, int S, int K, int SALTS>
 __device__ __forceinline__ void insert_one(typename WordOf<S>::type* filter, uint64_t blk, uint32_t hlo,
                                            uint64_t pol) {
-  using C = Cfg<B, S, K, 1, B / S, 1>;
+  using C = Cfg<B, S, K, 1, B / S, 1, SALTS>;
   using W = typename C::word_t;
   W* bp = filter + blk * C::s;
   static_for<C::s>([&](auto w) {
     constexpr int Wd = decltype(w)::value;
     W pat = 0;
-    static_for<C::kp>([&](auto t) { pat |= pattern_bit(hlo, salt_at<S>(Wd + C::s * decltype(t)::value)); });
+    static_for<C::kp>([&](auto t) { pat |= pattern_bit(hlo, salt_at<S, SALTS>(Wd + C::s * decltype(t)::value)); });
     red_or(bp + Wd, pat, pol);
   });
 }
 
 // Look a record up with one thread (Theta = 1, Phi = s): the overflow path of
 // the lookup flavour of the partition kernel.
-template <int B, int S, int K>
+template <int B, int S, int K, int SALTS>
 __device__ __forceinline__ bool lookup_one(const typename WordOf<S>::type* filter, uint64_t blk, uint32_t hlo,
                                            uint64_t pol) {
-  using C = Cfg<B, S, K, 1, B / S, 1>;
+  using C = Cfg<B, S, K, 1, B / S, 1, SALTS>;
   using W = typename C::word_t;
   W data[C::s];
   ld_words<C::s>(filter + blk * C::s, pol, data);
@@ -51,7 +51,7 @@ __device__ __forceinline__ bool lookup_one(const typename WordOf<S>::type* filte
   static_for<C::s>([&](auto w) {
     constexpr int Wd = decltype(w)::value;
     W pat = 0;
-    static_for<C::kp>([&](auto t) { pat |= pattern_bit(hlo, salt_at<S>(Wd + C::s * decltype(t)::value)); });
+    static_for<C::kp>([&](auto t) { pat |= pattern_bit(hlo, salt_at<S, SALTS>(Wd + C::s * decltype(t)::value)); });
     miss |= pat & ~data[Wd];
   });
   return miss == 0;
@@ -60,7 +60,7 @@ __device__ __forceinline__ bool lookup_one(const typename WordOf<S>::type* filte
 // LOOKUP = false: construction records.  LOOKUP = true: lookup records, each
 // with the index of its query in `idx`; a query whose slice buffer is full is
 // answered on the spot (its result bit is set if it is found).
-template <int B, int S, int K, bool LOOKUP>
+template <int B, int S, int K, bool LOOKUP, int SALTS = 0>
 __global__ void __launch_bounds__(kPartThreads, 3) sbf_partition_kernel(const PartArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* tile_rec = reinterpret_cast<uint64_t*>(smem);
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kPartThreads, 3) sbf_partition_kernel(const Pa
         if (dst < a.cap) {
           a.records[static_cast<uint64_t>(p) * a.cap + dst] = r;
           a.idx[static_cast<uint64_t>(p) * a.cap + dst] = q;
-        } else if (lookup_one<B, S, K>(static_cast<const W*>(a.filter), r >> 32, static_cast<uint32_t>(r),
+        } else if (lookup_one<B, S, K, SALTS>(static_cast<const W*>(a.filter), r >> 32, static_cast<uint32_t>(r),
                                        pol_filter)) {
           atomicOr(a.bitmap + (q >> 5), 1u << (q & 31u));
         }
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kPartThreads, 3) sbf_partition_kernel(const Pa
         if (dst < a.cap) {
           a.records[static_cast<uint64_t>(p) * a.cap + dst] = r;
         } else {
-          insert_one<B, S, K>(static_cast<W*>(a.filter), r >> 32, static_cast<uint32_t>(r), pol_filter);
+          insert_one<B, S, K, SALTS>(static_cast<W*>(a.filter), r >> 32, static_cast<uint32_t>(r), pol_filter);
         }
       }
     }

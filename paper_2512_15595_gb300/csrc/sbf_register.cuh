@@ -22,7 +22,7 @@ __host__ void host_static_for(F&& f) {
 
 constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
 
-template <int B, int S, int K>
+template <int B, int S, int K, int SALTS = 0>
 void register_k(std::vector<KernelEntry>& v) {
   constexpr int s = B / S;
   host_static_for<ilog2(s) + 1>([&](auto lt) {
@@ -31,18 +31,20 @@ void register_k(std::vector<KernelEntry>& v) {
       constexpr int P = 1 << decltype(lp)::value;
       host_static_for<3>([&](auto lk) {
         constexpr int KPT = 1 << decltype(lk)::value;
-        using C = Cfg<B, S, K, T, P, KPT>;
-        v.push_back({0, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_add_kernel<C>)});
-        v.push_back({1, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_contains_kernel<C>)});
-        v.push_back({2, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_add_records_kernel<C>)});
-        v.push_back({4, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_probe_records_kernel<C>)});
-        v.push_back({7, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_batch_kernel<C, true>)});
-        v.push_back({8, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_batch_kernel<C, false>)});
+        using C = Cfg<B, S, K, T, P, KPT, SALTS>;
+        v.push_back({0, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_add_kernel<C>), 0, SALTS});
+        v.push_back({1, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_contains_kernel<C>), 0, SALTS});
+        v.push_back({2, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_add_records_kernel<C>), 0, SALTS});
+        v.push_back({4, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_probe_records_kernel<C>), 0, SALTS});
+        v.push_back({7, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_batch_kernel<C, true>), 0, SALTS});
+        v.push_back({8, B, S, K, T, P, KPT, reinterpret_cast<const void*>(&sbf_batch_kernel<C, false>), 0, SALTS});
       });
     });
   });
-  v.push_back({3, B, S, K, 0, 0, 0, reinterpret_cast<const void*>(&sbf_partition_kernel<B, S, K, false>)});
-  v.push_back({5, B, S, K, 0, 0, 0, reinterpret_cast<const void*>(&sbf_partition_kernel<B, S, K, true>)});
+  v.push_back({3, B, S, K, 0, 0, 0, reinterpret_cast<const void*>(&sbf_partition_kernel<B, S, K, false, SALTS>), 0,
+               SALTS});
+  v.push_back({5, B, S, K, 0, 0, 0, reinterpret_cast<const void*>(&sbf_partition_kernel<B, S, K, true, SALTS>), 0,
+               SALTS});
 }
 
 template <int B, int S, int K, int Z>
@@ -79,6 +81,8 @@ void register_geometry(std::vector<KernelEntry>& v) {
   if constexpr (4 % s == 0) register_k<B, S, 4>(v);
   if constexpr (s <= 8) register_k<B, S, 8>(v);
   if constexpr (s <= 16) register_k<B, S, 16>(v);
+  // the Parquet split-block salt set exists for its one geometry
+  if constexpr (B == 256 && S == 32) register_k<256, 32, 8, 1>(v);
 }
 
 }  // namespace bloomgb

@@ -191,3 +191,29 @@ def test_mma_cost_arguments_rejected_without_gpu(L):
     assert lib.bf_mma_cost(64, 0, 0, ctypes.byref(c)) == L.BF_EINVAL
     assert lib.bf_mma_cost(64, 0, 1 << 25, ctypes.byref(c)) == L.BF_EINVAL
     assert lib.bf_mma_cost(64, 1, 10, None) == L.BF_EINVAL
+
+
+def test_parquet_salt_set_params(L):
+    ok = L.bf_params(100, 256, 32, 8, 0, 0, 1, 0)
+    assert L.bf_params_check(ok) == L.BF_OK
+    assert L.bf_params_check(L.bf_params(100, 256, 32, 8, 8, 0, 1, 0)) == L.BF_OK  # groups = s is sectorized
+    for bad in [(100, 256, 32, 16, 0, 0, 1, 0), (100, 512, 32, 16, 0, 0, 1, 0), (100, 256, 64, 8, 0, 0, 1, 0),
+                (100, 256, 32, 8, 2, 0, 1, 0), (100, 256, 32, 8, 0, 0, 2, 0)]:
+        assert L.bf_params_check(L.bf_params(*bad)) == L.BF_EINVAL, bad
+
+
+def test_params_struct_layout_matches_the_header(L, tmp_path):
+    import ctypes
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src = tmp_path / "p.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "bloomgb.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(bf_params), offsetof(bf_params, seed),'
+                   'offsetof(bf_params, salts), offsetof(bf_params, reserved)); return 0;}\n')
+    exe = tmp_path / "p"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    S = L.bf_params
+    assert got == [ctypes.sizeof(S), S.seed.offset, S.salts.offset, S.reserved.offset]
