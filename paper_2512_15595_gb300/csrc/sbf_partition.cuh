@@ -61,7 +61,7 @@ __device__ __forceinline__ bool lookup_one(const typename WordOf<S>::type* filte
 // with the index of its query in `idx`; a query whose slice buffer is full is
 // answered on the spot (its result bit is set if it is found).
 template <int B, int S, int K, bool LOOKUP, int SALTS = 0>
-__global__ void __launch_bounds__(kPartThreads, 3) sbf_partition_kernel(const PartArgs a) {
+__global__ void __launch_bounds__(kPartThreads, LOOKUP ? 3 : 4) sbf_partition_kernel(const PartArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* tile_rec = reinterpret_cast<uint64_t*>(smem);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(tile_rec + kPartTile);
