@@ -529,65 +529,156 @@ def run_sweep(args, w, wname):
     print(json.dumps({"sweep": wname, "key": res["key"], "best": res["entry"]}), flush=True)
 
 
-def run_batched(args):
-    """Batched filters: 4096 filters, log-uniform 4 KiB-16 MiB (256-bit blocks,
-    S=32, K=8), 2^28 keys split in proportion to size; one step = build all
-    filters + probe all of them (half of each run replaced by fresh keys), as
-    one captured CUDA graph of two launches, against one launch per filter per
-    operation."""
+BATCH_GEOMETRIES = [(64, 32), (128, 32), (256, 32), (64, 64), (128, 64), (256, 64), (512, 64)]  # K = 8 valid
+
+
+class _BatchRun:
+    """One geometry's batch over the batched workload's filters: an arena of
+    the filters' bit arrays (same bytes per filter for every geometry, whole
+    blocks), the Batch handle, and its captured build + probe graph."""
+
+    def __init__(self, torch, B, S, K, size_bytes, key_off, counts, ins, qd, out, device):
+        from synthkeys import batches
+        from paper_2512_15595_gb300 import Batch
+        self.B, self.S, self.K = B, S, K
+        bb = B // 8
+        self.blocks = batches.blocks_of(size_bytes, bb)
+        off, self.arena_bytes = batches.arena_offsets(self.blocks, bb)
+        self.arena = torch.zeros(self.arena_bytes, dtype=torch.uint8, device=device)
+        self.views = [self.arena[int(o):int(o) + int(b) * bb] for o, b in zip(off, self.blocks)]
+        self.batch = Batch([(v, int(b), int(ko), int(c))
+                            for v, b, ko, c in zip(self.views, self.blocks, key_off, counts)], B, S, K)
+        self.ins, self.qd, self.out = ins, qd, out
+        self.graph = None
+
+    def capture(self, torch):
+        stream = torch.cuda.Stream()
+        stream.wait_stream(torch.cuda.current_stream())
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=stream):
+            self.batch.add(self.ins, stream=stream)
+            self.batch.contains(self.qd, out=self.out, stream=stream)
+
+    def false_positives(self, torch) -> int:
+        """Positives among the fresh (odd-indexed) queries after a full step."""
+        self.batch.add(self.ins)
+        self.batch.contains(self.qd, out=self.out)
+        return int(self.out[1::2].sum().item())
+
+    def close(self):
+        self.batch.close()
+        self.arena = None
+        self.views = None
+
+
+def _batched_inputs(torch, device, B=256):
+    """The batched workload: 4096 filter sizes log-uniform 4 KiB-16 MiB (PCG64
+    seed 5), 2^28 insert keys split in proportion to the 256-bit-block counts,
+    queries = the insert stream with every second key replaced by a fresh one."""
     import numpy as np
-    import torch
     import synthkeys
     from synthkeys import batches
-    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS, Batch, Filter
-    device = torch.device("cuda", 0)
-    torch.cuda.set_device(device)
-    B, S, K, nfilters, total = 256, 32, 8, 4096, 1 << 28
-    bb = B // 8
-    blocks = batches.log_uniform_sizes(nfilters, 4 << 10, 16 << 20, bb, seed=5)
-    counts = batches.proportional_counts(blocks, total)
+    nfilters, total = 4096, 1 << 28
+    size_bytes = batches.log_uniform_bytes(nfilters, 4 << 10, 16 << 20, seed=5)
+    counts = batches.proportional_counts(batches.blocks_of(size_bytes, B // 8), total)
     key_off = np.zeros(nfilters, dtype=np.int64)
     key_off[1:] = np.cumsum(counts)[:-1]
-    off, arena_bytes = batches.arena_offsets(blocks, bb)
-    arena = torch.zeros(arena_bytes, dtype=torch.uint8, device=device)
-    views = [arena[int(o):int(o) + int(b) * bb] for o, b in zip(off, blocks)]
     ins = synthkeys.splitmix64_torch(synthkeys.SEED_INSERT, 0, total, device)
     fresh = synthkeys.splitmix64_torch(synthkeys.SEED_FRESH, 0, total, device)
     qd = ins.clone()
     qd[1::2] = fresh[1::2]
     del fresh
     out = torch.zeros(total, dtype=torch.uint8, device=device)
-    batch = Batch([(v, int(b), int(ko), int(c)) for v, b, ko, c in zip(views, blocks, key_off, counts)], B, S, K)
-    for op, lay in ((BF_OP_ADD, dict(cg=4, phi=2, kpt=4)), (BF_OP_CONTAINS, dict(cg=1, phi=8, kpt=4))):
-        batch.set_layout(op, **lay)
-    stream = torch.cuda.Stream()
-    stream.wait_stream(torch.cuda.current_stream())
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=stream):
-        batch.add(ins, stream=stream)
-        batch.contains(qd, out=out, stream=stream)
+    return size_bytes, counts, key_off, ins, qd, out
 
-    def timed(fn, steps, warm):
-        for _ in range(warm):
-            fn()
-        torch.cuda.synchronize()
-        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s_.record()
-        for _ in range(steps):
-            fn()
-        e_.record()
-        e_.synchronize()
-        return s_.elapsed_time(e_) / steps
 
-    ms_graph = timed(g.replay, args.steps, args.warmup)
-    # eager batched calls (same two launches, not captured)
-    ms_eager = timed(lambda: (batch.add(ins), batch.contains(qd, out=out)), args.steps, args.warmup)
+def _timed(torch, fn, steps, warm):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s_.record()
+    for _ in range(steps):
+        fn()
+    e_.record()
+    e_.synchronize()
+    return s_.elapsed_time(e_) / steps
+
+
+def run_batched_sweep(args):
+    """Autotune the batched workload: every compiled layout of the batched add
+    and contains launches for every geometry with K = 8, then the block width
+    (and word size) of the fastest step whose false positives on the fresh
+    queries stay within the 3-sigma band of the 256-bit / 32-bit geometry's.
+    Stores the layouts per geometry and the choice in tuned_layouts.json."""
+    import torch
+    from paper_2512_15595_gb300 import autotune
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    K = 8
+    size_bytes, counts, key_off, ins, qd, out = _batched_inputs(torch, device)
+    table = autotune.load_tuned()
+    results = []
+    for B, S in BATCH_GEOMETRIES:
+        run = _BatchRun(torch, B, S, K, size_bytes, key_off, counts, ins, qd, out, device)
+        res = autotune.sweep_batch(torch, run.batch, ins, qd, out, reps=3)
+        run.arena.zero_()
+        fp = run.false_positives(torch)
+        entry = dict(res["entry"], fp=fp, queries=int(counts.sum()) // 2, filter_bytes=int(run.arena_bytes))
+        table[res["key"]] = entry
+        results.append(dict(block_bits=B, word_bits=S, k=K, step_ms=entry["step_ms"], fp=fp,
+                            queries=entry["queries"]))
+        print(json.dumps({"sweep": "batched", "key": res["key"], "best": entry}), flush=True)
+        run.close()
+        del run
+        torch.cuda.empty_cache()
+    choice = autotune.choose_batch_geometry(results, (256, 32))
+    table[f"batch_K{K}_geometry"] = choice
+    autotune.save_tuned(table)
+    print(json.dumps({"sweep": "batched", "geometry": choice}), flush=True)
+
+
+def run_batched(args):
+    """Batched filters: 4096 filters, log-uniform 4 KiB-16 MiB (256-bit blocks,
+    S=32, K=8), 2^28 keys split in proportion to size; one step = build all
+    filters + probe all of them (half of each run replaced by fresh keys), as
+    one captured CUDA graph of two launches, against one launch per filter per
+    operation.  Layouts come from the autotuner's table when it holds this
+    geometry; the geometry the autotuner picked (block width at the same FPR
+    band) is timed beside it when it differs."""
+    import numpy as np
+    import torch
+    import synthkeys
+    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS, Filter, autotune
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    B, S, K = 256, 32, 8
+    size_bytes, counts, key_off, ins, qd, out = _batched_inputs(torch, device)
+    nfilters, total = len(counts), int(counts.sum())
+    default_layouts = {BF_OP_ADD: dict(cg=4, phi=2, kpt=4), BF_OP_CONTAINS: dict(cg=1, phi=8, kpt=4)}
+
+    def layouts_for(b, s_):
+        tuned = {op: autotune.tuned_batch_layout(b, s_, K, op) for op in (BF_OP_ADD, BF_OP_CONTAINS)}
+        if all(tuned.values()):
+            return tuned, True
+        return default_layouts, False
+
+    run = _BatchRun(torch, B, S, K, size_bytes, key_off, counts, ins, qd, out, device)
+    lays, autotuned = layouts_for(B, S)
+    for op, lay in lays.items():
+        run.batch.set_layout(op, **lay)
+    run.capture(torch)
+    ms_graph = _timed(torch, run.graph.replay, args.steps, args.warmup)
+    # eager batched calls (same two launches, not captured), and each operation alone
+    ms_eager = _timed(torch, lambda: (run.batch.add(ins), run.batch.contains(qd, out=out)), args.steps, args.warmup)
+    ms_add = _timed(torch, lambda: run.batch.add(ins), args.steps, 1)
+    ms_con = _timed(torch, lambda: run.batch.contains(qd, out=out), args.steps, 1)
     # one launch per filter per operation, on the same buffers
-    fs = [Filter(int(b), B, S, K, 0, words=v) for v, b in zip(views, blocks)]
+    fs = [Filter(int(b), B, S, K, 0, words=v) for v, b in zip(run.views, run.blocks)]
     for f in fs:
         f.set_partition(mode=0, lookup_mode=0)
-        f.set_layout(BF_OP_ADD, cg=4, phi=2, kpt=4)
-        f.set_layout(BF_OP_CONTAINS, cg=1, phi=8, kpt=4)
+        for op, lay in lays.items():
+            f.set_layout(op, **lay)
     runs = [(f, ins[ko:ko + c], qd[ko:ko + c], out[ko:ko + c]) for f, ko, c in zip(fs, key_off, counts) if c]
 
     def per_filter():
@@ -595,22 +686,30 @@ def run_batched(args):
             f.add(k_)
         for f, k_, q_, o_ in runs:
             f.contains(q_, out=o_)
-    ms_per_filter = timed(per_filter, max(1, args.steps // 2), 1)
+    ms_per_filter = _timed(torch, per_filter, max(1, args.steps // 2), 1)
+    for f in fs:
+        f.close()
+    per_filter_launches = 2 * len(runs)
+    del fs, runs
     # properties: no false negatives; FPR of the fresh half
-    g.replay()
+    run.graph.replay()
     torch.cuda.synchronize()
-    members = out[0::2]
-    fn = int((members == 0).sum().item())
-    fpr = float(out[1::2].float().mean().item())
+    fn = int((out[0::2] == 0).sum().item())
+    fp = int(out[1::2].sum().item())
     # spot parity of a few filters against the oracle
     import oracle
     sample = [0, 1, nfilters // 2, nfilters - 1]
     mismatches = 0
     for i in sample:
-        geom = oracle.Geometry(num_blocks=int(blocks[i]), block_bits=B, word_bits=S, k=K, seed=0)
+        geom = oracle.Geometry(num_blocks=int(run.blocks[i]), block_bits=B, word_bits=S, k=K, seed=0)
         ref = oracle.SBF(geom)
         ref.add(synthkeys.splitmix64(synthkeys.SEED_INSERT, int(key_off[i]), int(counts[i])))
-        mismatches += int(not np.array_equal(views[i].cpu().numpy(), ref.as_bytes()))
+        mismatches += int(not np.array_equal(run.views[i].cpu().numpy(), ref.as_bytes()))
+    layouts = {"add": run.batch.layout(BF_OP_ADD), "contains": run.batch.layout(BF_OP_CONTAINS)}
+    arena_bytes = run.arena_bytes
+    run.close()
+    del run
+    torch.cuda.empty_cache()
     keys_per_step = 2 * total
     line = {
         "metric": "batched build+probe, G keys/s (4096 filters, one CUDA-graph launch per step)",
@@ -619,19 +718,38 @@ def run_batched(args):
         "dtype": "u64 keys / u32 words (integer)", "data": "synthetic",
         "config": {"workload": "batched", "filters": nfilters, "sizes": "log-uniform 4 KiB-16 MiB (seed 5)",
                    "filter_bytes": int(arena_bytes), "keys": total, "queries": total,
-                   "layouts": {"add": batch.layout(BF_OP_ADD), "contains": batch.layout(BF_OP_CONTAINS)}},
+                   "layouts": layouts, "layouts_autotuned": autotuned},
         "eager_batched_ms_per_step": ms_eager,
-        "per_filter_launches": {"ms_per_step": ms_per_filter, "launches_per_step": 2 * len(runs),
+        "add_gkeys_s": total / (ms_add * 1e-3) / 1e9, "contains_gkeys_s": total / (ms_con * 1e-3) / 1e9,
+        "per_filter_launches": {"ms_per_step": ms_per_filter, "launches_per_step": per_filter_launches,
                                 "value": keys_per_step / (ms_per_filter * 1e-3) / 1e9},
         "speedup_vs_per_filter": ms_per_filter / ms_graph,
         "gpu_launches": 2 * args.steps,
-        "checks": {"false_negatives": fn, "fpr_fresh_half": fpr, "oracle_filters_checked": len(sample),
+        "checks": {"false_negatives": fn, "false_positives": fp, "fresh_queries": total // 2,
+                   "fpr_fresh_half": fp / (total // 2), "oracle_filters_checked": len(sample),
                    "oracle_mismatches": mismatches},
     }
+    choice = autotune.load_tuned().get(f"batch_K{K}_geometry")
+    if choice and (choice["block_bits"], choice["word_bits"]) != (B, S):
+        Bt, St = choice["block_bits"], choice["word_bits"]
+        trun = _BatchRun(torch, Bt, St, K, size_bytes, key_off, counts, ins, qd, out, device)
+        tl, _ = layouts_for(Bt, St)
+        for op, lay in tl.items():
+            trun.batch.set_layout(op, **lay)
+        tfp = trun.false_positives(torch)
+        tfn = int((out[0::2] == 0).sum().item())
+        trun.capture(torch)
+        tms = _timed(torch, trun.graph.replay, args.steps, args.warmup)
+        line["tuned_geometry"] = {"block_bits": Bt, "word_bits": St, "k": K, "ms_per_step": tms,
+                                  "value": keys_per_step / (tms * 1e-3) / 1e9, "false_positives": tfp,
+                                  "false_negatives": tfn, "fp_limit": choice["fp_limit"],
+                                  "layouts": {"add": trun.batch.layout(BF_OP_ADD),
+                                              "contains": trun.batch.layout(BF_OP_CONTAINS)},
+                                  "filter_bytes": int(trun.arena_bytes), "gpu_launches": 2 * args.steps}
+        trun.close()
+    elif choice:
+        line["tuned_geometry"] = {"block_bits": B, "word_bits": S, "k": K, "same_as_workload": True}
     print(json.dumps(line), flush=True)
-    for f in fs:
-        f.close()
-    batch.close()
 
 
 def run_frontier(args):
@@ -1063,6 +1181,8 @@ def main():
     if args.workload == "batched":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "no CPU arm for the batched workload"}))
+        elif args.sweep:
+            run_batched_sweep(args)
         else:
             run_batched(args)
         return

@@ -6,7 +6,10 @@ across architectures).  This module times every compiled layout (Theta, Phi,
 keys per thread) of one geometry through the C ABI with CUDA events, keeps
 the fastest per operation, and stores the choice in ``tuned_layouts.json``
 next to this file, keyed by geometry and residency regime.  Filters built
-through :func:`apply_tuned` start from that choice.
+through :func:`apply_tuned` start from that choice.  For batches of filters
+(one launch per operation over all of them) it tunes the batched launches'
+layouts per geometry and picks the block width and word size at a
+false-positive band (:func:`sweep_batch`, :func:`choose_batch_geometry`).
 """
 from __future__ import annotations
 
@@ -122,3 +125,100 @@ def sweep(torch, f: Filter, keys_add, keys_q, out, regime: str, kpts=(1, 2, 4), 
     entry = {"add": best["add"], "contains": best["contains"],
              "n_add": keys_add.numel(), "n_contains": keys_q.numel(), "filter_bytes": f.nbytes}
     return {"key": key_of(p.block_bits, p.word_bits, p.k, regime), "entry": entry, "rows": rows}
+
+
+# --- batched filters ---------------------------------------------------------
+#
+# A batch fixes one geometry for all its filters; the autotuner times every
+# compiled layout (Theta, Phi, keys per thread) of the batched add and
+# contains launches, and, across geometries with the same K at the same bytes
+# per filter, picks the block width (and word size) of the fastest build +
+# probe step whose measured false-positive count stays within the binomial
+# 3-sigma band of a reference geometry's.
+
+
+def batch_key(block_bits: int, word_bits: int, k: int) -> str:
+    return f"batch_B{block_bits}_S{word_bits}_K{k}"
+
+
+def tuned_batch_layout(block_bits: int, word_bits: int, k: int, op: int) -> dict | None:
+    entry = load_tuned().get(batch_key(block_bits, word_bits, k))
+    if not entry:
+        return None
+    return entry.get("add" if op == BF_OP_ADD else "contains", {}).get("layout")
+
+
+def time_call(torch, fn, reps: int = 5, warmup: int = 2) -> float:
+    """Median device time (ms) of fn() on the current stream."""
+    stream = torch.cuda.current_stream()
+    times = []
+    for i in range(warmup + reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        e.synchronize()
+        if i >= warmup:
+            times.append(s.elapsed_time(e))
+    times.sort()
+    return times[len(times) // 2]
+
+
+def sweep_batch(torch, batch, keys_add, keys_q, out, kpts=(1, 2, 4), reps: int = 5, log=None) -> dict:
+    """Time every layout of the batched add and contains; returns the table entry.
+
+    ``batch``: a :class:`Batch`; its layouts are left at the best found.
+    """
+    p = batch.params
+    rows, best = [], {}
+    for op, name in ((BF_OP_ADD, "add"), (BF_OP_CONTAINS, "contains")):
+        if op == BF_OP_ADD:
+            fn = lambda: batch.add(keys_add)  # noqa: E731
+        else:
+            fn = lambda: batch.contains(keys_q, out=out)  # noqa: E731
+        for cg, phi in valid_layouts(p.block_bits, p.word_bits):
+            for kpt in kpts:
+                lay = dict(cg=cg, phi=phi, kpt=kpt)
+                batch.set_layout(op, **lay)
+                ms = time_call(torch, fn, reps=reps)
+                g = batch.total_keys / (ms * 1e-3) / 1e9
+                row = dict(op=name, gkeys_s=g, ms=ms, **lay)
+                rows.append(row)
+                if log:
+                    log(row)
+                if name not in best or ms < best[name]["ms"]:
+                    best[name] = dict(gkeys_s=g, ms=ms, layout=lay)
+        batch.set_layout(op, **best[name]["layout"])
+    entry = {"add": best["add"], "contains": best["contains"], "step_ms": best["add"]["ms"] + best["contains"]["ms"],
+             "filters": batch.nfilters, "keys": batch.total_keys}
+    return {"key": batch_key(p.block_bits, p.word_bits, p.k), "entry": entry, "rows": rows}
+
+
+def fp_count_limit(reference_count: int) -> float:
+    """Upper end of the 3-sigma band of a false-positive count (Poisson
+    approximation of the binomial, at least one count of width)."""
+    return reference_count + 3.0 * max(1.0, reference_count) ** 0.5
+
+
+def choose_batch_geometry(results: list, reference: tuple, min_gain: float = 0.03) -> dict:
+    """Pick the fastest geometry whose false positives stay within the band.
+
+    ``results``: dicts with block_bits, word_bits, k, step_ms, fp (false
+    positives among ``queries`` non-member queries), queries.  ``reference``:
+    (block_bits, word_bits) of the geometry whose count sets the band.  Another
+    geometry replaces the reference only if its step is at least ``min_gain``
+    (a fraction) faster, so that timing noise does not trade FPR for nothing.
+    """
+    ref = [r for r in results if (r["block_bits"], r["word_bits"]) == tuple(reference)]
+    if not ref:
+        raise ValueError("reference geometry not among the results")
+    limit = fp_count_limit(ref[0]["fp"])
+    ok = [r for r in results if r["fp"] <= limit]
+    best = min(ok, key=lambda r: r["step_ms"])
+    if best["step_ms"] > ref[0]["step_ms"] * (1.0 - min_gain):
+        best = ref[0]
+    return {"block_bits": best["block_bits"], "word_bits": best["word_bits"], "k": best["k"],
+            "step_ms": best["step_ms"], "fp": best["fp"], "fp_limit": limit,
+            "reference": {"block_bits": reference[0], "word_bits": reference[1], "fp": ref[0]["fp"],
+                          "step_ms": ref[0]["step_ms"]},
+            "min_gain": min_gain, "queries": best["queries"]}

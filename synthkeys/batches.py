@@ -11,12 +11,21 @@ from __future__ import annotations
 import numpy as np
 
 
-def log_uniform_sizes(nfilters: int, min_bytes: int, max_bytes: int, block_bytes: int, seed: int = 5):
+def log_uniform_bytes(nfilters: int, min_bytes: int, max_bytes: int, seed: int = 5):
+    """Filter sizes in whole bytes, log-uniform in [min_bytes, max_bytes)."""
     rng = np.random.default_rng(seed)
     u = rng.random(nfilters)
     sizes = np.exp(np.log(min_bytes) + u * (np.log(max_bytes) - np.log(min_bytes)))
-    blocks = np.maximum(1, (sizes // block_bytes).astype(np.int64))
-    return blocks
+    return np.floor(sizes).astype(np.int64)
+
+
+def blocks_of(size_bytes: np.ndarray, block_bytes: int):
+    """Whole blocks per filter (at least one)."""
+    return np.maximum(1, size_bytes // block_bytes)
+
+
+def log_uniform_sizes(nfilters: int, min_bytes: int, max_bytes: int, block_bytes: int, seed: int = 5):
+    return blocks_of(log_uniform_bytes(nfilters, min_bytes, max_bytes, seed), block_bytes)
 
 
 def proportional_counts(weights: np.ndarray, total: int) -> np.ndarray:

@@ -153,3 +153,33 @@ def test_empty_batch_and_errors(torch):
         Batch([(buf, 0, 0, 10)], 256, 32, 8)  # no blocks
     with pytest.raises(BloomError):
         Batch([(buf, 32, 0, 10)], 256, 32, 4)  # k < s
+
+
+def test_batch_autotune_sweep_keeps_parity(torch):
+    """The batched autotuner times every layout, leaves the fastest set, and
+    the batch built with it still equals the oracle filter by filter."""
+    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS, autotune, valid_layouts
+    B, S, k = 256, 32, 8
+    batch, filters, keys, views = make_batch(torch, B, S, k, nfilters=41, total_keys=120_000, seed=9)
+    q = queries_for(keys, filters, 56)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dq = torch.from_numpy(q.view(np.int64)).cuda()
+    out = torch.zeros(q.size, dtype=torch.uint8, device="cuda")
+    res = autotune.sweep_batch(torch, batch, dk, dq, out, kpts=(1, 4), reps=1)
+    assert res["key"] == "batch_B256_S32_K8"
+    assert len(res["rows"]) == 2 * 2 * len(valid_layouts(B, S))
+    for op, name in ((BF_OP_ADD, "add"), (BF_OP_CONTAINS, "contains")):
+        got = batch.layout(op)
+        want = res["entry"][name]["layout"]
+        assert (got["cg"], got["phi"], got["kpt"]) == (want["cg"], want["phi"], want["kpt"])
+        assert res["entry"][name]["ms"] == min(r["ms"] for r in res["rows"] if r["op"] == name)
+    for v in views:
+        v.zero_()
+    batch.add(dk)
+    got = batch.contains(dq, out=out).cpu().numpy()
+    want = np.zeros(q.size, dtype=np.uint8)
+    for i, (v, b, ko, c) in enumerate(filters):
+        ref = oracle_for(filters, keys, B, S, k, i)
+        assert np.array_equal(v.cpu().numpy(), ref.as_bytes()), f"filter {i}"
+        want[ko:ko + c] = ref.contains(q[ko:ko + c])
+    assert np.array_equal(got, want)
