@@ -217,3 +217,23 @@ def test_params_struct_layout_matches_the_header(L, tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     S = L.bf_params
     assert got == [ctypes.sizeof(S), S.seed.offset, S.salts.offset, S.reserved.offset]
+
+
+def test_partition_struct_layout_matches_the_header(L, tmp_path):
+    import ctypes
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    fields = ("mode", "slice_log2", "chunk_keys", "cap_override", "window_log2", "lookup_mode",
+              "lookup_chunk_keys")
+    src = tmp_path / "q.c"
+    offs = ", ".join(f"offsetof(bf_partition, {f})" for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "bloomgb.h"\n'
+                   'int main(void){printf("' + " ".join(["%zu"] * (len(fields) + 1)) + '\\n", '
+                   'sizeof(bf_partition), ' + offs + '); return 0;}\n')
+    exe = tmp_path / "q"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    S = L.bf_partition
+    assert got == [ctypes.sizeof(S)] + [getattr(S, f).offset for f in fields]
