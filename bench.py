@@ -571,14 +571,14 @@ class _BatchRun:
         self.views = None
 
 
-def _batched_inputs(torch, device, B=256):
+def _batched_inputs(torch, device, nfilters=4096, total=1 << 28, B=256):
     """The batched workload: 4096 filter sizes log-uniform 4 KiB-16 MiB (PCG64
     seed 5), 2^28 insert keys split in proportion to the 256-bit-block counts,
-    queries = the insert stream with every second key replaced by a fresh one."""
+    queries = the insert stream with every second key replaced by a fresh one
+    (fewer filters and keys for profiling-sized cases)."""
     import numpy as np
     import synthkeys
     from synthkeys import batches
-    nfilters, total = 4096, 1 << 28
     size_bytes = batches.log_uniform_bytes(nfilters, 4 << 10, 16 << 20, seed=5)
     counts = batches.proportional_counts(batches.blocks_of(size_bytes, B // 8), total)
     key_off = np.zeros(nfilters, dtype=np.int64)
@@ -607,21 +607,25 @@ def _timed(torch, fn, steps, warm):
 
 def run_batched_sweep(args):
     """Autotune the batched workload: every compiled layout of the batched add
-    and contains launches for every geometry with K = 8, then the block width
+    and contains launches (with and without the L2 prefetch hint, at four grid
+    sizes) for every geometry with K = 8, then the block width
     (and word size) of the fastest step whose false positives on the fresh
     queries stay within the 3-sigma band of the 256-bit / 32-bit geometry's.
     Stores the layouts per geometry and the choice in tuned_layouts.json."""
     import torch
-    from paper_2512_15595_gb300 import autotune
+    from paper_2512_15595_gb300 import BF_HINT_PREFETCH_L2, autotune
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
     K = 8
-    size_bytes, counts, key_off, ins, qd, out = _batched_inputs(torch, device)
+    size_bytes, counts, key_off, ins, qd, out = _batched_inputs(torch, device, args.batch_filters, args.batch_keys)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    grids = (0, sms, 2 * sms, 4 * sms)
     table = autotune.load_tuned()
     results = []
     for B, S in BATCH_GEOMETRIES:
         run = _BatchRun(torch, B, S, K, size_bytes, key_off, counts, ins, qd, out, device)
-        res = autotune.sweep_batch(torch, run.batch, ins, qd, out, reps=3)
+        res = autotune.sweep_batch(torch, run.batch, ins, qd, out, reps=3, flag_sets=(0, BF_HINT_PREFETCH_L2),
+                                   grids=grids)
         run.arena.zero_()
         fp = run.false_positives(torch)
         entry = dict(res["entry"], fp=fp, queries=int(counts.sum()) // 2, filter_bytes=int(run.arena_bytes))
@@ -653,7 +657,7 @@ def run_batched(args):
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
     B, S, K = 256, 32, 8
-    size_bytes, counts, key_off, ins, qd, out = _batched_inputs(torch, device)
+    size_bytes, counts, key_off, ins, qd, out = _batched_inputs(torch, device, args.batch_filters, args.batch_keys)
     nfilters, total = len(counts), int(counts.sum())
     default_layouts = {BF_OP_ADD: dict(cg=4, phi=2, kpt=4), BF_OP_CONTAINS: dict(cg=1, phi=8, kpt=4)}
 
@@ -678,7 +682,8 @@ def run_batched(args):
     for f in fs:
         f.set_partition(mode=0, lookup_mode=0)
         for op, lay in lays.items():
-            f.set_layout(op, **lay)
+            # the same thread layout; each launch sized for its own filter
+            f.set_layout(op, cg=lay["cg"], phi=lay["phi"], kpt=lay["kpt"])
     runs = [(f, ins[ko:ko + c], qd[ko:ko + c], out[ko:ko + c]) for f, ko, c in zip(fs, key_off, counts) if c]
 
     def per_filter():
@@ -712,11 +717,12 @@ def run_batched(args):
     torch.cuda.empty_cache()
     keys_per_step = 2 * total
     line = {
-        "metric": "batched build+probe, G keys/s (4096 filters, one CUDA-graph launch per step)",
+        "metric": f"batched build+probe, G keys/s ({nfilters} filters, one CUDA-graph launch per step)",
         "value": keys_per_step / (ms_graph * 1e-3) / 1e9, "unit": "G keys/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
         "dtype": "u64 keys / u32 words (integer)", "data": "synthetic",
-        "config": {"workload": "batched", "filters": nfilters, "sizes": "log-uniform 4 KiB-16 MiB (seed 5)",
+        "config": {"workload": "batched" if (nfilters, total) == (4096, 1 << 28) else "batched (reduced)",
+                   "filters": nfilters, "sizes": "log-uniform 4 KiB-16 MiB (seed 5)",
                    "filter_bytes": int(arena_bytes), "keys": total, "queries": total,
                    "layouts": layouts, "layouts_autotuned": autotuned},
         "eager_batched_ms_per_step": ms_eager,
@@ -1153,6 +1159,8 @@ def main():
     ap.add_argument("--learned-members", type=int, default=1 << 26,
                     help="member keys of the learned workload (queries: as many non-members again)")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--batch-filters", type=int, default=4096, help="batched workload: number of filters")
+    ap.add_argument("--batch-keys", type=int, default=1 << 28, help="batched workload: keys (and queries)")
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--frontier", action="store_true")
     ap.add_argument("--sweep-keys", type=int, default=1 << 28)

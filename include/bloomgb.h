@@ -100,7 +100,12 @@ typedef enum { BF_OP_ADD = 0, BF_OP_CONTAINS = 1 } bf_op;
 /* Cache-policy hints (bit flags of bf_layout.flags). */
 enum {
     BF_HINT_FILTER_EVICT_LAST = 1u << 0,   /* filter accesses carry an L2 evict_last policy */
-    BF_HINT_KEYS_EVICT_NORMAL = 1u << 1    /* keys load with evict_normal instead of evict_first */
+    BF_HINT_KEYS_EVICT_NORMAL = 1u << 1,   /* keys load with evict_normal instead of evict_first */
+    BF_HINT_PREFETCH_L2 = 1u << 2          /* batched kernels only (others ignore it): while a warp
+                                              works on a key chunk, it bulk-prefetches into L2 the
+                                              share of its filter's bit array that belongs to the
+                                              chunk one grid-stride step ahead, so that filters
+                                              are streamed into L2 before their keys arrive */
 };
 
 /* Execution layout of one operation (Sec. IV-A, IV-C).

@@ -9,10 +9,11 @@ from __future__ import annotations
 
 from . import _lib
 from ._lib import (BF_GUPS_LOAD, BF_GUPS_RED_OR, BF_HINT_FILTER_EVICT_LAST, BF_HINT_KEYS_EVICT_NORMAL,
-                   BF_OP_ADD, BF_OP_CONTAINS, BloomError, bf_layout, bf_params)
+                   BF_HINT_PREFETCH_L2, BF_OP_ADD, BF_OP_CONTAINS, BloomError, bf_layout, bf_params)
 
 __all__ = ["Filter", "BloomError", "bf_params", "bf_layout", "BF_OP_ADD", "BF_OP_CONTAINS",
-           "BF_HINT_FILTER_EVICT_LAST", "BF_HINT_KEYS_EVICT_NORMAL", "BF_GUPS_LOAD", "BF_GUPS_RED_OR",
+           "BF_HINT_FILTER_EVICT_LAST", "BF_HINT_KEYS_EVICT_NORMAL", "BF_HINT_PREFETCH_L2", "BF_GUPS_LOAD",
+           "BF_GUPS_RED_OR",
            "valid_layouts", "device_tensor", "Batch"]
 
 

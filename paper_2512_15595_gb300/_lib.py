@@ -17,6 +17,7 @@ BF_OK, BF_EINVAL, BF_ENOMEM, BF_ECUDA, BF_EUNSUPPORTED, BF_ETIMEDOUT = range(6)
 BF_OP_ADD, BF_OP_CONTAINS = 0, 1
 BF_HINT_FILTER_EVICT_LAST = 1 << 0
 BF_HINT_KEYS_EVICT_NORMAL = 1 << 1
+BF_HINT_PREFETCH_L2 = 1 << 2
 BF_GUPS_LOAD, BF_GUPS_RED_OR = 0, 1
 BF_HOST_AUTO, BF_HOST_STAGED = 0, 1
 

@@ -164,10 +164,15 @@ def time_call(torch, fn, reps: int = 5, warmup: int = 2) -> float:
     return times[len(times) // 2]
 
 
-def sweep_batch(torch, batch, keys_add, keys_q, out, kpts=(1, 2, 4), reps: int = 5, log=None) -> dict:
+def sweep_batch(torch, batch, keys_add, keys_q, out, kpts=(1, 2, 4), reps: int = 5, log=None,
+                flag_sets=(0,), grids=(0,)) -> dict:
     """Time every layout of the batched add and contains; returns the table entry.
 
     ``batch``: a :class:`Batch`; its layouts are left at the best found.
+    ``flag_sets``: layout flag values to try with every layout (e.g. with and
+    without the L2 prefetch hint); ``grids``: CTA counts to try (0 = SMs x
+    resident CTAs per SM).  A smaller grid narrows the run of filters the
+    warps work on at a time, which decides how much of it stays in L2.
     """
     p = batch.params
     rows, best = [], {}
@@ -178,16 +183,18 @@ def sweep_batch(torch, batch, keys_add, keys_q, out, kpts=(1, 2, 4), reps: int =
             fn = lambda: batch.contains(keys_q, out=out)  # noqa: E731
         for cg, phi in valid_layouts(p.block_bits, p.word_bits):
             for kpt in kpts:
-                lay = dict(cg=cg, phi=phi, kpt=kpt)
-                batch.set_layout(op, **lay)
-                ms = time_call(torch, fn, reps=reps)
-                g = batch.total_keys / (ms * 1e-3) / 1e9
-                row = dict(op=name, gkeys_s=g, ms=ms, **lay)
-                rows.append(row)
-                if log:
-                    log(row)
-                if name not in best or ms < best[name]["ms"]:
-                    best[name] = dict(gkeys_s=g, ms=ms, layout=lay)
+                for flags in flag_sets:
+                    for grid in grids:
+                        lay = dict(cg=cg, phi=phi, kpt=kpt, flags=flags, grid_ctas=grid)
+                        batch.set_layout(op, **lay)
+                        ms = time_call(torch, fn, reps=reps)
+                        g = batch.total_keys / (ms * 1e-3) / 1e9
+                        row = dict(op=name, gkeys_s=g, ms=ms, **lay)
+                        rows.append(row)
+                        if log:
+                            log(row)
+                        if name not in best or ms < best[name]["ms"]:
+                            best[name] = dict(gkeys_s=g, ms=ms, layout=lay)
         batch.set_layout(op, **best[name]["layout"])
     entry = {"add": best["add"], "contains": best["contains"], "step_ms": best["add"]["ms"] + best["contains"]["ms"],
              "filters": batch.nfilters, "keys": batch.total_keys}

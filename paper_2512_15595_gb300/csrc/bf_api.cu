@@ -277,7 +277,7 @@ bf_status resolve_layout(const bf_params& p, int op, const bf_layout* in, bf_lay
   if (l.kpt != 1 && l.kpt != 2 && l.kpt != 4) return fail(BF_EINVAL, "kpt must be 1, 2 or 4");
   if (l.block_threads % 32 != 0 || l.block_threads > static_cast<uint32_t>(kMaxBlockThreadsHost))
     return fail(BF_EINVAL, "block_threads must be a multiple of 32 and <= 512");
-  if (l.flags & ~(BF_HINT_FILTER_EVICT_LAST | BF_HINT_KEYS_EVICT_NORMAL))
+  if (l.flags & ~(BF_HINT_FILTER_EVICT_LAST | BF_HINT_KEYS_EVICT_NORMAL | BF_HINT_PREFETCH_L2))
     return fail(BF_EINVAL, "unknown layout flag");
   const KernelEntry* e = z ? find_csbf(op == BF_OP_ADD ? 9 : 10, p, l, z) : find_sbf(op, p, l);
   if (!e) return fail(BF_EUNSUPPORTED, "no compiled kernel for this geometry and layout");
@@ -1066,8 +1066,11 @@ bf_status batch_resolve(bf_batch* b, int op, const bf_layout* in) {
 
 bf_status batch_launch(const bf_batch* b, int op, const uint64_t* keys, uint8_t* out, cudaStream_t stream) {
   if (b->total_chunks == 0) return BF_OK;
+  const uint64_t ahead = (b->layout[op].flags & BF_HINT_PREFETCH_L2)
+                            ? static_cast<uint64_t>(b->grid[op]) * (b->layout[op].block_threads / 32)
+                            : 0;
   BatchArgs a{b->d_filters, b->d_chunk_begin, b->nfilters, b->total_chunks, keys, out,
-              b->p.seed + 0x27D4EB2F165667C5ull + 8ull, b->layout[op].flags};
+              b->p.seed + 0x27D4EB2F165667C5ull + 8ull, b->layout[op].flags, ahead};
   void* args[] = {&a};
   cudaError_t e = cudaLaunchKernel(b->entry[op]->fn, dim3(b->grid[op]), dim3(b->layout[op].block_threads), args, 0,
                                    stream);

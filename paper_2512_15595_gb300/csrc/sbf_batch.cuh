@@ -22,6 +22,29 @@ __device__ __forceinline__ uint32_t batch_filter_of(const uint64_t* __restrict__
   return lo;  // the last filter starting at or before `chunk` (empty filters are skipped)
 }
 
+// Bulk-prefetch into L2 the share of chunk c's filter that belongs to chunk c:
+// bytes [i*F/n, (i+1)*F/n) of the filter's F bytes for its chunk i of n
+// (widened to 128-byte lines, clipped to the bit array).  All chunks of a
+// filter together prefetch the whole filter.  A hint: no completion is
+// awaited and the bits do not depend on it.
+template <class C>
+__device__ __forceinline__ void batch_prefetch(const BatchArgs& a, uint64_t c) {
+  if (c >= a.total_chunks) return;
+  const uint32_t fi = batch_filter_of(a.chunk_begin, a.nfilters, c);
+  const uint64_t c0 = __ldg(a.chunk_begin + fi), n = __ldg(a.chunk_begin + fi + 1) - c0;
+  const BatchFilter e = a.filters[fi];
+  const uint64_t bytes = (e.nblocks * (C::B / 8)) & ~15ull;
+  const uint64_t i = c - c0, per = bytes / n;
+  const uint64_t lo = (per * i) & ~127ull;
+  uint64_t hi = i + 1 == n ? bytes : ((per * (i + 1) + 127) & ~127ull);
+  if (hi > bytes) hi = bytes;
+  const char* base = static_cast<const char*>(e.words);
+  for (uint64_t p = lo; p < hi; p += (1u << 20)) {
+    const uint32_t len = static_cast<uint32_t>(hi - p < (1u << 20) ? hi - p : (1u << 20));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + p), "r"(len) : "memory");
+  }
+}
+
 template <class C, bool ADD>
 __global__ void __launch_bounds__(kMaxBlockThreads) sbf_batch_kernel(const BatchArgs a) {
   const TileCtx<C> t(a.flags);
@@ -30,6 +53,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_batch_kernel(const Batch
   const uint64_t warps_per_cta = blockDim.x >> 5;
   const uint64_t nwarps = static_cast<uint64_t>(gridDim.x) * warps_per_cta;
   for (uint64_t c = blockIdx.x * warps_per_cta + (threadIdx.x >> 5); c < a.total_chunks; c += nwarps) {
+    if (a.prefetch_chunks && (threadIdx.x & 31u) == 0) batch_prefetch<C>(a, c + a.prefetch_chunks);
     const uint32_t fi = batch_filter_of(a.chunk_begin, a.nfilters, c);
     const BatchFilter e = a.filters[fi];
     const uint64_t first = (c - __ldg(a.chunk_begin + fi)) * kBatchChunk;

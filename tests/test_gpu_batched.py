@@ -65,7 +65,7 @@ def queries_for(keys, filters, seed):
 
 @pytest.mark.parametrize("B,S,k", [(256, 32, 8), (512, 64, 16), (128, 32, 4)])
 def test_batch_matches_oracle_per_filter(torch, B, S, k):
-    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS, valid_layouts
+    from paper_2512_15595_gb300 import BF_HINT_PREFETCH_L2, BF_OP_ADD, BF_OP_CONTAINS, valid_layouts
     batch, filters, keys, views = make_batch(torch, B, S, k)
     q = queries_for(keys, filters, 55)
     refs = [oracle_for(filters, keys, B, S, k, i) for i in range(len(filters))]
@@ -74,12 +74,15 @@ def test_batch_matches_oracle_per_filter(torch, B, S, k):
         want[ko:ko + c] = ref.contains(q[ko:ko + c])
     dk = torch.from_numpy(keys.view(np.int64)).cuda()
     dq = torch.from_numpy(q.view(np.int64)).cuda()
+    it = 0
     for cg, phi in valid_layouts(B, S):
         for kpt in (1, 2, 4):
             for v in views:
                 v.zero_()
-            batch.set_layout(BF_OP_ADD, cg=cg, phi=phi, kpt=kpt)
-            batch.set_layout(BF_OP_CONTAINS, cg=cg, phi=phi, kpt=kpt)
+            flags = BF_HINT_PREFETCH_L2 if it % 2 else 0  # the L2 prefetch hint on every other layout
+            it += 1
+            batch.set_layout(BF_OP_ADD, cg=cg, phi=phi, kpt=kpt, flags=flags)
+            batch.set_layout(BF_OP_CONTAINS, cg=cg, phi=phi, kpt=kpt, flags=flags)
             batch.add(dk)
             out = batch.contains(dq)
             torch.cuda.synchronize()
@@ -91,6 +94,36 @@ def test_batch_matches_oracle_per_filter(torch, B, S, k):
                 covered[ko:ko + c] = True
             assert np.array_equal(got[covered], want[covered]), (cg, phi, kpt)
             assert not got[~covered].any()
+    batch.close()
+
+
+def test_batch_prefetch_tiny_and_ragged_filters(torch):
+    """The L2 prefetch hint on 64-bit blocks: filters of 1-5 blocks (8-40
+    bytes, below one 16-byte prefetch unit or with an 8-byte tail), odd
+    block counts and many chunks per filter; bits and answers as the oracle's."""
+    from paper_2512_15595_gb300 import BF_HINT_PREFETCH_L2, BF_OP_ADD, BF_OP_CONTAINS, Batch
+    B, S, k = 64, 32, 8
+    blocks = np.array([1, 2, 3, 5, 1, 4097, 3, 65537, 7, 1], dtype=np.int64)
+    counts = np.array([50, 0, 300, 1000, 7, 40_000, 129, 150_001, 1, 128], dtype=np.int64)
+    key_off = np.zeros(blocks.size, dtype=np.int64)
+    key_off[1:] = np.cumsum(counts)[:-1]
+    keys = synthkeys.splitmix64(301, 0, int(counts.sum()))
+    q = queries_for(keys, None, 302)
+    off, arena_bytes = batches.arena_offsets(blocks, B // 8)
+    arena = torch.zeros(arena_bytes, dtype=torch.uint8, device="cuda")
+    views = [arena[int(o):int(o) + int(b) * (B // 8)] for o, b in zip(off, blocks)]
+    filters = [(v, int(b), int(ko), int(c)) for v, b, ko, c in zip(views, blocks, key_off, counts)]
+    batch = Batch(filters, B, S, k, seed=11)
+    for op in (BF_OP_ADD, BF_OP_CONTAINS):
+        batch.set_layout(op, kpt=2, flags=BF_HINT_PREFETCH_L2)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dq = torch.from_numpy(q.view(np.int64)).cuda()
+    batch.add(dk)
+    got = batch.contains(dq).cpu().numpy().astype(np.uint8)
+    for i, (v, b, ko, c) in enumerate(filters):
+        ref = oracle_for(filters, keys, B, S, k, i)
+        assert np.array_equal(v.cpu().numpy(), ref.as_bytes()), i
+        assert np.array_equal(got[ko:ko + c], ref.contains(q[ko:ko + c])), i
     batch.close()
 
 
@@ -158,20 +191,22 @@ def test_empty_batch_and_errors(torch):
 def test_batch_autotune_sweep_keeps_parity(torch):
     """The batched autotuner times every layout, leaves the fastest set, and
     the batch built with it still equals the oracle filter by filter."""
-    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS, autotune, valid_layouts
+    from paper_2512_15595_gb300 import BF_HINT_PREFETCH_L2, BF_OP_ADD, BF_OP_CONTAINS, autotune, valid_layouts
     B, S, k = 256, 32, 8
     batch, filters, keys, views = make_batch(torch, B, S, k, nfilters=41, total_keys=120_000, seed=9)
     q = queries_for(keys, filters, 56)
     dk = torch.from_numpy(keys.view(np.int64)).cuda()
     dq = torch.from_numpy(q.view(np.int64)).cuda()
     out = torch.zeros(q.size, dtype=torch.uint8, device="cuda")
-    res = autotune.sweep_batch(torch, batch, dk, dq, out, kpts=(1, 4), reps=1)
+    res = autotune.sweep_batch(torch, batch, dk, dq, out, kpts=(1, 4), reps=1, flag_sets=(0, BF_HINT_PREFETCH_L2),
+                               grids=(0, 7))
     assert res["key"] == "batch_B256_S32_K8"
-    assert len(res["rows"]) == 2 * 2 * len(valid_layouts(B, S))
+    assert len(res["rows"]) == 2 * 2 * 2 * 2 * len(valid_layouts(B, S))
     for op, name in ((BF_OP_ADD, "add"), (BF_OP_CONTAINS, "contains")):
         got = batch.layout(op)
         want = res["entry"][name]["layout"]
-        assert (got["cg"], got["phi"], got["kpt"]) == (want["cg"], want["phi"], want["kpt"])
+        assert (got["cg"], got["phi"], got["kpt"], got["flags"], got["grid_ctas"]) == \
+            (want["cg"], want["phi"], want["kpt"], want["flags"], want["grid_ctas"])
         assert res["entry"][name]["ms"] == min(r["ms"] for r in res["rows"] if r["op"] == name)
     for v in views:
         v.zero_()
