@@ -678,7 +678,7 @@ def run_batched(args):
     ms_add = _timed(torch, lambda: run.batch.add(ins), args.steps, 1)
     ms_con = _timed(torch, lambda: run.batch.contains(qd, out=out), args.steps, 1)
     # one launch per filter per operation, on the same buffers
-    fs = [Filter(int(b), B, S, K, 0, words=v) for v, b in zip(run.views, run.blocks)]
+    fs = [] if args.no_per_filter else [Filter(int(b), B, S, K, 0, words=v) for v, b in zip(run.views, run.blocks)]
     for f in fs:
         f.set_partition(mode=0, lookup_mode=0)
         for op, lay in lays.items():
@@ -691,7 +691,7 @@ def run_batched(args):
             f.add(k_)
         for f, k_, q_, o_ in runs:
             f.contains(q_, out=o_)
-    ms_per_filter = _timed(torch, per_filter, max(1, args.steps // 2), 1)
+    ms_per_filter = _timed(torch, per_filter, max(1, args.steps // 2), 1) if runs else None
     for f in fs:
         f.close()
     per_filter_launches = 2 * len(runs)
@@ -727,15 +727,16 @@ def run_batched(args):
                    "layouts": layouts, "layouts_autotuned": autotuned},
         "eager_batched_ms_per_step": ms_eager,
         "add_gkeys_s": total / (ms_add * 1e-3) / 1e9, "contains_gkeys_s": total / (ms_con * 1e-3) / 1e9,
-        "per_filter_launches": {"ms_per_step": ms_per_filter, "launches_per_step": per_filter_launches,
-                                "value": keys_per_step / (ms_per_filter * 1e-3) / 1e9},
-        "speedup_vs_per_filter": ms_per_filter / ms_graph,
+        "per_filter_launches": None if ms_per_filter is None else {
+            "ms_per_step": ms_per_filter, "launches_per_step": per_filter_launches,
+            "value": keys_per_step / (ms_per_filter * 1e-3) / 1e9},
+        "speedup_vs_per_filter": None if ms_per_filter is None else ms_per_filter / ms_graph,
         "gpu_launches": 2 * args.steps,
         "checks": {"false_negatives": fn, "false_positives": fp, "fresh_queries": total // 2,
                    "fpr_fresh_half": fp / (total // 2), "oracle_filters_checked": len(sample),
                    "oracle_mismatches": mismatches},
     }
-    choice = autotune.load_tuned().get(f"batch_K{K}_geometry")
+    choice = None if args.no_per_filter else autotune.load_tuned().get(f"batch_K{K}_geometry")
     if choice and (choice["block_bits"], choice["word_bits"]) != (B, S):
         Bt, St = choice["block_bits"], choice["word_bits"]
         trun = _BatchRun(torch, Bt, St, K, size_bytes, key_off, counts, ins, qd, out, device)
@@ -1161,6 +1162,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--batch-filters", type=int, default=4096, help="batched workload: number of filters")
     ap.add_argument("--batch-keys", type=int, default=1 << 28, help="batched workload: keys (and queries)")
+    ap.add_argument("--no-per-filter", action="store_true",
+                    help="batched workload: skip the per-filter-launch comparison and the tuned-geometry run")
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--frontier", action="store_true")
     ap.add_argument("--sweep-keys", type=int, default=1 << 28)
