@@ -165,7 +165,11 @@ bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, ui
        cudaHostAlloc / cudaHostRegister, or any host memory on a GPU with
        pageable memory access, as on Grace-coupled GB300), the kernels read the
        keys and write the results in place over the CPU-GPU link; bf_add_host
-       then takes the same construction path as bf_add;
+       then takes the same construction path as bf_add, except that a
+       slice-partitioned construction runs in (at least) eight passes over two
+       alternating workspaces (twice the workspace of one such pass), the
+       record inserts of one pass on an internal stream while the next pass's
+       partition reads the host keys;
      staged: otherwise, or when bf_set_staging selected BF_HOST_STAGED, keys
        are copied in chunks into device staging buffers on three internal
        streams, overlapping the copies with the kernels, and results are

@@ -185,6 +185,10 @@ struct bf_filter {
   void* staging = nullptr;  // kPipelineDepth slots of slot_bytes(chunk_keys)
   cudaStream_t pipe[kPipelineDepth]{};
   cudaEvent_t ev_start = nullptr;
+  // construction from host-resident keys: record inserts on their own stream
+  cudaStream_t rec_stream = nullptr;
+  cudaEvent_t ev_part[2]{};
+  cudaEvent_t ev_rec[2]{};
   cudaEvent_t ev_done[kPipelineDepth]{};
   int host_access = 0;  // 0: kernels read device-accessible host buffers directly; 1: always stage
   bool l2_window = false;
@@ -419,6 +423,93 @@ bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cud
   return BF_OK;
 }
 
+// Construction from keys the kernels read in host memory: the slice
+// partition is bound by the host link, the record inserts (L2, no host
+// traffic) are not.  The keys go in kHostPasses passes over two alternating
+// workspaces; the record inserts of pass i run on a second stream while the
+// partition of pass i + 1 reads the link, the partition grid limited to
+// kHostPartCtas CTAs per SM so that record-insert CTAs find room beside it.
+// Ordering: pass i + 2 reuses pass i's workspace only after pass i's record
+// inserts (event), and the caller's stream waits for every record insert.
+constexpr uint64_t kHostPasses = 8;
+constexpr int kHostPartCtas = 1;
+
+bf_status launch_partitioned_host(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
+  const PartPlan pl = part_plan(f);
+  const uint64_t pass = std::min<uint64_t>(f->part.chunk_keys, (n + kHostPasses - 1) / kHostPasses);
+  const uint64_t counts_bytes = 8ull * static_cast<uint32_t>(kMaxParts);
+  const uint64_t ws_one = counts_bytes + static_cast<uint64_t>(pl.nparts) * part_cap(f, pl, pass) * 8;
+  if (ensure_part_ws(f, 2 * ws_one) != BF_OK) return launch_partitioned(f, keys, n, stream);
+  cudaError_t e;
+  if (!f->rec_stream && (e = cudaStreamCreateWithFlags(&f->rec_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamCreate");
+  for (int i = 0; i < 2; ++i) {
+    if (!f->ev_part[i] && (e = cudaEventCreateWithFlags(&f->ev_part[i], cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreate");
+    if (!f->ev_rec[i] && (e = cudaEventCreateWithFlags(&f->ev_rec[i], cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreate");
+  }
+  const KernelEntry* pe = find_op(3, f->p, 0, 0, 0);
+  const bf_layout& l = f->layout[BF_OP_ADD];
+  const KernelEntry* re = find_op(2, f->p, l.cg, l.phi, l.kpt);
+  if (!pe || !re) return fail(BF_EUNSUPPORTED, "no partition kernels for this geometry");
+  const size_t smem = partition_smem_bytes(static_cast<int>(pl.nparts));
+  if ((e = cudaFuncSetAttribute(pe->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
+      cudaSuccess)
+    return cuda_fail(e, "cudaFuncSetAttribute(partition)");
+  int sms = 0, per_sm = 0;
+  bf_status s = sm_count(f->device, &sms);
+  if (s != BF_OK) return s;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pe->fn, kPartThreads, smem)) != cudaSuccess)
+    return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(partition)");
+  per_sm = std::max(1, std::min(per_sm, kHostPartCtas));
+  const uint32_t slice_bytes_log2 = pl.shift + static_cast<uint32_t>(__builtin_ctz(f->p.block_bits / 8));
+  const uint32_t per_launch =
+      f->part.window_log2 > slice_bytes_log2 ? 1u << std::min<uint32_t>(f->part.window_log2 - slice_bytes_log2, 20) : 1u;
+  bool used[2] = {false, false};
+  uint64_t i = 0;
+  for (uint64_t lo = 0; lo < n; lo += pass, ++i) {
+    const int w = static_cast<int>(i & 1);
+    const uint64_t cnt = std::min(pass, n - lo);
+    const uint64_t cap = part_cap(f, pl, cnt);
+    char* base = static_cast<char*>(f->part_ws) + w * ws_one;
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(base);
+    uint64_t* records = reinterpret_cast<uint64_t*>(base + counts_bytes);
+    if (used[w] && (e = cudaStreamWaitEvent(stream, f->ev_rec[w], 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
+    if ((e = cudaMemsetAsync(counts, 0, 8ull * pl.nparts, stream)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    PartArgs pa{keys + lo, cnt, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, f->p.num_blocks,
+                f->p.num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, f->words};
+    const uint64_t tiles = (cnt + kPartTile - 1) / kPartTile;
+    const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, static_cast<uint64_t>(sms) * per_sm));
+    void* pargs[] = {&pa};
+    if ((e = cudaLaunchKernel(pe->fn, dim3(grid), dim3(kPartThreads), pargs, smem, stream)) != cudaSuccess)
+      return cuda_fail(e, "launch partition kernel");
+    f->last_launches += 1;
+    if ((e = cudaEventRecord(f->ev_part[w], stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(f->rec_stream, f->ev_part[w], 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
+    for (uint32_t plo = 0; plo < pl.nparts; plo += per_launch) {
+      const uint32_t phi = std::min(pl.nparts, plo + per_launch);
+      RecArgs ra{f->words, records, counts, plo, phi, cap, l.flags};
+      uint32_t rgrid = 0;
+      if ((s = resolve_grid(re->fn, f->device, l.block_threads, l.grid_ctas, (phi - plo) * cap, l.kpt, &rgrid)) !=
+          BF_OK)
+        return s;
+      void* rargs[] = {&ra};
+      if ((e = cudaLaunchKernel(re->fn, dim3(rgrid), dim3(l.block_threads), rargs, 0, f->rec_stream)) != cudaSuccess)
+        return cuda_fail(e, "launch record-insert kernel");
+      f->last_launches += 1;
+    }
+    if ((e = cudaEventRecord(f->ev_rec[w], f->rec_stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    used[w] = true;
+  }
+  for (int w = 0; w < 2; ++w)
+    if (used[w] && (e = cudaStreamWaitEvent(stream, f->ev_rec[w], 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
+  return BF_OK;
+}
+
 bool use_partitioned_lookup(const bf_filter* f, uint64_t n) {
   if (f->part.lookup_mode == BF_PART_OFF || f->p.num_blocks > (1ull << 32) || csbf_groups(f->p)) return false;
   const PartPlan pl = part_plan(f);
@@ -562,6 +653,13 @@ bf_status ensure_pipeline(bf_filter* f) {
 void release_pipeline(bf_filter* f) {
   if (f->staging) cudaFree(f->staging);
   f->staging = nullptr;
+  if (f->rec_stream) cudaStreamDestroy(f->rec_stream);
+  f->rec_stream = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    if (f->ev_part[i]) cudaEventDestroy(f->ev_part[i]);
+    if (f->ev_rec[i]) cudaEventDestroy(f->ev_rec[i]);
+    f->ev_part[i] = f->ev_rec[i] = nullptr;
+  }
   for (int i = 0; i < kPipelineDepth; ++i) {
     if (f->pipe[i]) cudaStreamDestroy(f->pipe[i]);
     if (f->ev_done[i]) cudaEventDestroy(f->ev_done[i]);
@@ -580,7 +678,8 @@ bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n
   // Grace-coupled GPUs read host memory coherently over NVLink-C2C: the
   // kernels then stream the keys (and write the results) in place.
   if (device_can_access(f, h_keys) && (op == BF_OP_ADD || device_can_access(f, h_out))) {
-    if (op == BF_OP_ADD) return run_add(f, h_keys, n, stream);
+    if (op == BF_OP_ADD)
+      return use_partitioned(f, n) ? launch_partitioned_host(f, h_keys, n, stream) : run_add(f, h_keys, n, stream);
     return run_contains(f, h_keys, n, h_out, stream);
   }
   bf_status s = ensure_pipeline(f);

@@ -119,7 +119,7 @@ struct BatchArgs {
   uint8_t* out;         // lookup results, same indexing as keys
   uint64_t acc0;
   uint32_t flags;
-  uint64_t prefetch_chunks;  // kHintPrefetchL2: lookahead in chunks (the grid's warp count); else 0
+  uint64_t prefetch_chunks;  // BF_HINT_PREFETCH_L2: lookahead in chunks (the grid's warp count); else 0
 };
 
 struct KernelEntry {

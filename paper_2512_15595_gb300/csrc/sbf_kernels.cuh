@@ -22,7 +22,7 @@
 
 namespace bloomgb {
 
-enum : uint32_t { kHintFilterEvictLast = 1u << 0, kHintKeysEvictNormal = 1u << 1, kHintPrefetchL2 = 1u << 2 };
+enum : uint32_t { kHintFilterEvictLast = 1u << 0, kHintKeysEvictNormal = 1u << 1 };
 
 // SALTS_: the salt set (0: SplitMix64 tables; 1: the Parquet split-block
 // multipliers, valid for B = 256, S = 32, K = 8 only)

@@ -261,6 +261,43 @@ def test_partitioned_add_bit_exact(torch, B, S, k):
                 f.close()
 
 
+def test_partitioned_add_from_host_keys(torch):
+    """Construction from pinned host keys read in place: passes over two
+    alternating workspaces with the record inserts on a second stream; bits as
+    the oracle's, launch counts as planned, and the workspace shared correctly
+    with a following device-key construction and a host-key lookup."""
+    geom = oracle.Geometry(num_blocks=(1 << 14) + 77, block_bits=256, word_bits=32, k=8, seed=5)
+    ins = synthkeys.insert_keys(150_001, seed=87)
+    more = synthkeys.insert_keys(40_000, seed=88)
+    q, is_mem = synthkeys.mixed_queries(150_001, 30_000, 60_001, seed_insert=87)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    want_first = ref.as_bytes().copy()
+    ref.add(more)
+    h_ins = torch.from_numpy(ins.view(np.int64)).pin_memory().numpy()
+    h_q = torch.from_numpy(q.view(np.int64)).pin_memory().numpy()
+    h_out = torch.empty(q.size, dtype=torch.uint8).pin_memory().numpy()
+    cases = [dict(slice_log2=16), dict(slice_log2=16, chunk_keys=4096 * 5 + 1), dict(slice_log2=16, cap_override=128),
+             dict(slice_log2=17, window_log2=17)]
+    for cfg in cases:
+        f = gpu_filter(geom, torch)
+        f.set_partition(mode=1, **cfg)
+        f.add_host(h_ins)
+        torch.cuda.synchronize()
+        nparts = -(-geom.nbytes // (1 << cfg["slice_log2"]))
+        per_launch = 1 << max(0, cfg.get("window_log2", 26) - cfg["slice_log2"])
+        pass_keys = min(cfg.get("chunk_keys", 1 << 32), -(-ins.size // 8))
+        passes = -(-ins.size // pass_keys)
+        assert f.last_launches() == passes * (1 + -(-nparts // per_launch)), (cfg, f.last_launches())
+        assert np.array_equal(words_np(f), want_first), cfg
+        f.add(dev_keys(torch, more))
+        f.contains_host(h_q, h_out)
+        torch.cuda.synchronize()
+        assert np.array_equal(words_np(f), ref.as_bytes()), cfg
+        assert np.array_equal(h_out, ref.contains(q)), cfg
+        f.close()
+
+
 def test_partitioned_add_skewed_keys(torch):
     # every key lands in one slice (duplicates): the slice buffer overflows and
     # the overflow records take the direct path
