@@ -371,6 +371,72 @@ bf_status ensure_ws(void** ws, uint64_t* ws_bytes, uint64_t bytes) {
 
 bf_status ensure_part_ws(bf_filter* f, uint64_t bytes) { return ensure_ws(&f->part_ws, &f->part_ws_bytes, bytes); }
 
+// Kernels and launch shapes of a slice-partitioned construction.
+struct PartLaunch {
+  const KernelEntry* pe = nullptr;  // slice partition
+  const KernelEntry* re = nullptr;  // record insert (the add layout)
+  size_t smem = 0;
+  uint32_t max_grid = 0;    // partition CTAs: SMs x min(resident, max_per_sm)
+  uint32_t per_launch = 1;  // slices per record-insert launch (one window)
+};
+
+bf_status prepare_part_launch(bf_filter* f, const PartPlan& pl, int max_per_sm, PartLaunch* L) {
+  const bf_layout& l = f->layout[BF_OP_ADD];
+  L->pe = find_op(3, f->p, 0, 0, 0);
+  L->re = find_op(2, f->p, l.cg, l.phi, l.kpt);
+  if (!L->pe || !L->re) return fail(BF_EUNSUPPORTED, "no partition kernels for this geometry");
+  L->smem = partition_smem_bytes(static_cast<int>(pl.nparts));
+  cudaError_t e =
+      cudaFuncSetAttribute(L->pe->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L->smem));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(partition)");
+  int sms = 0, per_sm = 0;
+  bf_status s = sm_count(f->device, &sms);
+  if (s != BF_OK) return s;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L->pe->fn, kPartThreads, L->smem)) != cudaSuccess)
+    return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(partition)");
+  L->max_grid = static_cast<uint32_t>(sms * std::max(1, std::min(per_sm, max_per_sm)));
+  const uint32_t slice_bytes_log2 = pl.shift + static_cast<uint32_t>(__builtin_ctz(f->p.block_bits / 8));
+  L->per_launch = f->part.window_log2 > slice_bytes_log2
+                      ? 1u << std::min<uint32_t>(f->part.window_log2 - slice_bytes_log2, 20)
+                      : 1u;
+  return BF_OK;
+}
+
+// Zero the slice counts and partition keys[0, cnt) into the slice buffers.
+bf_status launch_partition_pass(bf_filter* f, const PartLaunch& L, const PartPlan& pl, const uint64_t* keys,
+                                uint64_t cnt, uint64_t cap, unsigned long long* counts, uint64_t* records,
+                                cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, 8ull * pl.nparts, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  PartArgs pa{keys, cnt, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, f->p.num_blocks,
+              f->p.num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, f->words};
+  const uint64_t tiles = (cnt + kPartTile - 1) / kPartTile;
+  const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, L.max_grid));
+  void* pargs[] = {&pa};
+  if ((e = cudaLaunchKernel(L.pe->fn, dim3(grid), dim3(kPartThreads), pargs, L.smem, stream)) != cudaSuccess)
+    return cuda_fail(e, "launch partition kernel");
+  f->last_launches += 1;
+  return BF_OK;
+}
+
+// Insert the slice buffers' records, one window of slices per launch.
+bf_status launch_record_windows(bf_filter* f, const PartLaunch& L, const PartPlan& pl, const uint64_t* records,
+                                const unsigned long long* counts, uint64_t cap, cudaStream_t stream) {
+  const bf_layout& l = f->layout[BF_OP_ADD];
+  for (uint32_t plo = 0; plo < pl.nparts; plo += L.per_launch) {
+    const uint32_t phi = std::min(pl.nparts, plo + L.per_launch);
+    RecArgs ra{f->words, records, counts, plo, phi, cap, l.flags};
+    uint32_t rgrid = 0;
+    bf_status s = resolve_grid(L.re->fn, f->device, l.block_threads, l.grid_ctas, (phi - plo) * cap, l.kpt, &rgrid);
+    if (s != BF_OK) return s;
+    void* rargs[] = {&ra};
+    cudaError_t e = cudaLaunchKernel(L.re->fn, dim3(rgrid), dim3(l.block_threads), rargs, 0, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch record-insert kernel");
+    f->last_launches += 1;
+  }
+  return BF_OK;
+}
+
 bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
   const PartPlan pl = part_plan(f);
   const uint64_t pass = std::min<uint64_t>(n, f->part.chunk_keys);
@@ -378,47 +444,15 @@ bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cud
   const uint64_t counts_bytes = 8ull * static_cast<uint32_t>(kMaxParts);
   bf_status s = ensure_part_ws(f, counts_bytes + static_cast<uint64_t>(pl.nparts) * cap_max * 8);
   if (s != BF_OK) return launch_sbf(f, BF_OP_ADD, keys, n, nullptr, stream);  // no memory: direct kernel
-  const KernelEntry* pe = find_op(3, f->p, 0, 0, 0);
-  const bf_layout& l = f->layout[BF_OP_ADD];
-  const KernelEntry* re = find_op(2, f->p, l.cg, l.phi, l.kpt);
-  if (!pe || !re) return fail(BF_EUNSUPPORTED, "no partition kernels for this geometry");
+  PartLaunch L;
+  if ((s = prepare_part_launch(f, pl, 1 << 30, &L)) != BF_OK) return s;
   unsigned long long* counts = static_cast<unsigned long long*>(f->part_ws);
   uint64_t* records = reinterpret_cast<uint64_t*>(static_cast<char*>(f->part_ws) + counts_bytes);
-  const size_t smem = partition_smem_bytes(static_cast<int>(pl.nparts));
-  cudaError_t e = cudaFuncSetAttribute(pe->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(partition)");
-  int sms = 0, per_sm = 0;
-  if ((s = sm_count(f->device, &sms)) != BF_OK) return s;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pe->fn, kPartThreads, smem);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(partition)");
-  per_sm = std::max(per_sm, 1);
   for (uint64_t lo = 0; lo < n; lo += pass) {
     const uint64_t cnt = std::min(pass, n - lo);
     const uint64_t cap = part_cap(f, pl, cnt);
-    if ((e = cudaMemsetAsync(counts, 0, 8ull * pl.nparts, stream)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    PartArgs pa{keys + lo, cnt, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, f->p.num_blocks,
-                f->p.num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, f->words};
-    const uint64_t tiles = (cnt + kPartTile - 1) / kPartTile;
-    const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, static_cast<uint64_t>(sms) * per_sm));
-    void* pargs[] = {&pa};
-    if ((e = cudaLaunchKernel(pe->fn, dim3(grid), dim3(kPartThreads), pargs, smem, stream)) != cudaSuccess)
-      return cuda_fail(e, "launch partition kernel");
-    f->last_launches += 1;
-    const uint32_t slice_bytes_log2 = pl.shift + static_cast<uint32_t>(__builtin_ctz(f->p.block_bits / 8));
-    const uint32_t per_launch =
-        f->part.window_log2 > slice_bytes_log2 ? 1u << std::min<uint32_t>(f->part.window_log2 - slice_bytes_log2, 20) : 1u;
-    for (uint32_t plo = 0; plo < pl.nparts; plo += per_launch) {
-      const uint32_t phi = std::min(pl.nparts, plo + per_launch);
-      RecArgs ra{f->words, records, counts, plo, phi, cap, l.flags};
-      uint32_t rgrid = 0;
-      if ((s = resolve_grid(re->fn, f->device, l.block_threads, l.grid_ctas, (phi - plo) * cap, l.kpt, &rgrid)) !=
-          BF_OK)
-        return s;
-      void* rargs[] = {&ra};
-      if ((e = cudaLaunchKernel(re->fn, dim3(rgrid), dim3(l.block_threads), rargs, 0, stream)) != cudaSuccess)
-        return cuda_fail(e, "launch record-insert kernel");
-      f->last_launches += 1;
-    }
+    if ((s = launch_partition_pass(f, L, pl, keys + lo, cnt, cap, counts, records, stream)) != BF_OK) return s;
+    if ((s = launch_record_windows(f, L, pl, records, counts, cap, stream)) != BF_OK) return s;
   }
   return BF_OK;
 }
@@ -449,23 +483,9 @@ bf_status launch_partitioned_host(bf_filter* f, const uint64_t* keys, uint64_t n
     if (!f->ev_rec[i] && (e = cudaEventCreateWithFlags(&f->ev_rec[i], cudaEventDisableTiming)) != cudaSuccess)
       return cuda_fail(e, "cudaEventCreate");
   }
-  const KernelEntry* pe = find_op(3, f->p, 0, 0, 0);
-  const bf_layout& l = f->layout[BF_OP_ADD];
-  const KernelEntry* re = find_op(2, f->p, l.cg, l.phi, l.kpt);
-  if (!pe || !re) return fail(BF_EUNSUPPORTED, "no partition kernels for this geometry");
-  const size_t smem = partition_smem_bytes(static_cast<int>(pl.nparts));
-  if ((e = cudaFuncSetAttribute(pe->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
-      cudaSuccess)
-    return cuda_fail(e, "cudaFuncSetAttribute(partition)");
-  int sms = 0, per_sm = 0;
-  bf_status s = sm_count(f->device, &sms);
+  PartLaunch L;
+  bf_status s = prepare_part_launch(f, pl, kHostPartCtas, &L);
   if (s != BF_OK) return s;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pe->fn, kPartThreads, smem)) != cudaSuccess)
-    return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(partition)");
-  per_sm = std::max(1, std::min(per_sm, kHostPartCtas));
-  const uint32_t slice_bytes_log2 = pl.shift + static_cast<uint32_t>(__builtin_ctz(f->p.block_bits / 8));
-  const uint32_t per_launch =
-      f->part.window_log2 > slice_bytes_log2 ? 1u << std::min<uint32_t>(f->part.window_log2 - slice_bytes_log2, 20) : 1u;
   bool used[2] = {false, false};
   uint64_t i = 0;
   for (uint64_t lo = 0; lo < n; lo += pass, ++i) {
@@ -477,30 +497,11 @@ bf_status launch_partitioned_host(bf_filter* f, const uint64_t* keys, uint64_t n
     uint64_t* records = reinterpret_cast<uint64_t*>(base + counts_bytes);
     if (used[w] && (e = cudaStreamWaitEvent(stream, f->ev_rec[w], 0)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamWaitEvent");
-    if ((e = cudaMemsetAsync(counts, 0, 8ull * pl.nparts, stream)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    PartArgs pa{keys + lo, cnt, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, f->p.num_blocks,
-                f->p.num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, f->words};
-    const uint64_t tiles = (cnt + kPartTile - 1) / kPartTile;
-    const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, static_cast<uint64_t>(sms) * per_sm));
-    void* pargs[] = {&pa};
-    if ((e = cudaLaunchKernel(pe->fn, dim3(grid), dim3(kPartThreads), pargs, smem, stream)) != cudaSuccess)
-      return cuda_fail(e, "launch partition kernel");
-    f->last_launches += 1;
+    if ((s = launch_partition_pass(f, L, pl, keys + lo, cnt, cap, counts, records, stream)) != BF_OK) return s;
     if ((e = cudaEventRecord(f->ev_part[w], stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     if ((e = cudaStreamWaitEvent(f->rec_stream, f->ev_part[w], 0)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamWaitEvent");
-    for (uint32_t plo = 0; plo < pl.nparts; plo += per_launch) {
-      const uint32_t phi = std::min(pl.nparts, plo + per_launch);
-      RecArgs ra{f->words, records, counts, plo, phi, cap, l.flags};
-      uint32_t rgrid = 0;
-      if ((s = resolve_grid(re->fn, f->device, l.block_threads, l.grid_ctas, (phi - plo) * cap, l.kpt, &rgrid)) !=
-          BF_OK)
-        return s;
-      void* rargs[] = {&ra};
-      if ((e = cudaLaunchKernel(re->fn, dim3(rgrid), dim3(l.block_threads), rargs, 0, f->rec_stream)) != cudaSuccess)
-        return cuda_fail(e, "launch record-insert kernel");
-      f->last_launches += 1;
-    }
+    if ((s = launch_record_windows(f, L, pl, records, counts, cap, f->rec_stream)) != BF_OK) return s;
     if ((e = cudaEventRecord(f->ev_rec[w], f->rec_stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     used[w] = true;
   }
