@@ -1160,6 +1160,8 @@ def main():
     ap.add_argument("--learned-members", type=int, default=1 << 26,
                     help="member keys of the learned workload (queries: as many non-members again)")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--n-lookup", type=int, default=0,
+                    help="filter workloads: lookups per step instead of the workload's (profiling-sized runs)")
     ap.add_argument("--batch-filters", type=int, default=4096, help="batched workload: number of filters")
     ap.add_argument("--batch-keys", type=int, default=1 << 28, help="batched workload: keys (and queries)")
     ap.add_argument("--no-per-filter", action="store_true",
@@ -1198,6 +1200,9 @@ def main():
             run_batched(args)
         return
     w = dict(WORKLOADS[args.workload])
+    if args.n_lookup:
+        w["n_lookup"] = args.n_lookup
+        w["desc"] = w["desc"] + f"; reduced to {args.n_lookup} lookups per step"
     if args.salts == "parquet":
         if (w["block_bits"], w["word_bits"], w["k"]) != (256, 32, 8):
             ap.error("the Parquet salt set exists for 256-bit blocks, S = 32, K = 8 only")
