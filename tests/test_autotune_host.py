@@ -80,3 +80,79 @@ def test_bench_batch_geometries_are_valid():
     for B, S in bench.BATCH_GEOMETRIES:
         assert _lib.bf_params_check(_lib.bf_params(1000, B, S, 8, 0, 0, 0, 0)) == _lib.BF_OK, (B, S)
     assert (256, 32) in bench.BATCH_GEOMETRIES
+
+
+class _FakeEvent:
+    """Stands in for torch.cuda.Event: elapsed time from a shared fake clock."""
+    clock = [0.0]
+
+    def __init__(self, enable_timing=True):
+        self.t = None
+
+    def record(self, stream=None):
+        self.t = _FakeEvent.clock[0]
+
+    def synchronize(self):
+        pass
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+class _FakeTorch:
+    class cuda:
+        Event = _FakeEvent
+
+        @staticmethod
+        def current_stream():
+            return None
+
+
+class _FakeBatch:
+    """A batch whose calls advance the fake clock by a cost that depends on
+    its layout, so the sweep's choice is known in advance."""
+
+    def __init__(self, cost):
+        self.params = type("P", (), {"block_bits": 256, "word_bits": 32, "k": 8})()
+        self.total_keys = 1000
+        self.nfilters = 3
+        self.cost = cost
+        self.lay = {}
+
+    def set_layout(self, op, **lay):
+        self.lay[op] = dict(lay)
+
+    def _run(self, op):
+        _FakeEvent.clock[0] += self.cost(op, self.lay[op])
+
+    def add(self, keys):
+        self._run(BF_OP_ADD)
+
+    def contains(self, keys, out=None):
+        self._run(BF_OP_CONTAINS)
+
+
+def test_sweep_batch_picks_the_fastest_layout_per_operation():
+    def cost(op, lay):
+        base = 5.0 if op == BF_OP_ADD else 3.0
+        if op == BF_OP_ADD and (lay["cg"], lay["phi"], lay["kpt"], lay["flags"], lay["grid_ctas"]) == (4, 2, 4, 4, 304):
+            return 1.0
+        if op == BF_OP_CONTAINS and (lay["cg"], lay["phi"], lay["kpt"], lay["grid_ctas"]) == (1, 8, 2, 0):
+            return 0.5 + 0.1 * lay["flags"]
+        return base + 0.01 * lay["cg"]
+
+    b = _FakeBatch(cost)
+    res = autotune.sweep_batch(_FakeTorch, b, None, None, None, kpts=(1, 2, 4), reps=3,
+                               flag_sets=(0, 4), grids=(0, 304))
+    assert res["key"] == "batch_B256_S32_K8"
+    e = res["entry"]
+    assert e["add"]["layout"] == dict(cg=4, phi=2, kpt=4, flags=4, grid_ctas=304)
+    assert e["contains"]["layout"] == dict(cg=1, phi=8, kpt=2, flags=0, grid_ctas=0)
+    assert e["add"]["ms"] == pytest.approx(1.0) and e["contains"]["ms"] == pytest.approx(0.5)
+    assert e["step_ms"] == pytest.approx(1.5)
+    assert e["add"]["gkeys_s"] == pytest.approx(1000 / 1e-3 / 1e9)
+    # every (cg, phi) of a 256/32 block x 3 kpt x 2 flag sets x 2 grids, per operation
+    from paper_2512_15595_gb300 import valid_layouts
+    assert len(res["rows"]) == 2 * len(valid_layouts(256, 32)) * 3 * 2 * 2
+    # the batch is left at the best layouts
+    assert b.lay[BF_OP_ADD] == e["add"]["layout"] and b.lay[BF_OP_CONTAINS] == e["contains"]["layout"]
