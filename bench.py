@@ -770,7 +770,7 @@ def run_frontier(args):
     One JSON line per configuration, then a summary line."""
     import torch
     import synthkeys
-    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS, Filter, valid_layouts
+    from paper_2512_15595_gb300 import BF_OP_ADD, BF_OP_CONTAINS, Filter
     from paper_2512_15595_gb300.autotune import time_op
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)

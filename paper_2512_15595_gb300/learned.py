@@ -8,7 +8,6 @@ the library's kernels; this module allocates tensors and passes pointers.
 """
 from __future__ import annotations
 
-import ctypes
 import math
 
 import numpy as np

@@ -175,7 +175,7 @@ def test_batch_cuda_graph_replay(torch):
 
 
 def test_empty_batch_and_errors(torch):
-    from paper_2512_15595_gb300 import Batch, BloomError, _lib
+    from paper_2512_15595_gb300 import Batch, BloomError
     b = Batch([], 256, 32, 8)
     b.add(torch.zeros(1, dtype=torch.int64, device="cuda"))
     b.close()

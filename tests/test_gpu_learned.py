@@ -15,7 +15,6 @@
   the combined lookup (score >= tau or backup filter) element by element;
   no member is ever rejected.
 """
-import ctypes
 
 import numpy as np
 import pytest
