@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "bloomgb.h"
+#include "key_ring.h"
 #include "registry.h"
 
 using namespace bloomgb;
@@ -93,7 +94,7 @@ struct bf_server {
   // key / result arena: a ring of `cap` key slots
   uint64_t* d_keys = nullptr;
   uint8_t* d_out = nullptr;
-  uint64_t cap = 0, head = 0, tail = 0, used = 0;
+  KeyRing ring;
   Launch launches[kMaxInflight];
   std::deque<int> inflight;  // launch slots in submission order
   // requests
@@ -112,58 +113,6 @@ struct bf_server {
 
 namespace {
 
-// Take space for n keys from the ring: one contiguous run, wrapping to slot
-// 0 when the end of the ring is too short (the skipped end is consumed by
-// this allocation until its launch is released).  Occupied slots are the run
-// from `tail` to `head` (mod cap).  Returns false if there is no room now;
-// else the offset, and the slots consumed in *consumed.
-bool ring_take(bf_server* s, uint64_t n, uint64_t* off, uint64_t* consumed) {
-  if (n > s->cap) return false;
-  if (n == 0) {
-    *off = s->head < s->cap ? s->head : 0;
-    *consumed = 0;
-    return true;
-  }
-  if (s->used == 0) s->head = s->tail = 0;
-  if (s->used >= s->cap) return false;
-  if (s->used == 0 || s->head > s->tail) {
-    // free: [head, cap) and [0, tail)
-    if (s->cap - s->head >= n) {
-      *off = s->head;
-      *consumed = n;
-      s->head += n;
-      s->used += n;
-      return true;
-    }
-    if (s->tail >= n) {
-      *consumed = (s->cap - s->head) + n;
-      s->used += *consumed;
-      *off = 0;
-      s->head = n;
-      return true;
-    }
-    return false;
-  }
-  // head < tail: free is [head, tail)
-  if (s->tail - s->head >= n) {
-    *off = s->head;
-    *consumed = n;
-    s->head += n;
-    s->used += n;
-    return true;
-  }
-  return false;
-}
-
-// Release a launch's slots (launches complete in submission order); a launch
-// that consumed nothing (only empty requests) releases nothing.
-void ring_release(bf_server* s, uint64_t consumed, uint64_t end) {
-  if (consumed == 0) return;
-  s->used -= std::min(s->used, consumed);
-  s->tail = end;
-  if (s->used == 0) s->head = s->tail = 0;
-}
-
 void complete_front(bf_server* s) {
   const int slot = s->inflight.front();
   Launch& L = s->launches[slot];
@@ -178,7 +127,7 @@ void complete_front(bf_server* s) {
   }
   s->last_done = t;
   s->launches_done += 1;
-  ring_release(s, L.arena_used, L.arena_end);
+  s->ring.release(L.arena_used, L.arena_end);
   L.reqs.clear();
   L.busy = false;
   s->inflight.pop_front();
@@ -250,13 +199,13 @@ void worker_loop(bf_server* s) {
         while (!s->pending.empty() && L.reqs.size() < s->max_reqs) {
           Request* r = s->pending.front();
           uint64_t off = 0, consumed = 0;
-          if (!ring_take(s, r->n, &off, &consumed)) break;
+          if (!s->ring.take(r->n, &off, &consumed)) break;
           r->arena_off = off;
           L.arena_used += consumed;
           L.reqs.push_back(r);
           s->pending.pop_front();
         }
-        L.arena_end = s->head;
+        L.arena_end = s->ring.head;
       }
       if (!L.reqs.empty()) {
         L.busy = true;
@@ -307,7 +256,7 @@ bf_status bf_server_create(const bf_params* params, const bf_batch_filter* filte
   if (!s) return BF_ENOMEM;
   s->p = p;
   s->kernel = k;
-  s->cap = arena_keys;
+  s->ring.cap = arena_keys;
   s->max_reqs = max_requests_per_launch;
   for (uint32_t i = 0; i < nfilters; ++i) s->filters.push_back(BatchFilter{filters[i].d_words, filters[i].num_blocks, 0, 0});
   cudaError_t e = cudaGetDevice(&s->device);
@@ -368,7 +317,7 @@ bf_status bf_server_destroy(bf_server* s) {
 
 bf_status bf_server_submit(bf_server* s, uint32_t filter, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
                            uint64_t* ticket) {
-  if (!s || !ticket || filter >= s->filters.size() || (n && (!h_keys || !h_out)) || n > s->cap) return BF_EINVAL;
+  if (!s || !ticket || filter >= s->filters.size() || (n && (!h_keys || !h_out)) || n > s->ring.cap) return BF_EINVAL;
   Request* r = new (std::nothrow) Request();
   if (!r) return BF_ENOMEM;
   r->filter = filter;
@@ -435,7 +384,7 @@ bf_status bf_server_run_poisson(bf_server* s, double rate_per_s, double duration
                                 uint64_t max_keys, const uint64_t* h_key_pool, uint64_t pool_keys, uint8_t* h_out_pool,
                                 uint64_t seed, bf_server_stats* out) {
   if (!s || !out || rate_per_s <= 0 || duration_s <= 0 || min_keys == 0 || max_keys < min_keys || !h_key_pool ||
-      !h_out_pool || pool_keys < max_keys || max_keys > s->cap)
+      !h_out_pool || pool_keys < max_keys || max_keys > s->ring.cap)
     return BF_EINVAL;
   bf_server_stats dummy;
   bf_server_get_stats(s, 1, &dummy);
