@@ -78,6 +78,7 @@ def lib():
             "orc_add_block_range": (i32, [P, vp, u64, u64, vp, u64]),
             "orc_contains": (i32, [P, vp, vp, u64, vp]),
             "orc_contains_block_range": (i32, [P, vp, u64, u64, vp, u64, vp]),
+            "orc_key_blocks": (i32, [P, vp, u64, vp, vp]),
             "orc_hash_keys": (None, [vp, u64, u64, vp]),
             "orc_block_indices": (None, [vp, u64, u64, u64, vp]),
         }
@@ -232,6 +233,26 @@ def add_block_range(geom: Geometry, block_lo: int, block_hi: int, keys, words=No
     rc = lib().orc_add_block_range(ctypes.byref(p), _ptr(words), block_lo, block_hi, _ptr(k), k.size)
     assert rc == 0
     return words
+
+
+def add_sparse(geom: Geometry, keys) -> tuple[np.ndarray, np.ndarray]:
+    """Construction of a filter too large to hold, for few keys: the sorted
+    indices of the blocks the keys touch and those blocks' words
+    ([blocks, s]), every other block being zero.  Each key's block image
+    comes from the oracle (its pattern in an empty block); the images of keys
+    sharing a block are ORed (Sec. II-A: construction ORs every key's pattern
+    into its block)."""
+    p = geom.cparams()
+    k = _keys(keys)
+    blocks = np.empty(k.size, dtype=np.uint64)
+    images = np.empty((k.size, geom.s), dtype=geom.word_dtype)
+    rc = lib().orc_key_blocks(ctypes.byref(p), _ptr(k), k.size, _ptr(blocks), _ptr(images))
+    assert rc == 0
+    order = np.argsort(blocks, kind="stable")
+    blocks, images = blocks[order], images[order]
+    uniq, first = np.unique(blocks, return_index=True)
+    words = np.bitwise_or.reduceat(images, first, axis=0) if k.size else images
+    return uniq, words
 
 
 def contains_block_range(geom: Geometry, words: np.ndarray, block_lo: int, block_hi: int, keys) -> np.ndarray:

@@ -405,6 +405,29 @@ int orc_contains_block_range(const orc_params* p, const void* words, uint64_t bl
     return 0;
 }
 
+/* Each key's own contribution: its block index in out_block[i] and the s
+   words of that block with only this key's pattern set, in
+   out_words[i*s .. i*s+s-1] (S-bit words).  Construction is the OR of these
+   images into their blocks; used to check very sparse filters block by block
+   without a full-size array. */
+int orc_key_blocks(const orc_params* p, const uint64_t* keys, uint64_t n, uint64_t* out_block, void* out_words)
+{
+    if (orc_check(p) != 0) return -1;
+    uint32_t s = p->block_bits / p->word_bits;
+    uint32_t z = effective_groups(p);
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t h = orc_key_hash(keys[i], p->seed);
+        out_block[i] = orc_block_index(h, p->num_blocks);
+        for (uint32_t w = 0; w < s; ++w) {
+            if (p->word_bits == 32) ((uint32_t*)out_words)[i * s + w] = 0;
+            else ((uint64_t*)out_words)[i * s + w] = 0;
+        }
+        for (uint32_t q = 0; q < z; ++q)
+            word_or(out_words, p->word_bits, i * s + orc_group_word(p, h, q), orc_group_pattern(p, h, q));
+    }
+    return 0;
+}
+
 /* per-key base hash and block index, for statistics tests */
 void orc_hash_keys(const uint64_t* keys, uint64_t n, uint64_t seed, uint64_t* out)
 {

@@ -128,3 +128,25 @@ def test_block_index_rule():
     for b in (2**32 + 1, 2**40 + 12345):
         for h in hs:
             assert oracle.block_index(h, b) == (h * b) >> 64
+
+
+@pytest.mark.parametrize("B,S,k,z", [(256, 32, 8, 0), (512, 64, 16, 0), (64, 32, 4, 0), (1024, 64, 16, 2),
+                                     (256, 64, 8, 2)])
+def test_sparse_construction_equals_dense(B, S, k, z):
+    """add_sparse (per-key block images ORed per block) against the dense
+    construction: the same words in every touched block, zero elsewhere,
+    with duplicates and shared blocks present."""
+    geom = oracle.Geometry(num_blocks=97, block_bits=B, word_bits=S, k=k, seed=11, groups=z)
+    keys = synthkeys.splitmix64(31, 0, 400)
+    keys = np.concatenate([keys, keys[:50]])
+    blocks, words = oracle.add_sparse(geom, keys)
+    f = oracle.SBF(geom)
+    f.add(keys)
+    dense = f.as_bytes().view(geom.word_dtype).reshape(geom.num_blocks, geom.s)
+    assert np.array_equal(np.unique(oracle.block_indices(keys, geom.num_blocks, geom.seed)), blocks)
+    assert np.array_equal(dense[blocks.astype(np.int64)], words)
+    rest = np.ones(geom.num_blocks, dtype=bool)
+    rest[blocks.astype(np.int64)] = False
+    assert not dense[rest].any()
+    b0, w0 = oracle.add_sparse(geom, keys[:0])
+    assert b0.size == 0 and w0.shape == (0, geom.s)
