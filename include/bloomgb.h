@@ -229,7 +229,14 @@ bf_status bf_set_l2_persist(bf_filter* f, bf_stream_t stream, float hit_ratio);
    chunk_keys / lookup_chunk_keys: keys per pass (lookup default 2^28, so that
    the pass's result bitmap stays in L2).  cap_override: slots per slice
    buffer (0 = computed from the pass size; small values force the overflow
-   path, for tests). */
+   path, for tests).
+   passes: 0 or 1 = each pass of at most chunk_keys keys is partitioned, then
+   its records inserted; >= 2 = the keys are split into at least this many
+   passes over two alternating workspaces (twice the workspace of one such
+   pass) and the phases overlap: the record inserts of pass i run on an
+   internal stream while the partition of pass i + 1 runs on the caller's.
+   part_ctas: partition CTAs per SM (0 = as many as fit; with passes >= 2 a
+   smaller value leaves room for the record inserts beside the partition). */
 typedef enum { BF_PART_OFF = 0, BF_PART_ON = 1, BF_PART_AUTO = 2 } bf_part_mode;
 typedef struct {
     uint32_t mode;               /* construction; default BF_PART_AUTO */
@@ -239,9 +246,24 @@ typedef struct {
     uint32_t window_log2;        /* 16..36; default 26 (64 MiB) */
     uint32_t lookup_mode;        /* default BF_PART_AUTO */
     uint64_t lookup_chunk_keys;  /* 4096..2^32; default 2^28 */
+    uint32_t passes;             /* 0..64; default 0 (no overlap) */
+    uint32_t part_ctas;          /* 0..8; default 0 */
 } bf_partition;
 bf_status bf_set_partition(bf_filter* f, const bf_partition* cfg);
 bf_status bf_get_partition(const bf_filter* f, bf_partition* out);
+
+/* Index checks of the slice-partitioned kernels.  Those kernels keep every
+   index they derive from data inside its array (clamped, or checked before
+   use); a failed check skips the access and sets a bit in a device status
+   word of the filter -- 2: a record's block index beyond the filter (record
+   insert, record probe), 8: a sorted record outside the slices (partition),
+   16: a slice-buffer slot outside the buffers (partition) -- so no index can
+   leave its buffer.  None of them fails when the kernels are correct; a
+   nonzero value means the result of some call is incomplete.
+   bf_device_status waits for `stream` (and the filter's internal stream),
+   returns the bits accumulated since the last call in *codes (0 = none) and
+   clears them. */
+bf_status bf_device_status(bf_filter* f, bf_stream_t stream, uint32_t* codes);
 
 /* Kernel launches made by the last bf_add / bf_contains / bf_add_host /
    bf_contains_host call on this filter (1 for a direct call; per pass of a
@@ -359,6 +381,12 @@ bf_status bf_server_run_poisson(bf_server* s, double rate_per_s, double duration
    Errors are reported by the status only (bf_last_error is not updated). */
 bf_status bf_add_noalloc(const bf_params* params, void* d_words, const uint64_t* d_keys, uint64_t n,
                          uint64_t* max_keys, bf_stream_t stream);
+
+/* The index-check bits (as for bf_device_status) that bf_add_noalloc calls on
+   the current device have accumulated in the shared array since the last
+   bf_noalloc_status; clears them.  A synchronous copy: call it once those
+   calls have completed. */
+bf_status bf_noalloc_status(uint32_t* codes);
 
 /* ---------------------------------------------------------------------------
    Learned prefilter (an extension beside the paper's filters; the paper has no

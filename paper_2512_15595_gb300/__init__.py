@@ -108,19 +108,26 @@ class Filter:
 
     def set_partition(self, mode: int | None = None, slice_log2: int | None = None, chunk_keys: int | None = None,
                       cap_override: int | None = None, window_log2: int | None = None,
-                      lookup_mode: int | None = None, lookup_chunk_keys: int | None = None) -> None:
+                      lookup_mode: int | None = None, lookup_chunk_keys: int | None = None,
+                      passes: int | None = None, part_ctas: int | None = None) -> None:
         """Slice-partitioned construction / lookup settings (modes: 0 off, 1 on,
         2 auto); arguments left as None keep their current value."""
         cur = _lib.bf_get_partition(self.handle)
         for name, val in (("mode", mode), ("slice_log2", slice_log2), ("chunk_keys", chunk_keys),
                           ("cap_override", cap_override), ("window_log2", window_log2),
-                          ("lookup_mode", lookup_mode), ("lookup_chunk_keys", lookup_chunk_keys)):
+                          ("lookup_mode", lookup_mode), ("lookup_chunk_keys", lookup_chunk_keys),
+                          ("passes", passes), ("part_ctas", part_ctas)):
             if val is not None:
                 setattr(cur, name, val)
         _lib.bf_set_partition(self.handle, cur)
 
     def partition(self) -> dict:
         return _lib.bf_get_partition(self.handle).as_dict()
+
+    def device_status(self, stream=None) -> int:
+        """Bits of failed index checks in the slice-partitioned kernels since
+        the last call (0 = none; waits for the stream)."""
+        return _lib.bf_device_status(self.handle, stream)
 
     def last_launches(self) -> int:
         return _lib.bf_last_launches(self.handle)

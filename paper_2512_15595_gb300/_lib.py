@@ -26,7 +26,7 @@ EXPORTED = (
     "bf_params_check", "bf_layout_check", "bf_create", "bf_destroy", "bf_clear", "bf_add",
     "bf_contains", "bf_add_host", "bf_contains_host", "bf_set_staging", "bf_words",
     "bf_get_params", "bf_set_layout", "bf_get_layout", "bf_set_l2_persist", "bf_gups",
-    "bf_set_partition", "bf_get_partition", "bf_last_launches", "bf_add_noalloc", "bf_batch_create",
+    "bf_set_partition", "bf_get_partition", "bf_last_launches", "bf_add_noalloc", "bf_noalloc_status", "bf_device_status", "bf_batch_create",
     "bf_batch_destroy", "bf_batch_set_layout", "bf_batch_get_layout", "bf_batch_add", "bf_batch_contains",
     "bf_batch_info", "bf_server_create", "bf_server_destroy", "bf_server_submit", "bf_server_wait",
     "bf_server_get_stats", "bf_server_run_poisson", "bf_mlp_workspace_bytes", "bf_mlp_grad", "bf_mlp_adam",
@@ -64,7 +64,8 @@ class bf_partition(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("slice_log2", ctypes.c_uint32),
                 ("chunk_keys", ctypes.c_uint64), ("cap_override", ctypes.c_uint64),
                 ("window_log2", ctypes.c_uint32), ("lookup_mode", ctypes.c_uint32),
-                ("lookup_chunk_keys", ctypes.c_uint64)]
+                ("lookup_chunk_keys", ctypes.c_uint64), ("passes", ctypes.c_uint32),
+                ("part_ctas", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -130,6 +131,8 @@ def lib():
         "bf_set_l2_persist": (i32, [vp, vp, ctypes.c_float]),
         "bf_gups": (i32, [i32, vp, u64, u32, vp, u64, vp, LY, vp]),
         "bf_set_partition": (i32, [vp, ctypes.POINTER(bf_partition)]),
+        "bf_device_status": (i32, [vp, vp, ctypes.POINTER(ctypes.c_uint32)]),
+        "bf_noalloc_status": (i32, [ctypes.POINTER(ctypes.c_uint32)]),
         "bf_get_partition": (i32, [vp, ctypes.POINTER(bf_partition)]),
         "bf_last_launches": (i32, [vp, ctypes.POINTER(u32)]),
         "bf_add_noalloc": (i32, [P, vp, vp, u64, ctypes.POINTER(u64), vp]),
@@ -269,6 +272,14 @@ def bf_gups(mode: int, d_table: int, table_bytes: int, unit_bytes: int, d_keys: 
 
 def bf_set_partition(f: int, cfg: bf_partition) -> None:
     _check(lib().bf_set_partition(f, ctypes.byref(cfg)), "bf_set_partition")
+
+
+def bf_device_status(f: int, stream=None) -> int:
+    """Index-check bits of the filter's slice-partitioned kernels since the
+    last call (0 = none); waits for the stream."""
+    v = ctypes.c_uint32()
+    _check(lib().bf_device_status(f, _stream(stream), ctypes.byref(v)), "bf_device_status")
+    return v.value
 
 
 def bf_get_partition(f: int) -> bf_partition:

@@ -193,13 +193,14 @@ struct bf_filter {
   int host_access = 0;  // 0: kernels read device-accessible host buffers directly; 1: always stage
   bool l2_window = false;
   // L2-blocked construction
-  bf_partition part{BF_PART_AUTO, 24, 1ull << 32, 0, 26, BF_PART_AUTO, 1ull << 28};
+  bf_partition part{BF_PART_AUTO, 24, 1ull << 32, 0, 26, BF_PART_AUTO, 1ull << 28, 0, 0};
   void* part_ws = nullptr;
   uint64_t part_ws_bytes = 0;
   void* look_ws = nullptr;  // slice-partitioned lookup workspace
   uint64_t look_ws_bytes = 0;
   uint64_t l2_bytes = 0;
   uint32_t last_launches = 0;
+  uint32_t* status = nullptr;  // device word: kStatus* bits of failed index checks
 };
 
 namespace {
@@ -371,6 +372,23 @@ bf_status ensure_ws(void** ws, uint64_t* ws_bytes, uint64_t bytes) {
 
 bf_status ensure_part_ws(bf_filter* f, uint64_t bytes) { return ensure_ws(&f->part_ws, &f->part_ws_bytes, bytes); }
 
+// the status word the slice-partitioned kernels report failed index checks in
+bf_status ensure_status(bf_filter* f) {
+  if (f->status) return BF_OK;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BF_ENOMEM, "status word allocation failed");
+  }
+  if ((e = cudaMemset(p, 0, 256)) != cudaSuccess) {
+    cudaFree(p);
+    return cuda_fail(e, "cudaMemset");
+  }
+  f->status = static_cast<uint32_t*>(p);
+  return BF_OK;
+}
+
 // Kernels and launch shapes of a slice-partitioned construction.
 struct PartLaunch {
   const KernelEntry* pe = nullptr;  // slice partition
@@ -381,6 +399,8 @@ struct PartLaunch {
 };
 
 bf_status prepare_part_launch(bf_filter* f, const PartPlan& pl, int max_per_sm, PartLaunch* L) {
+  bf_status st = ensure_status(f);
+  if (st != BF_OK) return st;
   const bf_layout& l = f->layout[BF_OP_ADD];
   L->pe = find_op(3, f->p, 0, 0, 0);
   L->re = find_op(2, f->p, l.cg, l.phi, l.kpt);
@@ -409,8 +429,9 @@ bf_status launch_partition_pass(bf_filter* f, const PartLaunch& L, const PartPla
   cudaError_t e = cudaMemsetAsync(counts, 0, 8ull * pl.nparts, stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   PartArgs pa{keys, cnt, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, f->p.num_blocks,
-              f->p.num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, f->words};
-  const uint64_t tiles = (cnt + kPartTile - 1) / kPartTile;
+              f->p.num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, f->words,
+              nullptr, nullptr, f->status};
+  const uint64_t tiles = (cnt + part_tile(false) - 1) / part_tile(false);
   const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, L.max_grid));
   void* pargs[] = {&pa};
   if ((e = cudaLaunchKernel(L.pe->fn, dim3(grid), dim3(kPartThreads), pargs, L.smem, stream)) != cudaSuccess)
@@ -425,7 +446,7 @@ bf_status launch_record_windows(bf_filter* f, const PartLaunch& L, const PartPla
   const bf_layout& l = f->layout[BF_OP_ADD];
   for (uint32_t plo = 0; plo < pl.nparts; plo += L.per_launch) {
     const uint32_t phi = std::min(pl.nparts, plo + L.per_launch);
-    RecArgs ra{f->words, records, counts, plo, phi, cap, l.flags};
+    RecArgs ra{f->words, records, counts, plo, phi, cap, l.flags, f->p.num_blocks, f->status};
     uint32_t rgrid = 0;
     bf_status s = resolve_grid(L.re->fn, f->device, l.block_threads, l.grid_ctas, (phi - plo) * cap, l.kpt, &rgrid);
     if (s != BF_OK) return s;
@@ -437,7 +458,8 @@ bf_status launch_record_windows(bf_filter* f, const PartLaunch& L, const PartPla
   return BF_OK;
 }
 
-bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
+// One partition pass over all keys per chunk_keys, then its record inserts.
+bf_status launch_partitioned_serial(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
   const PartPlan pl = part_plan(f);
   const uint64_t pass = std::min<uint64_t>(n, f->part.chunk_keys);
   const uint64_t cap_max = part_cap(f, pl, pass);
@@ -445,7 +467,9 @@ bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cud
   bf_status s = ensure_part_ws(f, counts_bytes + static_cast<uint64_t>(pl.nparts) * cap_max * 8);
   if (s != BF_OK) return launch_sbf(f, BF_OP_ADD, keys, n, nullptr, stream);  // no memory: direct kernel
   PartLaunch L;
-  if ((s = prepare_part_launch(f, pl, 1 << 30, &L)) != BF_OK) return s;
+  if ((s = prepare_part_launch(f, pl, f->part.part_ctas ? static_cast<int>(f->part.part_ctas) : 1 << 30, &L)) !=
+      BF_OK)
+    return s;
   unsigned long long* counts = static_cast<unsigned long long*>(f->part_ws);
   uint64_t* records = reinterpret_cast<uint64_t*>(static_cast<char*>(f->part_ws) + counts_bytes);
   for (uint64_t lo = 0; lo < n; lo += pass) {
@@ -457,23 +481,22 @@ bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cud
   return BF_OK;
 }
 
-// Construction from keys the kernels read in host memory: the slice
-// partition is bound by the host link, the record inserts (L2, no host
-// traffic) are not.  The keys go in kHostPasses passes over two alternating
-// workspaces; the record inserts of pass i run on a second stream while the
-// partition of pass i + 1 reads the link, the partition grid limited to
-// kHostPartCtas CTAs per SM so that record-insert CTAs find room beside it.
-// Ordering: pass i + 2 reuses pass i's workspace only after pass i's record
-// inserts (event), and the caller's stream waits for every record insert.
-constexpr uint64_t kHostPasses = 8;
-constexpr int kHostPartCtas = 1;
-
-bf_status launch_partitioned_host(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
+// Construction in at least `passes` passes over two alternating workspaces,
+// overlapping the two phases: the record inserts of pass i (bound by the
+// SM-to-L2 atomic path, little DRAM traffic) run on the filter's second
+// stream while the partition of pass i + 1 (a DRAM stream) runs on `stream`,
+// its grid limited to part_ctas CTAs per SM so that record-insert CTAs find
+// room beside it.  Ordering: pass i + 2 reuses pass i's workspace only after
+// pass i's record inserts (event), and the caller's stream waits for every
+// record insert.  Without room for two workspaces it falls back to the
+// serial schedule.
+bf_status launch_partitioned_overlap(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream,
+                                     uint64_t passes, int part_ctas) {
   const PartPlan pl = part_plan(f);
-  const uint64_t pass = std::min<uint64_t>(f->part.chunk_keys, (n + kHostPasses - 1) / kHostPasses);
+  const uint64_t pass = std::min<uint64_t>(f->part.chunk_keys, (n + passes - 1) / passes);
   const uint64_t counts_bytes = 8ull * static_cast<uint32_t>(kMaxParts);
   const uint64_t ws_one = counts_bytes + static_cast<uint64_t>(pl.nparts) * part_cap(f, pl, pass) * 8;
-  if (ensure_part_ws(f, 2 * ws_one) != BF_OK) return launch_partitioned(f, keys, n, stream);
+  if (ensure_part_ws(f, 2 * ws_one) != BF_OK) return launch_partitioned_serial(f, keys, n, stream);
   cudaError_t e;
   if (!f->rec_stream && (e = cudaStreamCreateWithFlags(&f->rec_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamCreate");
@@ -484,7 +507,7 @@ bf_status launch_partitioned_host(bf_filter* f, const uint64_t* keys, uint64_t n
       return cuda_fail(e, "cudaEventCreate");
   }
   PartLaunch L;
-  bf_status s = prepare_part_launch(f, pl, kHostPartCtas, &L);
+  bf_status s = prepare_part_launch(f, pl, part_ctas, &L);
   if (s != BF_OK) return s;
   bool used[2] = {false, false};
   uint64_t i = 0;
@@ -509,6 +532,26 @@ bf_status launch_partitioned_host(bf_filter* f, const uint64_t* keys, uint64_t n
     if (used[w] && (e = cudaStreamWaitEvent(stream, f->ev_rec[w], 0)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamWaitEvent");
   return BF_OK;
+}
+
+bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
+  if (f->part.passes >= 2 && n >= 2ull * part_tile(false))
+    return launch_partitioned_overlap(f, keys, n, stream, f->part.passes,
+                                      f->part.part_ctas ? static_cast<int>(f->part.part_ctas) : 1 << 30);
+  return launch_partitioned_serial(f, keys, n, stream);
+}
+
+// Construction from keys the kernels read in host memory: the slice
+// partition is bound by the host link, the record inserts (L2, no host
+// traffic) are not, so the overlapped schedule runs with at least
+// kHostPasses passes and kHostPartCtas partition CTAs per SM (enough for the
+// link).
+constexpr uint64_t kHostPasses = 8;
+constexpr int kHostPartCtas = 1;
+
+bf_status launch_partitioned_host(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
+  return launch_partitioned_overlap(f, keys, n, stream, std::max<uint64_t>(kHostPasses, f->part.passes),
+                                    kHostPartCtas);
 }
 
 bool use_partitioned_lookup(const bf_filter* f, uint64_t n) {
@@ -546,6 +589,7 @@ bf_status launch_contains_partitioned(const bf_filter* fc, const uint64_t* keys,
   const KernelEntry* qe = find_op(4, f->p, l.cg, l.phi, l.kpt);
   const KernelEntry* xe = find_expand();
   if (!pe || !qe || !xe) return fail(BF_EUNSUPPORTED, "no partitioned lookup kernels for this geometry");
+  if ((s = ensure_status(f)) != BF_OK) return s;
   char* ws = static_cast<char*>(f->look_ws);
   unsigned long long* counts = reinterpret_cast<unsigned long long*>(ws);
   uint64_t* records = reinterpret_cast<uint64_t*>(ws + counts_bytes);
@@ -570,8 +614,8 @@ bf_status launch_contains_partitioned(const bf_filter* fc, const uint64_t* keys,
       return cuda_fail(e, "cudaMemsetAsync");
     PartArgs pa{keys + lo, cnt, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, f->p.num_blocks,
                 f->p.num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, f->words, idx,
-                bitmap};
-    const uint64_t tiles = (cnt + kPartTile - 1) / kPartTile;
+                bitmap, f->status};
+    const uint64_t tiles = (cnt + part_tile(true) - 1) / part_tile(true);
     const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, static_cast<uint64_t>(sms) * per_sm));
     void* pargs[] = {&pa};
     if ((e = cudaLaunchKernel(pe->fn, dim3(grid), dim3(kPartThreads), pargs, smem, stream)) != cudaSuccess)
@@ -579,7 +623,7 @@ bf_status launch_contains_partitioned(const bf_filter* fc, const uint64_t* keys,
     f->last_launches += 1;
     for (uint32_t plo = 0; plo < pl.nparts; plo += per_launch) {
       const uint32_t phi = std::min(pl.nparts, plo + per_launch);
-      ProbeArgs qa{f->words, records, idx, counts, plo, phi, cap, bitmap, l.flags};
+      ProbeArgs qa{f->words, records, idx, counts, plo, phi, cap, bitmap, l.flags, f->p.num_blocks, f->status};
       uint32_t qgrid = 0;
       if ((s = resolve_grid(qe->fn, f->device, l.block_threads, l.grid_ctas, (phi - plo) * cap, l.kpt, &qgrid)) !=
           BF_OK)
@@ -786,6 +830,7 @@ bf_status bf_destroy(bf_filter* f) {
   release_pipeline(f);
   if (f->part_ws) cudaFree(f->part_ws);
   if (f->look_ws) cudaFree(f->look_ws);
+  if (f->status) cudaFree(f->status);
   if (f->owned && f->words) cudaFree(f->words);
   delete f;
   return BF_OK;
@@ -960,6 +1005,8 @@ bf_status bf_set_partition(bf_filter* f, const bf_partition* cfg) {
   if (cfg->lookup_mode > BF_PART_AUTO) return fail(BF_EINVAL, "lookup_mode must be BF_PART_OFF, BF_PART_ON or BF_PART_AUTO");
   if (cfg->lookup_chunk_keys < 4096 || cfg->lookup_chunk_keys > (1ull << 32))
     return fail(BF_EINVAL, "lookup_chunk_keys must be in [4096, 2^32]");
+  if (cfg->passes > 64) return fail(BF_EINVAL, "passes must be <= 64");
+  if (cfg->part_ctas > 8) return fail(BF_EINVAL, "part_ctas must be <= 8");
   f->part = *cfg;
   return BF_OK;
 }
@@ -973,6 +1020,22 @@ bf_status bf_get_partition(const bf_filter* f, bf_partition* out) {
 bf_status bf_last_launches(const bf_filter* f, uint32_t* n) {
   if (!f || !n) return fail(BF_EINVAL, "NULL argument");
   *n = f->last_launches;
+  return BF_OK;
+}
+
+bf_status bf_device_status(bf_filter* f, bf_stream_t stream, uint32_t* codes) {
+  if (!f || !codes) return fail(BF_EINVAL, "NULL argument");
+  *codes = 0;
+  if (!f->status) return BF_OK;  // no slice-partitioned call yet
+  DeviceGuard g(f->device);
+  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess && f->rec_stream) e = cudaStreamSynchronize(f->rec_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  uint32_t v = 0;
+  if ((e = cudaMemcpy(&v, f->status, sizeof v, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpy(status)");
+  if (v && (e = cudaMemset(f->status, 0, sizeof v)) != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+  *codes = v;
   return BF_OK;
 }
 
@@ -1010,7 +1073,9 @@ const char* bf_version(void) { return "bloomgb 0.1 (sm_103a)"; }
 namespace {
 
 constexpr uint64_t kNoAllocScratchBytes = 16ull << 20;            // 16 MiB per device
+constexpr uint64_t kNoAllocStatusBytes = 256;                      // status word of the index checks
 constexpr uint64_t kNoAllocCountsBytes = 8ull * kMaxParts;         // per-slice counters
+constexpr uint64_t kNoAllocHeadBytes = kNoAllocStatusBytes + kNoAllocCountsBytes;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
@@ -1073,7 +1138,7 @@ extern "C" bf_status bf_add_noalloc(const bf_params* params, void* d_words, cons
   uint64_t lo = 0, hi = kNoAllocScratchBytes / 8;
   while (lo < hi) {
     const uint64_t mid = lo + (hi - lo + 1) / 2;
-    if (kNoAllocCountsBytes + static_cast<uint64_t>(pl.nparts) * part_cap(&plan, pl, mid) * 8 <= kNoAllocScratchBytes)
+    if (kNoAllocHeadBytes + static_cast<uint64_t>(pl.nparts) * part_cap(&plan, pl, mid) * 8 <= kNoAllocScratchBytes)
       lo = mid;
     else
       hi = mid - 1;
@@ -1087,8 +1152,9 @@ extern "C" bf_status bf_add_noalloc(const bf_params* params, void* d_words, cons
   if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kNoAllocMaxDevices) return BF_ECUDA;
   void* scratch = nullptr;
   if (noalloc_scratch(device, &scratch) != cudaSuccess) return BF_ECUDA;
-  unsigned long long* counts = static_cast<unsigned long long*>(scratch);
-  uint64_t* records = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + kNoAllocCountsBytes);
+  uint32_t* status = static_cast<uint32_t*>(scratch);
+  unsigned long long* counts = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + kNoAllocStatusBytes);
+  uint64_t* records = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + kNoAllocHeadBytes);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
   // the array keeps the previous call's contents: the counters must start at zero
@@ -1101,9 +1167,10 @@ extern "C" bf_status bf_add_noalloc(const bf_params* params, void* d_words, cons
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return BF_ECUDA;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pe->fn, kPartThreads, smem) != cudaSuccess)
     return BF_ECUDA;
-  const uint64_t tiles = (n + kPartTile - 1) / kPartTile;
+  const uint64_t tiles = (n + part_tile(false) - 1) / part_tile(false);
   PartArgs pa{d_keys, n, params->seed + 0x27D4EB2F165667C5ull + 8ull, params->num_blocks,
-              params->num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, d_words};
+              params->num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, d_words,
+              nullptr, nullptr, status};
   void* pargs[] = {&pa};
   const uint32_t pgrid = static_cast<uint32_t>(std::min<uint64_t>(tiles, static_cast<uint64_t>(sms) * std::max(per_sm, 1)));
   if (cudaLaunchKernel(pe->fn, dim3(pgrid), dim3(kPartThreads), pargs, smem, st) != cudaSuccess) return BF_ECUDA;
@@ -1115,7 +1182,7 @@ extern "C" bf_status bf_add_noalloc(const bf_params* params, void* d_words, cons
   const uint32_t per_launch = 26 > slice_bytes_log2 ? 1u << (26 - slice_bytes_log2) : 1u;
   for (uint32_t plo = 0; plo < pl.nparts; plo += per_launch) {
     const uint32_t phi = std::min(pl.nparts, plo + per_launch);
-    RecArgs ra{d_words, records, counts, plo, phi, cap, 0u};
+    RecArgs ra{d_words, records, counts, plo, phi, cap, 0u, params->num_blocks, status};
     const uint64_t rtiles = (static_cast<uint64_t>(phi - plo) * cap + 31) / 32;
     const uint64_t rctas = (rtiles + kThreads / 32 - 1) / (kThreads / 32);
     const uint32_t rgrid =
@@ -1123,6 +1190,20 @@ extern "C" bf_status bf_add_noalloc(const bf_params* params, void* d_words, cons
     void* rargs[] = {&ra};
     if (cudaLaunchKernel(re->fn, dim3(rgrid), dim3(kThreads), rargs, 0, st) != cudaSuccess) return BF_ECUDA;
   }
+  return BF_OK;
+}
+
+extern "C" bf_status bf_noalloc_status(uint32_t* codes) {
+  if (!codes) return BF_EINVAL;
+  *codes = 0;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kNoAllocMaxDevices) return BF_ECUDA;
+  void* scratch = nullptr;
+  if (noalloc_scratch(device, &scratch) != cudaSuccess) return BF_ECUDA;
+  uint32_t v = 0;
+  if (cudaMemcpy(&v, scratch, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return BF_ECUDA;
+  if (v && cudaMemset(scratch, 0, sizeof v) != cudaSuccess) return BF_ECUDA;
+  *codes = v;
   return BF_OK;
 }
 

@@ -31,20 +31,22 @@ struct GupsArgs {
 };
 
 // Launch geometry of the slice-partition kernel, shared by the kernel and the host.
+// A CTA of kPartThreads threads partitions tiles of part_tile(lookup) keys,
+// part_keys_per_thread(lookup) keys per thread.
 constexpr int kPartThreads = 512;
-constexpr int kPartKeysPerThread = 8;
-constexpr int kPartTile = kPartThreads * kPartKeysPerThread;  // keys per CTA tile
+constexpr int kPartKeysAdd = 6, kPartKeysLookup = 6;
+constexpr int part_keys_per_thread(bool lookup) { return lookup ? kPartKeysLookup : kPartKeysAdd; }
+constexpr int part_tile(bool lookup) { return kPartThreads * part_keys_per_thread(lookup); }
 constexpr int kMaxParts = 1024;
 constexpr uint64_t kRecTile = 128;  // slice buffer capacity granule: the largest record tile (32 x KPT)
 
 // dynamic shared memory of the partition kernel for `nparts` slices (the
-// lookup flavour also keeps each record's query index)
+// lookup flavour also keeps each record's in-tile query index)
 constexpr size_t partition_smem_bytes(int nparts, bool lookup = false) {
-  return static_cast<size_t>(kPartTile) * 8        // records of the tile, sorted by slice
-         + static_cast<size_t>(nparts) * 4 * 2     // per-slice count and start in the tile
-         + static_cast<size_t>(nparts) * 8         // per-slice global offset
-         + 64 * 4                                  // scan scratch (one entry per warp)
-         + (lookup ? static_cast<size_t>(kPartTile) * 4 : 0);  // query index of each sorted record
+  return static_cast<size_t>(part_tile(lookup)) * 8                    // the tile's records, sorted by slice
+         + static_cast<size_t>(nparts) * 8                               // per-slice packed buffer index and limit
+         + static_cast<size_t>(nparts) * 4 * 3                           // per-slice counts (two tiles) and start
+         + (lookup ? static_cast<size_t>(part_tile(lookup)) * 2 : 0);  // in-tile query index of each record
 }
 
 // Arguments of the slice-partition kernel (L2-blocked construction).
@@ -62,6 +64,7 @@ struct PartArgs {
   void* filter;                  // overflow records are inserted (or looked up) here directly
   uint32_t* idx;                 // lookup: [nparts * cap] query index of each record
   uint32_t* bitmap;              // lookup: one result bit per query (zeroed before launch)
+  uint32_t* status;              // kStatus* bits of index checks that failed (access skipped)
 };
 
 // Arguments of the record-probe kernel (slice-partitioned lookup): records
@@ -75,6 +78,8 @@ struct ProbeArgs {
   uint64_t cap;
   uint32_t* bitmap;
   uint32_t flags;
+  uint64_t nblocks;   // b: a record's block index must be below it
+  uint32_t* status;   // kStatus* bits of index checks that failed
 };
 
 // Arguments of the bitmap expansion: out[i] = bit i of `bitmap`, i < n.
@@ -84,7 +89,6 @@ struct ExpandArgs {
   uint8_t* out;
 };
 
-// Arguments of the record-insert kernel.
 // Arguments of the record-insert kernel: slices [part_lo, part_hi) of the
 // slice buffers (one launch per group of slices keeps the warps within one
 // L2-sized window of the filter; a kernel boundary re-synchronises them).
@@ -95,6 +99,18 @@ struct RecArgs {
   uint32_t part_lo, part_hi;
   uint64_t cap;
   uint32_t flags;
+  uint64_t nblocks;   // b: a record's block index must be below it
+  uint32_t* status;   // kStatus* bits of index checks that failed
+};
+
+// Index checks of the slice-partitioned kernels.  Indexes derived from data
+// are clamped into their arrays or checked before use; a failed check sets
+// its bit in the status word and skips the access, so no index can leave its
+// buffer.  None of them fails when the kernels are correct.
+enum : uint32_t {
+  kStatusBlockRange = 1u << 1,    // a record's block index >= b (record insert / probe)
+  kStatusRecordSlice = 1u << 3,   // a sorted record outside the slices, or its block >= b (partition)
+  kStatusBufferIndex = 1u << 4,   // a slice-buffer index outside the buffers (partition)
 };
 
 // One filter of a batch: its bit array and its run of the batch's keys.

@@ -196,6 +196,14 @@ __device__ __forceinline__ void red_or(uint64_t* p, uint64_t v, uint64_t pol) {
                : "memory");
 }
 
+// streaming 64-bit store with an L2 policy
+__device__ __forceinline__ void st_u64_hint(uint64_t* p, uint64_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_u32_hint(uint32_t* p, uint32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+
 // result stores: streaming
 __device__ __forceinline__ void st_out1(uint8_t* p, uint32_t v) {
   asm volatile("st.global.cs.u8 [%0], %1;" ::"l"(p), "r"(v) : "memory");

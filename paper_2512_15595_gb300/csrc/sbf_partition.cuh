@@ -13,7 +13,8 @@
 //     CTA-local counting sort by slice (j >> shift), one global atomic per
 //     (tile, slice) to reserve space, coalesced record stores.  A record whose
 //     slice buffer is full is inserted on the spot with direct atomics, so no
-//     key distribution can lose a key.
+//     key distribution can lose a key.  Few large slices (64 MiB) give long
+//     runs per slice and tile, which is what the DRAM writes need.
 //   sbf_add_records_kernel: the cooperative-group insert of sbf_add_kernel,
 //     reading records slice by slice instead of keys (no hashing).
 #pragma once
@@ -21,6 +22,9 @@
 #include "sbf_kernels.cuh"
 
 namespace bloomgb {
+
+// a failed index check: set its bit in the status word (the access is skipped)
+__device__ __forceinline__ void flag_status(uint32_t* status, uint32_t bit) { atomicOr(status, bit); }
 
 // OR a record's pattern into its block with one thread (Theta = 1, Phi = s):
 // the overflow path of the partition kernel.
@@ -57,126 +61,208 @@ __device__ __forceinline__ bool lookup_one(const typename WordOf<S>::type* filte
   return miss == 0;
 }
 
-// LOOKUP = false: construction records.  LOOKUP = true: lookup records, each
-// with the index of its query in `idx`; a query whose slice buffer is full is
-// answered on the spot (its result bit is set if it is found).
+// One tile of the slice partition (LOOKUP = false: construction records;
+// LOOKUP = true: lookup records, each with the index of its query in `idx`).
+// On entry key[] holds the tile's keys (loaded during the previous tile); on
+// exit it holds the next tile's keys.  Three barriers per tile:
+//   hash every key, rank it within its slice (shared-memory counters; two
+//     sets that alternate between tiles, so clearing one needs no barrier)
+//   B1 -> one warp scans the slice counts into start offsets; the other
+//     counter set is cleared
+//   B2 -> one global atomic per slice present reserves the slice's run in its
+//     buffer; every thread scatters its records into sorted order in shared
+//     memory and then loads the next tile's keys into the registers the
+//     records left; the reservations become a packed (buffer index, limit)
+//     per slice
+//   B3 -> coalesced write-out: consecutive sorted positions of one slice go
+//     to consecutive slots of that slice's buffer.
+// FULL = a tile of exactly TILE keys (every tile but the last): no per-key
+// bounds tests.  Indexes derived from data are clamped into their arrays;
+// a record whose slice buffer is full takes the direct path (inserted, or
+// looked up, on the spot), and one that fails a check is skipped and flagged
+// in the status word.
+template <int B, int S, int K, bool LOOKUP, int SALTS, int KPTH, bool FULL>
+__device__ __forceinline__ void partition_tile(const PartArgs& a, uint64_t (&key)[KPTH], uint32_t it, uint64_t tile,
+                                               uint64_t ntiles, uint64_t* trec, unsigned long long* oblim,
+                                               uint32_t* cnt, uint32_t* start, uint16_t* tidx, uint64_t pol_keys,
+                                               uint64_t pol_filter) {
+  constexpr uint32_t TILE = kPartThreads * KPTH;
+  constexpr uint64_t kMask48 = (1ull << 48) - 1;
+  using W = typename WordOf<S>::type;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t nparts = a.nparts, shift = a.shift;
+  const uint64_t base = tile * TILE;
+  const uint32_t tile_n = FULL ? TILE : static_cast<uint32_t>(a.n - base);
+  uint32_t* c = cnt + (it & 1u) * nparts;
+  // block index ((h >> 32) * b) >> 32 for b <= 2^32 (b = bl + 2^32 * bh, bh in {0, 1})
+  const uint32_t bl = static_cast<uint32_t>(a.nblocks), bh = static_cast<uint32_t>(a.nblocks >> 32);
+
+  // hash and rank; pr = slice << 13 | rank within the tile's slice run
+  uint32_t pr[KPTH];
+#pragma unroll
+  for (int u = 0; u < KPTH; ++u) {
+    const uint64_t h = xxh64_key(key[u], a.acc0);
+    const uint32_t hi = static_cast<uint32_t>(h >> 32);
+    const uint32_t j = __umulhi(hi, bl) + hi * bh;
+    key[u] = (static_cast<uint64_t>(j) << 32) | static_cast<uint32_t>(h);  // the record replaces the key
+    const uint32_t part = min(j >> shift, nparts - 1u);
+    if (FULL || u * kPartThreads + tid < tile_n) pr[u] = (part << 13) | atomicAdd(&c[part], 1u);
+    else pr[u] = 0xFFFFFFFFu;
+  }
+  __syncthreads();  // B1
+
+  if (warp == 0) {
+    // exclusive scan of the counts; lane l owns slices l, l + 32, ... (any
+    // slice order is a valid sort order: the runs only need disjoint ranges)
+    const uint32_t nq = (nparts + 31u) >> 5;
+    uint32_t sum = 0;
+    for (uint32_t q = 0; q < nq; ++q) {
+      const uint32_t p = q * 32u + lane;
+      if (p < nparts) sum += c[p];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t v = __shfl_up_sync(kFullMask, incl, d);
+      if (lane >= static_cast<uint32_t>(d)) incl += v;
+    }
+    uint32_t run = incl - sum;
+    for (uint32_t q = 0; q < nq; ++q) {
+      const uint32_t p = q * 32u + lane;
+      if (p < nparts) {
+        const uint32_t v = c[p];
+        start[p] = run;
+        run += v;
+      }
+    }
+  }
+  uint32_t* cn = cnt + ((it + 1u) & 1u) * nparts;  // the next tile's set (its last reader ran before B1)
+  for (uint32_t p = tid; p < nparts; p += kPartThreads) cn[p] = 0;
+  __syncthreads();  // B2
+
+  const uint32_t c0 = tid < nparts ? c[tid] : 0u;
+  const uint32_t c1 = tid + kPartThreads < nparts ? c[tid + kPartThreads] : 0u;
+  unsigned long long r0 = 0, r1 = 0;
+  if (c0) r0 = atomicAdd(a.counts + tid, static_cast<unsigned long long>(c0));
+  if (c1) r1 = atomicAdd(a.counts + tid + kPartThreads, static_cast<unsigned long long>(c1));
+#pragma unroll
+  for (int u = 0; u < KPTH; ++u) {
+    if (FULL || pr[u] != 0xFFFFFFFFu) {
+      const uint32_t pos = min(start[pr[u] >> 13] + (pr[u] & 0x1FFFu), TILE - 1u);
+      trec[pos] = key[u];
+      if constexpr (LOOKUP) tidx[pos] = static_cast<uint16_t>(u * kPartThreads + tid);
+    }
+  }
+  // the next tile's keys go into the registers the records just left
+  const uint64_t next = tile + gridDim.x;
+  if (next < ntiles) {
+    const uint64_t nb = next * TILE;
+    const uint64_t* kp = a.keys + nb + tid;
+    if (a.n - nb >= TILE) {
+#pragma unroll
+      for (int u = 0; u < KPTH; ++u) key[u] = ld_key1(kp + u * kPartThreads, pol_keys);
+    } else {
+      const uint32_t tn = static_cast<uint32_t>(a.n - nb);
+#pragma unroll
+      for (int u = 0; u < KPTH; ++u)
+        key[u] = u * kPartThreads + tid < tn ? ld_key1(kp + u * kPartThreads, pol_keys) : 0ull;
+    }
+  }
+  // per present slice: buffer index of sorted position i is ob + i while i is
+  // below the limit (the slots left in the slice buffer); ob mod 2^48 | limit << 48
+  auto pack = [&](uint32_t p, uint32_t cp, unsigned long long res) {
+    const uint32_t st = start[p];
+    const uint64_t avail = a.cap > res ? a.cap - res : 0ull;
+    const uint32_t lim = st + static_cast<uint32_t>(avail < cp ? avail : cp);
+    const uint64_t ob = (static_cast<uint64_t>(p) * a.cap + res - st) & kMask48;
+    oblim[p] = ob | (static_cast<uint64_t>(lim) << 48);
+  };
+  if (c0) pack(tid, c0, r0);
+  if (c1) pack(tid + kPartThreads, c1, r1);
+  __syncthreads();  // B3
+
+  // coalesced write-out; the slice is read back from the record's block
+  // index.  Records that do not go to their buffer here are handled after
+  // the loop (one branch per thread, not per record).
+  const uint64_t total = static_cast<uint64_t>(nparts) * a.cap;
+  uint32_t slow = 0;
+#pragma unroll
+  for (int u = 0; u < KPTH; ++u) {
+    const uint32_t i = u * kPartThreads + tid;
+    if (FULL || i < tile_n) {
+      const uint64_t r = trec[i];
+      const uint32_t praw = static_cast<uint32_t>(r >> 32) >> shift;
+      const unsigned long long pk = oblim[min(praw, nparts - 1u)];
+      const uint64_t dst = (pk + i) & kMask48;
+      const bool ok = i < static_cast<uint32_t>(pk >> 48) && praw < nparts && dst < total;
+      if (ok) {
+        st_u64_hint(a.records + dst, r, pol_keys);
+        if constexpr (LOOKUP) st_u32_hint(a.idx + dst, static_cast<uint32_t>(base) + tidx[i], pol_keys);
+      }
+      slow |= static_cast<uint32_t>(!ok) << u;
+    }
+  }
+  if (slow) {
+#pragma unroll 1
+    for (int u = 0; u < KPTH; ++u) {
+      if (!((slow >> u) & 1u)) continue;
+      const uint32_t i = u * kPartThreads + tid;
+      const uint64_t r = trec[i];
+      const uint32_t praw = static_cast<uint32_t>(r >> 32) >> shift;
+      if (praw >= nparts || (r >> 32) >= a.nblocks) {
+        flag_status(a.status, kStatusRecordSlice);
+        continue;
+      }
+      if (i < static_cast<uint32_t>(oblim[praw] >> 48)) {  // it fit, so its buffer index failed the check
+        flag_status(a.status, kStatusBufferIndex);
+        continue;
+      }
+      // the slice buffer is full: the direct method
+      if constexpr (LOOKUP) {
+        const uint32_t q = static_cast<uint32_t>(base) + tidx[i];
+        if (lookup_one<B, S, K, SALTS>(static_cast<const W*>(a.filter), r >> 32, static_cast<uint32_t>(r),
+                                       pol_filter))
+          atomicOr(a.bitmap + (q >> 5), 1u << (q & 31u));
+      } else {
+        insert_one<B, S, K, SALTS>(static_cast<W*>(a.filter), r >> 32, static_cast<uint32_t>(r), pol_filter);
+      }
+    }
+  }
+}
+
 template <int B, int S, int K, bool LOOKUP, int SALTS = 0>
 __global__ void __launch_bounds__(kPartThreads, LOOKUP ? 3 : 4) sbf_partition_kernel(const PartArgs a) {
+  constexpr int KPTH = LOOKUP ? kPartKeysLookup : kPartKeysAdd;
+  constexpr uint32_t TILE = kPartThreads * KPTH;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* tile_rec = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(tile_rec + kPartTile);
-  uint32_t* start = cnt + a.nparts;
-  // per slice: reserved global position minus the slice's first position in
-  // the tile (modulo 2^64), so that sorted position i goes to off[p] + i
-  unsigned long long* off = reinterpret_cast<unsigned long long*>(start + a.nparts);
-  uint32_t* warp_sum = reinterpret_cast<uint32_t*>(off + a.nparts);
-  uint32_t* tile_idx = warp_sum + 64;  // lookup only (kPartTile entries)
-
-  using W = typename WordOf<S>::type;
+  uint64_t* trec = reinterpret_cast<uint64_t*>(smem);                               // [TILE] sorted records
+  unsigned long long* oblim = reinterpret_cast<unsigned long long*>(trec + TILE);  // [nparts]
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(oblim + a.nparts);                   // [2][nparts]
+  uint32_t* start = cnt + 2 * a.nparts;                                            // [nparts]
+  uint16_t* tidx = reinterpret_cast<uint16_t*>(start + a.nparts);                  // lookup: [TILE]
   const uint64_t pol_keys = policy_evict_first();
   const uint64_t pol_filter = policy_evict_normal();
   const uint32_t tid = threadIdx.x;
-  const uint64_t ntiles = (a.n + kPartTile - 1) / kPartTile;
-
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const uint64_t base = tile * kPartTile;
-    const uint32_t tile_n = static_cast<uint32_t>(a.n - base < kPartTile ? a.n - base : kPartTile);
-    for (uint32_t p = tid; p < a.nparts; p += kPartThreads) cnt[p] = 0;
-    __syncthreads();
-
-    // key i of the tile is handled by thread i % kPartThreads; all loads are
-    // issued before any hashing so that their latencies overlap
-    uint64_t rec[kPartKeysPerThread];
+  const uint64_t ntiles = (a.n + TILE - 1) / TILE;
+  for (uint32_t p = tid; p < 2 * a.nparts; p += kPartThreads) cnt[p] = 0;
+  uint64_t key[KPTH];
+  uint64_t tile = blockIdx.x;
+  if (tile < ntiles) {
+    const uint64_t nb = tile * TILE;
+    const uint64_t* kp = a.keys + nb + tid;
+    const uint64_t tn = a.n - nb;
 #pragma unroll
-    for (int u = 0; u < kPartKeysPerThread; ++u) {
-      const uint32_t i = u * kPartThreads + tid;
-      rec[u] = i < tile_n ? ld_key1(a.keys + base + i, pol_keys) : 0;
-    }
-    // hash, count; pr = slice << 12 | rank within the tile's slice run
-    uint32_t pr[kPartKeysPerThread];
-#pragma unroll
-    for (int u = 0; u < kPartKeysPerThread; ++u) {
-      pr[u] = 0xFFFFFFFFu;
-      if (u * kPartThreads + tid < tile_n) {
-        const uint64_t h = xxh64_key(rec[u], a.acc0);
-        const uint64_t j = block_of(h, a.nblocks, a.block_mode);
-        rec[u] = (j << 32) | static_cast<uint32_t>(h);
-        const uint32_t part = static_cast<uint32_t>(j >> a.shift);
-        pr[u] = (part << 12) | atomicAdd(&cnt[part], 1u);
-      }
-    }
-    __syncthreads();
-
-    // exclusive scan of the per-slice counts (nparts <= 1024, two per thread)
-    {
-      const uint32_t p0 = 2 * tid, p1 = 2 * tid + 1;
-      const uint32_t c0 = p0 < a.nparts ? cnt[p0] : 0, c1 = p1 < a.nparts ? cnt[p1] : 0;
-      uint32_t incl = c0 + c1;
-      const uint32_t lane = tid & 31u, warp = tid >> 5;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t v = __shfl_up_sync(kFullMask, incl, d);
-        if (lane >= static_cast<uint32_t>(d)) incl += v;
-      }
-      if (lane == 31) warp_sum[warp] = incl;
-      __syncthreads();
-      if (warp == 0) {
-        uint32_t ws = lane < kPartThreads / 32 ? warp_sum[lane] : 0;
-        uint32_t wi = ws;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const uint32_t v = __shfl_up_sync(kFullMask, wi, d);
-          if (lane >= static_cast<uint32_t>(d)) wi += v;
-        }
-        if (lane < kPartThreads / 32) warp_sum[lane] = wi - ws;  // exclusive
-      }
-      __syncthreads();
-      const uint32_t excl = incl - (c0 + c1) + warp_sum[warp];
-      if (p0 < a.nparts) start[p0] = excl;
-      if (p1 < a.nparts) start[p1] = excl + c0;
-    }
-    __syncthreads();
-
-    // reserve space in each slice's buffer, and scatter into shared memory
-    for (uint32_t p = tid; p < a.nparts; p += kPartThreads)
-      off[p] = (cnt[p] ? atomicAdd(a.counts + p, static_cast<unsigned long long>(cnt[p])) : 0ull) -
-               static_cast<unsigned long long>(start[p]);
-#pragma unroll
-    for (int u = 0; u < kPartKeysPerThread; ++u) {
-      if (pr[u] != 0xFFFFFFFFu) {
-        const uint32_t part = pr[u] >> 12;
-        const uint32_t pos = start[part] + (pr[u] & 0xFFFu);
-        tile_rec[pos] = rec[u];
-        if constexpr (LOOKUP) tile_idx[pos] = static_cast<uint32_t>(base) + u * kPartThreads + tid;
-      }
-    }
-    __syncthreads();
-
-    // coalesced write-out: consecutive positions of one slice go to
-    // consecutive addresses of that slice's buffer (the slice is read back
-    // from the record's block index)
-    for (uint32_t i = tid; i < tile_n; i += kPartThreads) {
-      const uint64_t r = tile_rec[i];
-      const uint32_t p = static_cast<uint32_t>((r >> 32) >> a.shift);
-      const uint64_t dst = off[p] + i;
-      if constexpr (LOOKUP) {
-        const uint32_t q = tile_idx[i];
-        if (dst < a.cap) {
-          a.records[static_cast<uint64_t>(p) * a.cap + dst] = r;
-          a.idx[static_cast<uint64_t>(p) * a.cap + dst] = q;
-        } else if (lookup_one<B, S, K, SALTS>(static_cast<const W*>(a.filter), r >> 32, static_cast<uint32_t>(r),
-                                       pol_filter)) {
-          atomicOr(a.bitmap + (q >> 5), 1u << (q & 31u));
-        }
-      } else {
-        if (dst < a.cap) {
-          a.records[static_cast<uint64_t>(p) * a.cap + dst] = r;
-        } else {
-          insert_one<B, S, K, SALTS>(static_cast<W*>(a.filter), r >> 32, static_cast<uint32_t>(r), pol_filter);
-        }
-      }
-    }
-    __syncthreads();
+    for (int u = 0; u < KPTH; ++u)
+      key[u] = u * kPartThreads + tid < tn ? ld_key1(kp + u * kPartThreads, pol_keys) : 0ull;
+  }
+  __syncthreads();
+  for (uint32_t it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    if (a.n - tile * TILE >= TILE)
+      partition_tile<B, S, K, LOOKUP, SALTS, KPTH, true>(a, key, it, tile, ntiles, trec, oblim, cnt, start, tidx,
+                                                         pol_keys, pol_filter);
+    else
+      partition_tile<B, S, K, LOOKUP, SALTS, KPTH, false>(a, key, it, tile, ntiles, trec, oblim, cnt, start, tidx,
+                                                          pol_keys, pol_filter);
   }
 }
 
@@ -220,6 +306,10 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_add_records_kernel(const
         if constexpr (THETA > 1) {
           rm = __shfl_sync(kFullMask, rm, m, THETA);
           vm = __shfl_sync(kFullMask, vm, m, THETA);
+        }
+        if (((vm >> u) & 1u) && (rm >> 32) >= a.nblocks) {
+          flag_status(a.status, kStatusBlockRange);
+          vm &= ~(1u << u);
         }
         if ((vm >> u) & 1u) {
           const uint32_t hm = static_cast<uint32_t>(rm);
@@ -276,6 +366,10 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_probe_records_kernel(con
       for (int m = 0; m < THETA; ++m) {
         uint64_t rm = ((valid >> u) & 1u) ? rec[u] : 0ull;  // invalid slots read block 0
         if constexpr (THETA > 1) rm = __shfl_sync(kFullMask, rm, m, THETA);
+        if ((rm >> 32) >= a.nblocks) {  // a record outside the filter reads block 0 instead
+          flag_status(a.status, kStatusBlockRange);
+          rm &= 0xFFFFFFFFull;
+        }
         hk[u][m] = static_cast<uint32_t>(rm);
         const W* bp = filter + (rm >> 32) * C::s + r * PHI;
 #pragma unroll

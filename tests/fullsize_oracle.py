@@ -18,12 +18,19 @@ import oracle  # noqa: E402
 import synthkeys  # noqa: E402
 
 
+def _in_range(blocks, a, b):
+    return np.nonzero((blocks >= a) & (blocks < b))[0]
+
+
 def add_ranges(args):
-    """Bits of each block range contributed by insert keys [lo, hi)."""
+    """Bits of each block range contributed by insert keys [lo, hi).  The
+    oracle's block index selects each range's keys first, so the range
+    construction only sees keys that land in it."""
     geom_kw, ranges, lo, hi = args
     geom = oracle.Geometry(**geom_kw)
     keys = synthkeys.splitmix64(synthkeys.SEED_INSERT, lo, hi - lo)
-    return [oracle.add_block_range(geom, a, b, keys) for a, b in ranges]
+    blocks = oracle.block_indices(keys, geom.num_blocks, geom.seed)
+    return [oracle.add_block_range(geom, a, b, keys[_in_range(blocks, a, b)]) for a, b in ranges]
 
 
 def lookup_ranges(args):
@@ -32,10 +39,12 @@ def lookup_ranges(args):
     geom_kw, ranges, slices, lo, hi, n_insert, ratio_den = args
     geom = oracle.Geometry(**geom_kw)
     q, _ = synthkeys.stream_queries(lo, hi - lo, n_insert, ratio_den)
+    blocks = oracle.block_indices(q, geom.num_blocks, geom.seed)
     idx, ans = [], []
     for (a, b), words in zip(ranges, slices):
-        r = oracle.contains_block_range(geom, words, a, b, q)
-        hit = np.nonzero(r != 2)[0]
-        idx.append(hit + lo)
-        ans.append(r[hit])
+        sel = _in_range(blocks, a, b)
+        r = oracle.contains_block_range(geom, words, a, b, q[sel])
+        assert (r != 2).all()
+        idx.append(sel + lo)
+        ans.append(r)
     return np.concatenate(idx), np.concatenate(ans)

@@ -1,10 +1,14 @@
 """The 4 GiB workload at full size, in the launch configuration bench.py
 times (tuned layouts, slice-partitioned construction of 3,435,973,836 keys,
 slice-partitioned lookup of 10^9 queries in passes of 2^29), against the
-oracle on sampled outputs: the bit array of the first and the last 4096
-blocks, recomputed by the oracle from every insert key, and the answer of
-every query whose block lies in those ranges (about 61,000 of them); plus
-the property that holds at any size: every member query is found.
+oracle on sampled outputs: the bit array of five 4096-block ranges --
+the first and the last blocks, two ranges across the boundary between two
+record-insert windows (the 16th and the 48th window boundary) and one
+across a slice boundary inside a window (the 32nd window's first slice
+boundary), slice and window sizes taken from the tuned setting -- recomputed by the
+oracle from every insert key, and the answer of every query whose block
+lies in those ranges (about 150,000 of them); plus the property that holds
+at any size: every member query is found.
 
 The oracle's share runs in a spawn process pool over the host's cores
 (spawned workers start fresh interpreters: none inherits a CUDA context).
@@ -32,6 +36,13 @@ SPAN = 4096
 CHUNK = 1 << 23
 
 
+def tuned_slice_window():
+    """Blocks per slice and per record-insert window of the tuned setting."""
+    from paper_2512_15595_gb300 import autotune
+    part = autotune.tuned_layout(B, S, K, "hbm", 0)["partition"]
+    return (1 << part["slice_log2"]) // (B // 8), (1 << part["window_log2"]) // (B // 8)
+
+
 def test_4gib_workload_sampled_parity():
     import torch
     from paper_2512_15595_gb300 import Filter, autotune, build
@@ -39,7 +50,12 @@ def test_4gib_workload_sampled_parity():
 
     geom_kw = dict(num_blocks=NBLOCKS, block_bits=B, word_bits=S, k=K, seed=0)
     oracle.build()  # compiled once here, before the pool's workers load it
-    ranges = [(0, SPAN), (NBLOCKS - SPAN, NBLOCKS)]
+    SLICE, WINDOW = tuned_slice_window()
+    assert WINDOW > SLICE and NBLOCKS // WINDOW >= 64
+    half = SPAN // 2
+    ranges = [(0, SPAN), (WINDOW * 16 - half, WINDOW * 16 + half),
+              (WINDOW * 32 + SLICE - half, WINDOW * 32 + SLICE + half),
+              (WINDOW * 48 - half, WINDOW * 48 + half), (NBLOCKS - SPAN, NBLOCKS)]
     ctx = mp.get_context("spawn")
     workers = max(1, min(32, os.cpu_count() or 1))
     with ctx.Pool(workers) as pool:
@@ -62,6 +78,7 @@ def test_4gib_workload_sampled_parity():
         f.contains(qd, out=out)
         launches_con = f.last_launches()
         torch.cuda.synchronize()
+        assert f.device_status() == 0  # no index check failed in the partitioned kernels
         assert launches_add > 1 and launches_con > 1  # the slice-partitioned paths ran
         members = flags == 1
         assert int(members.sum().item()) > 0
@@ -85,7 +102,7 @@ def test_4gib_workload_sampled_parity():
         res = pool.map(FO.lookup_ranges, look_jobs, chunksize=1)
     idx = np.concatenate([r[0] for r in res])
     ans = np.concatenate([r[1] for r in res])
-    expect = SPAN * 2 / NBLOCKS * N_LOOKUP
+    expect = SPAN * len(ranges) / NBLOCKS * N_LOOKUP
     assert 0.9 * expect < idx.size < 1.1 * expect, idx.size
     mism = np.nonzero(got_out[idx] != ans)[0]
     assert mism.size == 0, f"{mism.size} sampled answers differ, e.g. query {idx[mism[0]]}"

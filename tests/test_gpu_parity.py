@@ -258,6 +258,7 @@ def test_partitioned_add_bit_exact(torch, B, S, k):
                 assert np.array_equal(words_np(f), ref.as_bytes()), (cfg, cg, phi, kpt)
                 passes = -(-ins.size // cfg.get("chunk_keys", 1 << 32))
                 assert launches == per_pass * passes, (cfg, launches)
+                assert f.device_status() == 0
                 f.close()
 
 
@@ -295,6 +296,74 @@ def test_partitioned_add_from_host_keys(torch):
         torch.cuda.synchronize()
         assert np.array_equal(words_np(f), ref.as_bytes()), cfg
         assert np.array_equal(h_out, ref.contains(q)), cfg
+        assert f.device_status() == 0
+        f.close()
+
+
+@pytest.mark.parametrize("B,S,k", [(256, 32, 8), (512, 64, 16)])
+def test_partitioned_add_overlapped_passes(torch, B, S, k):
+    """Device-key construction in passes over two workspaces, the record
+    inserts of one pass on a second stream beside the next pass's partition
+    (grid limited to part_ctas CTAs per SM): the oracle's bits for every pass
+    count and CTA limit, keys at a 16-byte and at an 8-byte offset, and a
+    following serial construction on the same filter."""
+    geom = oracle.Geometry(num_blocks=(1 << 14) + 77, block_bits=B, word_bits=S, k=k, seed=77)
+    ins = synthkeys.insert_keys(150_001, seed=85)
+    more = synthkeys.insert_keys(30_000, seed=86)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    want_first = ref.as_bytes().copy()
+    ref.add(more)
+    buf = torch.zeros(ins.size + 1, dtype=torch.int64, device="cuda")
+    nparts = -(-geom.nbytes // (1 << 16))
+    windows = -(-nparts // (1 << (26 - 16)))
+    for passes, part_ctas, offset, chunk in [(2, 0, 0, 1 << 32), (3, 1, 1, 1 << 32), (7, 2, 0, 1 << 32),
+                                            (2, 1, 1, 4096 * 5 + 1)]:
+        dk = buf[offset:offset + ins.size]
+        dk.copy_(dev_keys(torch, ins))
+        f = gpu_filter(geom, torch)
+        f.set_partition(mode=1, slice_log2=16, passes=passes, part_ctas=part_ctas, chunk_keys=chunk)
+        f.add(dk)
+        pass_keys = min(chunk, -(-ins.size // passes))
+        assert f.last_launches() == -(-ins.size // pass_keys) * (1 + windows), (passes, f.last_launches())
+        assert np.array_equal(words_np(f), want_first), (passes, part_ctas, offset)
+        f.set_partition(passes=0)
+        f.add(dev_keys(torch, more))
+        assert np.array_equal(words_np(f), ref.as_bytes()), (passes, part_ctas, offset)
+        assert f.device_status() == 0
+        f.close()
+
+
+def test_partition_many_tiles_per_cta(torch):
+    """Each partition CTA walks many tiles (grid limited to one CTA per SM for
+    construction; lookup queries spanning several grid-strides): the
+    prefetch of the next tile into the other key buffer, the alternating
+    counter sets and the reuse of a tile's key buffer for its sorted records
+    all run, with an odd key count (the last key copied alone) and keys at a
+    16-byte and at an 8-byte offset."""
+    from paper_2512_15595_gb300 import BF_OP_CONTAINS
+    geom = oracle.Geometry(num_blocks=(1 << 15) + 5, block_bits=256, word_bits=32, k=8, seed=3)
+    ins = synthkeys.insert_keys(2_000_007, seed=95)
+    q, is_mem = synthkeys.mixed_queries(2_000_007, 1_000_000, 5_000_003, seed_insert=95)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    ref_out = ref.contains(q)
+    kbuf = torch.zeros(ins.size + 1, dtype=torch.int64, device="cuda")
+    qbuf = torch.zeros(q.size + 1, dtype=torch.int64, device="cuda")
+    for offset in (0, 1):
+        dk, dq = kbuf[offset:offset + ins.size], qbuf[offset:offset + q.size]
+        dk.copy_(dev_keys(torch, ins))
+        dq.copy_(dev_keys(torch, q))
+        f = gpu_filter(geom, torch)
+        f.set_partition(mode=1, slice_log2=16, part_ctas=1, lookup_mode=1)
+        f.set_layout(BF_OP_CONTAINS, cg=1, phi=8, kpt=4)
+        f.add(dk)
+        assert np.array_equal(words_np(f), ref.as_bytes()), offset
+        out = f.contains(dq)
+        got = out.cpu().numpy().astype(np.uint8)
+        assert np.array_equal(got, ref_out), offset
+        assert got[is_mem == 1].all()
+        assert f.device_status() == 0
         f.close()
 
 
@@ -310,6 +379,7 @@ def test_partitioned_add_skewed_keys(torch):
     f.set_partition(mode=1, slice_log2=16)
     f.add(dev_keys(torch, ins))
     assert np.array_equal(words_np(f), ref.as_bytes())
+    assert f.device_status() == 0
     f.close()
 
 
@@ -347,6 +417,7 @@ def test_partitioned_lookup_bit_exact(torch, B, S, k):
                 got = out.cpu().numpy()
                 assert np.array_equal(got, ref_out), (cfg, cg, phi, kpt)
                 assert got[is_mem == 1].all()
+    assert f.device_status() == 0
     f.close()
 
 
@@ -364,6 +435,7 @@ def test_partition_auto_and_off(torch):
         f.set_partition(mode=1, slice_log2=8)
     with pytest.raises(Exception):
         f.set_partition(mode=1, cap_override=100)
+    assert f.device_status() == 0
     f.close()
 
 
@@ -376,6 +448,7 @@ def test_rejects_misaligned_keys_before_launch(torch):
         _lib.bf_add(f.handle, buf.data_ptr() + 4, 1)
     with pytest.raises(BloomError):
         f.set_layout(0, cg=16)
+    assert f.device_status() == 0
     f.close()
 
 
@@ -405,6 +478,7 @@ def test_l2_resident_32mib_with_and_without_persistence(torch):
             f.set_l2_persist(0.0)
         assert np.array_equal(words_np(f), ref.as_bytes())
         assert np.array_equal(out.cpu().numpy().astype(np.uint8), ref_out)
+        assert f.device_status() == 0
         f.close()
 
 
@@ -428,6 +502,7 @@ def test_hbm_resident_256mib(torch):
         out = f.contains(dq)
         assert np.array_equal(words_np(f), ref.as_bytes())
         assert np.array_equal(out.cpu().numpy().astype(np.uint8), ref_out)
+        assert f.device_status() == 0
         f.close()
 
 

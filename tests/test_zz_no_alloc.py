@@ -22,6 +22,12 @@ from conftest import gpu_available
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
 
 
+def f_status(L):
+    v = ctypes.c_uint32()
+    assert L.lib().bf_noalloc_status(ctypes.byref(v)) == L.BF_OK
+    return v.value
+
+
 @pytest.fixture(scope="module")
 def env():
     import torch
@@ -52,6 +58,7 @@ def test_noalloc_matches_bf_add_on_two_calls(env, num_blocks, B, S, k):
             assert limit.value >= n
             torch.cuda.synchronize()
             assert torch.equal(got, ref), f"bit arrays differ after call {call + 1}"
+            assert f_status(L) == 0
         assert int(got.ne(0).sum().item()) > 0
     finally:
         L.bf_destroy(h)
@@ -69,3 +76,42 @@ def test_noalloc_rejects_too_many_keys(env):
     assert 1_000_000 < limit.value < (16 << 20) // 8
     torch.cuda.synchronize()
     assert not words.any().item()  # nothing ran
+
+
+@pytest.mark.parametrize("num_blocks", [1 << 29, 1 << 15])
+def test_noalloc_at_its_limit_matches_the_oracle(env, num_blocks):
+    """The documented extremes, against the oracle: a 16 GiB filter of
+    256-bit blocks (1024 slices of 16 MiB, where the slice buffers are
+    smallest and overflow to the direct path is likeliest) and a 1 MiB
+    filter of one slice, each with two calls in a row of exactly *max_keys
+    keys.  The 16 GiB array is compared block by block: the oracle gives the
+    blocks the keys touch and their words, and every other block must be
+    zero."""
+    import oracle
+    torch, L = env
+    geom = oracle.Geometry(num_blocks=num_blocks, block_bits=256, word_bits=32, k=8, seed=0)
+    p = L.bf_params(num_blocks, 256, 32, 8, 0, 0)
+    limit = ctypes.c_uint64()
+    words = torch.zeros(num_blocks * 32, dtype=torch.uint8, device="cuda")
+    probe = torch.zeros(8, dtype=torch.int64, device="cuda")
+    rc = L.lib().bf_add_noalloc(ctypes.byref(p), words.data_ptr(), probe.data_ptr(), 1 << 40,
+                                ctypes.byref(limit), None)
+    assert rc == L.BF_EINVAL and limit.value > 1_000_000
+    n = limit.value
+    stream = torch.cuda.current_stream().cuda_stream
+    host = []
+    for seed in (201, 202):
+        keys = synthkeys.splitmix64(seed, 0, n)
+        host.append(keys)
+        dk = torch.from_numpy(keys.view(np.int64)).cuda()
+        rc = L.lib().bf_add_noalloc(ctypes.byref(p), words.data_ptr(), dk.data_ptr(), n, None, stream)
+        assert rc == L.BF_OK
+        torch.cuda.synchronize()
+        del dk
+    assert f_status(L) == 0
+    blocks, want = oracle.add_sparse(geom, np.concatenate(host))
+    w = words.view(torch.int64).view(-1, 4)
+    nz = (w != 0).any(dim=1).nonzero().squeeze(1)
+    assert np.array_equal(nz.cpu().numpy().astype(np.uint64), blocks), "touched blocks differ from the oracle's"
+    got = w[nz].cpu().numpy().view(np.uint32).reshape(-1, 8)
+    assert np.array_equal(got, want), "block contents differ from the oracle's"
