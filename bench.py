@@ -188,6 +188,61 @@ def cpu_oracle_rate(w, budget_s: float):
             "insert_gkeys_s": done_i / t_i / 1e9, "lookup_gkeys_s": done_q / t_q / 1e9}
 
 
+def _oracle_range_worker(job):
+    """One process of the all-core oracle timing: the unchanged oracle over
+    one block range of the full-size filter.  Every worker hashes the whole
+    sample (the oracle's block index) and inserts / looks up only the keys
+    whose block is in its range, so the ranges' bits are exactly the
+    oracle's; returns (insert seconds, lookup seconds)."""
+    import numpy as np
+    import oracle
+    import synthkeys
+    geom_kw, lo, hi, n_ins, n_q, n_insert_total, member_den, chunk = job
+    geom = oracle.Geometry(**geom_kw)
+    words = np.zeros((hi - lo) * geom.s, dtype=geom.word_dtype)
+    ti = tq = 0.0  # oracle time only (the input generation is not timed)
+    for c0 in range(0, n_ins, chunk):
+        keys = synthkeys.splitmix64(synthkeys.SEED_INSERT, c0, min(chunk, n_ins - c0))
+        t0 = time.perf_counter()
+        j = oracle.block_indices(keys, geom.num_blocks, geom.seed)
+        oracle.add_block_range(geom, lo, hi, keys[(j >= lo) & (j < hi)], words)
+        ti += time.perf_counter() - t0
+    for c0 in range(0, n_q, chunk):
+        q, _ = synthkeys.stream_queries(c0, min(chunk, n_q - c0), n_insert_total, member_den)
+        t0 = time.perf_counter()
+        j = oracle.block_indices(q, geom.num_blocks, geom.seed)
+        oracle.contains_block_range(geom, words, lo, hi, q[(j >= lo) & (j < hi)])
+        tq += time.perf_counter() - t0
+    return ti, tq
+
+
+def cpu_oracle_rate_all_cores(w, n_sample: int = 1 << 24):
+    """The oracle on every host core: a spawn pool with one worker per core,
+    each owning one block range of the full-size filter (the oracle's
+    construction ORs without atomics, so workers split the filter, not the
+    keys).  Throughput = sample keys / the slowest worker's time."""
+    import multiprocessing as mp
+    b, n_ins, n_q = wl_sizes(w)
+    cores = os.cpu_count() or 1
+    if w["member_den"] == 2:
+        return None  # the small workload's mixed query set is built on one host only
+    geom_kw = dict(num_blocks=b, block_bits=w["block_bits"], word_bits=w["word_bits"], k=w["k"], seed=0,
+                   salts=w.get("salts", 0))
+    ni, nq = min(n_sample, n_ins), min(n_sample, n_q)
+    step = -(-b // cores)
+    jobs = [(geom_kw, lo, min(b, lo + step), ni, nq, n_ins, w["member_den"], 1 << 22) for lo in range(0, b, step)]
+    import oracle
+    oracle.build()
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_oracle_range_worker, jobs, chunksize=1)
+    ti = max(r[0] for r in res)
+    tq = max(r[1] for r in res)
+    return {"value": (ni + nq) / (ti + tq) / 1e9, "unit": "G keys/s", "cores": len(jobs),
+            "insert_gkeys_s": ni / ti / 1e9, "lookup_gkeys_s": nq / tq / 1e9,
+            "sample": f"first {ni:,} inserts and first {nq:,} queries, the full-size filter split into "
+                      f"{len(jobs)} block ranges, one spawn worker per range (every worker hashes the whole sample)"}
+
+
 def run_reference(args, w, wname):
     """The reference arm: the CPU oracle as it stands, on the host cores."""
     world, rank, _ = dist_env()
@@ -221,7 +276,8 @@ def run_reference(args, w, wname):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
-KERNEL_SOURCES = ("sbf_kernels.cuh", "sbf_device.cuh", "salts.cuh", "sbf_partition.cuh", "sbf_expand.cu")
+KERNEL_SOURCES = ("sbf_kernels.cuh", "sbf_device.cuh", "salts.cuh", "sbf_partition.cuh", "sbf_expand.cu",
+                  "registry.h")
 
 
 def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
@@ -273,22 +329,27 @@ def gen_inputs(torch, w, device):
     return ins, qd, flags
 
 
-def gups_bounds(torch, w, ins, q, device, reps=3):
-    """Random-access bound on the filter's footprint with the same key streams."""
-    from paper_2512_15595_gb300 import BF_GUPS_LOAD, BF_GUPS_RED_OR, _lib, bf_layout
+def gups_bounds(torch, w, ins, q, device, reps=3, window_bytes=None):
+    """Random-access bound on the filter's footprint with the same key
+    streams; with window_bytes, also the full-sector OR rate (the record-insert
+    kernel's traffic) on a table of one record-insert window."""
+    from paper_2512_15595_gb300 import BF_GUPS_LOAD, BF_GUPS_RED_OR, BF_GUPS_RED_OR_SECTOR, _lib, bf_layout
     unit = max(32, w["block_bits"] // 8)
     table = torch.zeros(w["nbytes"], dtype=torch.uint8, device=device)
     gout = torch.empty(q.numel(), dtype=torch.uint8, device=device)
     stream = torch.cuda.current_stream()
     best = {}
-    for mode, name, keys in ((BF_GUPS_LOAD, "load", q), (BF_GUPS_RED_OR, "red_or", ins)):
+    runs = [(BF_GUPS_LOAD, "load", q, w["nbytes"]), (BF_GUPS_RED_OR, "red_or", ins, w["nbytes"])]
+    if window_bytes:
+        runs.append((BF_GUPS_RED_OR_SECTOR, "red_sector_window", ins, min(window_bytes, w["nbytes"])))
+    for mode, name, keys, tbytes in runs:
         for kpt in (1, 2, 4):
             lay = bf_layout(0, 0, kpt, 256, 0, 0)
             ts = []
             for i in range(reps + 1):
                 s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 s.record(stream)
-                _lib.bf_gups(mode, table.data_ptr(), table.numel(), unit, keys.data_ptr(), keys.numel(),
+                _lib.bf_gups(mode, table.data_ptr(), tbytes, unit, keys.data_ptr(), keys.numel(),
                              gout.data_ptr() if mode == BF_GUPS_LOAD else None, lay, stream)
                 e.record(stream)
                 e.synchronize()
@@ -296,7 +357,7 @@ def gups_bounds(torch, w, ins, q, device, reps=3):
                     ts.append(s.elapsed_time(e))
             g = keys.numel() / (min(ts) * 1e-3) / 1e9
             if name not in best or g > best[name]["gkeys_s"]:
-                best[name] = {"gkeys_s": g, "kpt": kpt, "unit_bytes": unit}
+                best[name] = {"gkeys_s": g, "kpt": kpt, "unit_bytes": unit, "table_bytes": tbytes}
     del table, gout
     torch.cuda.empty_cache()
     return best
@@ -321,6 +382,35 @@ def popcount_fpr(torch, words, w):
     return total / nblocks
 
 
+PHASE_KERNELS = {
+    "add_direct": "sbf_add_kernel", "contains_direct": "sbf_contains_kernel",
+    "partition_add": "sbf_partition_kernel (construction)", "record_insert": "sbf_add_records_kernel",
+    "partition_lookup": "sbf_partition_kernel (lookup)", "record_probe": "sbf_probe_records_kernel",
+    "bitmap_expand": "bitmap_expand_kernel",
+}
+
+
+def phase_bytes(phase, w, n_ins, n_q, part):
+    """Algorithmic DRAM bytes of one call's launches of one kernel: 8-byte
+    keys and records, 4-byte query indexes, 1-byte results, and the filter's
+    blocks -- for the direct kernels one random sector access per key (read
+    and written back for construction), for the windowed kernels every
+    window's blocks read (and written back) once per pass."""
+    fb = w["nbytes"]
+    sectors = max(1, w["block_bits"] // 256)
+    add_passes = -(-n_ins // max(1, part["chunk_keys"]))
+    look_passes = -(-n_q // max(1, part["lookup_chunk_keys"]))
+    return {
+        "add_direct": n_ins * (8 + 64 * sectors),
+        "contains_direct": n_q * (8 + 32 * sectors + 1),
+        "partition_add": n_ins * (8 + 8),
+        "record_insert": n_ins * 8 + 2 * fb * add_passes,
+        "partition_lookup": n_q * (8 + 12),
+        "record_probe": n_q * 12 + fb * look_passes,
+        "bitmap_expand": n_q // 8 + n_q,
+    }[phase]
+
+
 def run_ours(args, w, wname):
     import torch
     world, rank, local = dist_env()
@@ -340,7 +430,12 @@ def run_ours(args, w, wname):
     out = torch.empty(n_q, dtype=torch.uint8, device=device)
     stream = torch.cuda.current_stream()
 
-    bounds = gups_bounds(torch, w, ins, qd, device) if not args.no_gups else None
+    part0 = f.partition()
+    bounds = (gups_bounds(torch, w, ins, qd, device,
+                          window_bytes=(1 << part0["window_log2"]) if regime == "hbm" else None)
+              if not args.no_gups else None)
+    if args.l2_persist > 0:
+        f.set_l2_persist(args.l2_persist)
 
     launches = []
     launches_add, launches_con = [], []
@@ -369,6 +464,7 @@ def run_ours(args, w, wname):
     sampler.start()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    f.set_timing(True)  # per-kernel CUDA events on the launching streams, read after the region
     t_start.record(stream)
     for i in range(args.steps):
         step(evs[i])
@@ -376,6 +472,10 @@ def run_ours(args, w, wname):
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
+    phase_tm = f.timing()
+    f.set_timing(False)
+    if args.l2_persist > 0:
+        f.set_l2_persist(0.0)
     local_ms = t_start.elapsed_time(t_end)
     total_ms = max_over_ranks(local_ms, world, device)
     add_ms = statistics.median(e[0].elapsed_time(e[1]) for e in evs)
@@ -392,36 +492,66 @@ def run_ours(args, w, wname):
     missed = int((out[flags == 1] == 0).sum().item())
     realized_fpr = popcount_fpr(torch, f.words, w)
 
-    # roofline of the dominant operation, per call (one call = one launch of
-    # the direct kernel, or the partition + windowed kernels of the
-    # slice-partitioned path); algorithmic bytes per key: key + random sector
-    # read-modify-write (construction) or key + sector read + result (lookup)
-    sectors = max(1, w["block_bits"] // 256)
-    bytes_add = 8 + 2 * 32 * sectors
-    bytes_con = 8 + 32 * sectors + 1
-    dominant = "add" if add_ms >= con_ms else "contains"
-    per_key = bytes_add if dominant == "add" else bytes_con
-    dur = add_ms if dominant == "add" else con_ms
-    n_dom = n_ins if dominant == "add" else n_q
-    achieved = per_key * n_dom / (dur * 1e-3) / 1e9
+    # per-kernel device time of the timed steps (events around each group of
+    # launches, on the stream it runs on)
     peak, peak_kind = peaks()
     part = f.partition()
-    if dominant == "add":
-        desc = ("bf_add: sbf_partition_kernel + sbf_add_records_kernel (windowed)" if launches_add[-1] > 1
-                else "bf_add: sbf_add_kernel")
-    else:
-        desc = ("bf_contains: sbf_partition_kernel + sbf_probe_records_kernel + bitmap_expand_kernel"
-                if launches_con[-1] > 1 else "bf_contains: sbf_contains_kernel")
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": measured_traffic(dominant, wname), "kernel": desc, "per": "one call",
+    steps = args.steps
+    kern_ms = sum(v["ms"] for v in phase_tm.values()) or 1.0
+    kernels = {}
+    for ph, v in phase_tm.items():
+        nb = phase_bytes(ph, w, n_ins, n_q, part)
+        lpc = v["launches"] / steps
+        avg = v["ms"] / max(1, v["launches"])
+        kernels[ph] = {"kernel": PHASE_KERNELS[ph], "ms_per_step": v["ms"] / steps, "launches_per_step": lpc,
+                       "share": v["ms"] / kern_ms, "avg_launch_ms": avg,
+                       "algorithmic_bytes_per_launch": nb / lpc,
+                       "achieved_gbs": nb / lpc / (avg * 1e-3) / 1e9}
+    # roofline of the dominant kernel (largest share of the step)
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    kd = kernels[dom]
+    roof = {"bound": "hbm", "kernel": kd["kernel"], "achieved": kd["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": kd["achieved_gbs"] / peak,
+            "traffic": measured_traffic(dom, wname), "per": "one launch",
+            "algorithmic_bytes_per_launch": kd["algorithmic_bytes_per_launch"], "avg_launch_ms": kd["avg_launch_ms"],
+            "launches_per_step": kd["launches_per_step"], "share_of_kernel_time": kd["share"],
             "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)",
-            "algorithmic_bytes_per_key": per_key, "keys_per_call": n_dom, "ms_per_call": dur}
+            "algorithmic_bytes": {
+                "record_insert": "8 B per record + the window's blocks read and written back once",
+                "partition_add": "8 B key read + 8 B record written per key",
+                "add_direct": "8 B key + one random 32 B sector read and written back per key",
+            }.get(dom, "see phase_bytes() in bench.py")}
+    if roof["traffic"]:
+        roof["traffic_over_algorithmic"] = roof["traffic"] / kd["algorithmic_bytes_per_launch"]
+    if dom == "record_insert" and bounds and "red_sector_window" in bounds:
+        rb = bounds["red_sector_window"]
+        rec_s = n_ins / (kd["ms_per_step"] * 1e-3) / 1e9
+        roof["limit"] = {"what": "SM-to-L2 red path: one full 32-byte sector OR per record",
+                         "achieved_grecords_s": rec_s, "bound_grecords_s": rb["gkeys_s"],
+                         "frac": rec_s / rb["gkeys_s"],
+                         "how": f"bf_gups full-sector red.or (4 lanes x 64 bit) on a {rb['table_bytes'] >> 20} MiB "
+                                f"table (one window) with the insert key stream, best kpt"}
+    # whole operations: the random-access formulation (key + sector access per
+    # key; the slice-partitioned path replaces it by streaming, so this is an
+    # equivalent rate) next to the measured DRAM traffic of one call
+    sectors = max(1, w["block_bits"] // 256)
+    ops = {}
+    for op, ms_, n_, bpk in (("add", add_ms, n_ins, 8 + 64 * sectors), ("contains", con_ms, n_q, 9 + 32 * sectors)):
+        t = measured_traffic(op, wname)
+        ops[op] = {"ms_per_call": ms_, "random_access_bytes_per_key": bpk,
+                   "random_access_equivalent_frac": bpk * n_ / (ms_ * 1e-3) / 1e9 / peak,
+                   "traffic_per_call": t,
+                   "achieved_traffic_frac": (t / (ms_ * 1e-3) / 1e9 / peak) if t else None}
+    roof["operations"] = ops
     ra = None
     if bounds:
         ra = {"lookup_bound_gkeys_s": bounds["load"]["gkeys_s"], "insert_bound_gkeys_s": bounds["red_or"]["gkeys_s"],
               "lookup_frac": look_g / bounds["load"]["gkeys_s"], "insert_frac": ins_g / bounds["red_or"]["gkeys_s"],
               "unit_bytes": bounds["load"]["unit_bytes"], "how": "bf_gups: same key streams, same footprint, "
               "random unit loads (lookup) / red.or (insert), best kpt"}
+        if "red_sector_window" in bounds:
+            ra["window_full_sector_red_gkeys_s"] = bounds["red_sector_window"]["gkeys_s"]
+    status = f.device_status()
 
     e2e = None
     if not args.no_e2e:
@@ -435,7 +565,10 @@ def run_ours(args, w, wname):
         cpu = {"value": r["gkeys_s"], "unit": "G keys/s", "cores": 1, "kind": "oracle",
                "sample": f"first {r['insert_keys']:,} inserts into the full-size host filter and first "
                          f"{r['lookup_keys']:,} queries ({r['insert_s'] + r['lookup_s']:.1f} s single-thread)",
-               "insert_gkeys_s": r["insert_gkeys_s"], "lookup_gkeys_s": r["lookup_gkeys_s"]}
+               "insert_gkeys_s": r["insert_gkeys_s"], "lookup_gkeys_s": r["lookup_gkeys_s"],
+               "host_cores": os.cpu_count()}
+        if not args.no_cpu_all_cores:
+            cpu["all_cores"] = cpu_oracle_rate_all_cores(w)
 
     if rank == 0:
         line = {
@@ -454,8 +587,9 @@ def run_ours(args, w, wname):
             "random_access_bound": ra,
             "fpr": {"bits_per_key": w["nbytes"] * 8 / n_ins, "measured": measured_fpr,
                     "realized_filter": realized_fpr, "fresh_queries": n_fresh, "false_negatives": missed},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": sum(launches), "clocks": clocks,
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": sum(launches), "clocks": clocks, "device_status": status,
+            "l2_persist": args.l2_persist if args.l2_persist > 0 else None,
         }
         print(json.dumps(line), flush=True)
     f.close()
@@ -1172,6 +1306,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-gups", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", action="store_true", help="skip the all-core oracle timing")
+    ap.add_argument("--l2-persist", type=float, default=0.0,
+                    help="L2 persistence window over the filter with this hit ratio during the timed steps")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.warmup < 3:

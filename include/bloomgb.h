@@ -101,11 +101,18 @@ typedef enum { BF_OP_ADD = 0, BF_OP_CONTAINS = 1 } bf_op;
 enum {
     BF_HINT_FILTER_EVICT_LAST = 1u << 0,   /* filter accesses carry an L2 evict_last policy */
     BF_HINT_KEYS_EVICT_NORMAL = 1u << 1,   /* keys load with evict_normal instead of evict_first */
-    BF_HINT_PREFETCH_L2 = 1u << 2          /* batched kernels only (others ignore it): while a warp
+    BF_HINT_PREFETCH_L2 = 1u << 2,         /* batched kernels only (others ignore it): while a warp
                                               works on a key chunk, it bulk-prefetches into L2 the
                                               share of its filter's bit array that belongs to the
                                               chunk one grid-stride step ahead, so that filters
                                               are streamed into L2 before their keys arrive */
+    BF_HINT_WARP_AGGREGATE = 1u << 3       /* construction (direct, record-insert and batched
+                                              kernels; lookups ignore it): a key equal to the key
+                                              before it in the warp's tile of keys (or, in the
+                                              record-insert kernel, a record equal to the one
+                                              before it) issues no atomics -- it sets the same
+                                              bits -- so a run of repeated keys costs one update;
+                                              the bits are those without the hint */
 };
 
 /* Execution layout of one operation (Sec. IV-A, IV-C).
@@ -265,6 +272,32 @@ bf_status bf_get_partition(const bf_filter* f, bf_partition* out);
    clears them. */
 bf_status bf_device_status(bf_filter* f, bf_stream_t stream, uint32_t* codes);
 
+/* Per-phase device time (a measurement aid).  After bf_set_timing(f, 1),
+   every bf_add / bf_contains / host-buffer call records a CUDA event before
+   and after each group of launches of one kind, on the stream that group
+   runs on.  bf_get_timing waits for those events and returns, per phase, the
+   summed duration of the groups recorded since the previous bf_get_timing (or
+   bf_set_timing) in milliseconds and their number of launches, then starts a
+   new sum.  Phases of the overlapped construction schedule run concurrently,
+   so their sums may exceed the calls' duration.  Timing costs two event
+   records per group; bf_set_timing(f, 0) turns it off. */
+enum {
+    BF_PHASE_ADD_DIRECT = 0,        /* sbf_add_kernel (and the CSBF construction kernel) */
+    BF_PHASE_CONTAINS_DIRECT = 1,   /* sbf_contains_kernel (and the CSBF lookup kernel) */
+    BF_PHASE_PARTITION_ADD = 2,     /* slice partition of construction keys */
+    BF_PHASE_RECORD_INSERT = 3,     /* record inserts, one launch per window */
+    BF_PHASE_PARTITION_LOOKUP = 4,  /* slice partition of lookup queries */
+    BF_PHASE_RECORD_PROBE = 5,      /* record probes, one launch per window */
+    BF_PHASE_BITMAP_EXPAND = 6,     /* result bitmap to result bytes */
+    BF_PHASES = 8
+};
+typedef struct {
+    float ms[BF_PHASES];
+    uint32_t launches[BF_PHASES];
+} bf_timing;
+bf_status bf_set_timing(bf_filter* f, int enable);
+bf_status bf_get_timing(bf_filter* f, bf_timing* out);
+
 /* Kernel launches made by the last bf_add / bf_contains / bf_add_host /
    bf_contains_host call on this filter (1 for a direct call; per pass of a
    partitioned construction, one partition launch plus one record-insert
@@ -279,10 +312,14 @@ bf_status bf_last_launches(const bf_filter* f, uint32_t* n);
                           load when unit_bytes = 8), fold them to one byte and
                           store it to d_out[i];
      mode BF_GUPS_RED_OR: one red.global.or of a 32-bit value derived from
-                          d_keys[i] into each 32-byte sector of unit u.
+                          d_keys[i] into each 32-byte sector of unit u;
+     mode BF_GUPS_RED_OR_SECTOR: the record-insert kernel's traffic: each
+                          32-byte sector of unit u receives four 64-bit
+                          red.global.or (from four lanes, one instruction),
+                          i.e. one full-width update of its eight 32-bit words.
    unit_bytes in {8, 32, 64, 128}; d_table aligned to unit_bytes; layout uses
    kpt, block_threads and grid_ctas (cg/phi ignored). */
-typedef enum { BF_GUPS_LOAD = 0, BF_GUPS_RED_OR = 1 } bf_gups_mode;
+typedef enum { BF_GUPS_LOAD = 0, BF_GUPS_RED_OR = 1, BF_GUPS_RED_OR_SECTOR = 2 } bf_gups_mode;
 bf_status bf_gups(int mode, void* d_table, uint64_t table_bytes, uint32_t unit_bytes,
                   const uint64_t* d_keys, uint64_t n, uint8_t* d_out, const bf_layout* layout,
                   bf_stream_t stream);

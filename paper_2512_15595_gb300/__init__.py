@@ -8,12 +8,14 @@ wrapper over the ``bf_*`` functions for torch tensors.
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (BF_GUPS_LOAD, BF_GUPS_RED_OR, BF_HINT_FILTER_EVICT_LAST, BF_HINT_KEYS_EVICT_NORMAL,
-                   BF_HINT_PREFETCH_L2, BF_OP_ADD, BF_OP_CONTAINS, BloomError, bf_layout, bf_params)
+from ._lib import (BF_GUPS_LOAD, BF_GUPS_RED_OR, BF_GUPS_RED_OR_SECTOR, BF_HINT_FILTER_EVICT_LAST, BF_HINT_KEYS_EVICT_NORMAL,
+                   BF_HINT_PREFETCH_L2, BF_HINT_WARP_AGGREGATE, BF_OP_ADD, BF_OP_CONTAINS, BloomError, bf_layout,
+                   bf_params)
 
 __all__ = ["Filter", "BloomError", "bf_params", "bf_layout", "BF_OP_ADD", "BF_OP_CONTAINS",
-           "BF_HINT_FILTER_EVICT_LAST", "BF_HINT_KEYS_EVICT_NORMAL", "BF_HINT_PREFETCH_L2", "BF_GUPS_LOAD",
-           "BF_GUPS_RED_OR",
+           "BF_HINT_FILTER_EVICT_LAST", "BF_HINT_KEYS_EVICT_NORMAL", "BF_HINT_PREFETCH_L2", "BF_HINT_WARP_AGGREGATE",
+           "BF_GUPS_LOAD",
+           "BF_GUPS_RED_OR", "BF_GUPS_RED_OR_SECTOR",
            "valid_layouts", "device_tensor", "Batch"]
 
 
@@ -123,6 +125,14 @@ class Filter:
 
     def partition(self) -> dict:
         return _lib.bf_get_partition(self.handle).as_dict()
+
+    def set_timing(self, enable: bool = True) -> None:
+        """Record per-phase device times of every call (bf_set_timing)."""
+        _lib.bf_set_timing(self.handle, enable)
+
+    def timing(self) -> dict:
+        """Per-phase device time (ms) and launches since the last read."""
+        return _lib.bf_get_timing(self.handle)
 
     def device_status(self, stream=None) -> int:
         """Bits of failed index checks in the slice-partitioned kernels since

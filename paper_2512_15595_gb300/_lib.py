@@ -18,7 +18,8 @@ BF_OP_ADD, BF_OP_CONTAINS = 0, 1
 BF_HINT_FILTER_EVICT_LAST = 1 << 0
 BF_HINT_KEYS_EVICT_NORMAL = 1 << 1
 BF_HINT_PREFETCH_L2 = 1 << 2
-BF_GUPS_LOAD, BF_GUPS_RED_OR = 0, 1
+BF_HINT_WARP_AGGREGATE = 1 << 3
+BF_GUPS_LOAD, BF_GUPS_RED_OR, BF_GUPS_RED_OR_SECTOR = 0, 1, 2
 BF_HOST_AUTO, BF_HOST_STAGED = 0, 1
 
 # every symbol include/bloomgb.h declares
@@ -26,7 +27,8 @@ EXPORTED = (
     "bf_params_check", "bf_layout_check", "bf_create", "bf_destroy", "bf_clear", "bf_add",
     "bf_contains", "bf_add_host", "bf_contains_host", "bf_set_staging", "bf_words",
     "bf_get_params", "bf_set_layout", "bf_get_layout", "bf_set_l2_persist", "bf_gups",
-    "bf_set_partition", "bf_get_partition", "bf_last_launches", "bf_add_noalloc", "bf_noalloc_status", "bf_device_status", "bf_batch_create",
+    "bf_set_partition", "bf_get_partition", "bf_last_launches", "bf_set_timing", "bf_get_timing",
+    "bf_device_status", "bf_add_noalloc", "bf_noalloc_status", "bf_batch_create",
     "bf_batch_destroy", "bf_batch_set_layout", "bf_batch_get_layout", "bf_batch_add", "bf_batch_contains",
     "bf_batch_info", "bf_server_create", "bf_server_destroy", "bf_server_submit", "bf_server_wait",
     "bf_server_get_stats", "bf_server_run_poisson", "bf_mlp_workspace_bytes", "bf_mlp_grad", "bf_mlp_adam",
@@ -69,6 +71,19 @@ class bf_partition(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+BF_PHASES = 8
+PHASE_NAMES = ("add_direct", "contains_direct", "partition_add", "record_insert", "partition_lookup",
+               "record_probe", "bitmap_expand")
+
+
+class bf_timing(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_float * BF_PHASES), ("launches", ctypes.c_uint32 * BF_PHASES)]
+
+    def as_dict(self):
+        return {name: {"ms": self.ms[i], "launches": self.launches[i]}
+                for i, name in enumerate(PHASE_NAMES) if self.launches[i]}
 
 
 class bf_batch_filter(ctypes.Structure):
@@ -132,6 +147,8 @@ def lib():
         "bf_gups": (i32, [i32, vp, u64, u32, vp, u64, vp, LY, vp]),
         "bf_set_partition": (i32, [vp, ctypes.POINTER(bf_partition)]),
         "bf_device_status": (i32, [vp, vp, ctypes.POINTER(ctypes.c_uint32)]),
+        "bf_set_timing": (i32, [vp, ctypes.c_int]),
+        "bf_get_timing": (i32, [vp, ctypes.POINTER(bf_timing)]),
         "bf_noalloc_status": (i32, [ctypes.POINTER(ctypes.c_uint32)]),
         "bf_get_partition": (i32, [vp, ctypes.POINTER(bf_partition)]),
         "bf_last_launches": (i32, [vp, ctypes.POINTER(u32)]),
@@ -280,6 +297,17 @@ def bf_device_status(f: int, stream=None) -> int:
     v = ctypes.c_uint32()
     _check(lib().bf_device_status(f, _stream(stream), ctypes.byref(v)), "bf_device_status")
     return v.value
+
+
+def bf_set_timing(f: int, enable: bool) -> None:
+    _check(lib().bf_set_timing(f, int(bool(enable))), "bf_set_timing")
+
+
+def bf_get_timing(f: int) -> dict:
+    """Per-phase device time (ms) and launch count since the last read."""
+    out = bf_timing()
+    _check(lib().bf_get_timing(f, ctypes.byref(out)), "bf_get_timing")
+    return out.as_dict()
 
 
 def bf_get_partition(f: int) -> bf_partition:

@@ -201,6 +201,17 @@ struct bf_filter {
   uint64_t l2_bytes = 0;
   uint32_t last_launches = 0;
   uint32_t* status = nullptr;  // device word: kStatus* bits of failed index checks
+  // per-phase timing of the last call (bf_set_timing): event pairs around
+  // each group of launches, on the stream the group runs on
+  struct Seg {
+    int phase;
+    cudaEvent_t a, b;
+    uint32_t launches;
+  };
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<Seg> segs;
 };
 
 namespace {
@@ -282,7 +293,7 @@ bf_status resolve_layout(const bf_params& p, int op, const bf_layout* in, bf_lay
   if (l.kpt != 1 && l.kpt != 2 && l.kpt != 4) return fail(BF_EINVAL, "kpt must be 1, 2 or 4");
   if (l.block_threads % 32 != 0 || l.block_threads > static_cast<uint32_t>(kMaxBlockThreadsHost))
     return fail(BF_EINVAL, "block_threads must be a multiple of 32 and <= 512");
-  if (l.flags & ~(BF_HINT_FILTER_EVICT_LAST | BF_HINT_KEYS_EVICT_NORMAL | BF_HINT_PREFETCH_L2))
+  if (l.flags & ~(BF_HINT_FILTER_EVICT_LAST | BF_HINT_KEYS_EVICT_NORMAL | BF_HINT_PREFETCH_L2 | BF_HINT_WARP_AGGREGATE))
     return fail(BF_EINVAL, "unknown layout flag");
   const KernelEntry* e = z ? find_csbf(op == BF_OP_ADD ? 9 : 10, p, l, z) : find_sbf(op, p, l);
   if (!e) return fail(BF_EUNSUPPORTED, "no compiled kernel for this geometry and layout");
@@ -290,6 +301,44 @@ bf_status resolve_layout(const bf_params& p, int op, const bf_layout* in, bf_lay
   if (entry) *entry = e;
   return BF_OK;
 }
+
+// Phase timing: phase_begin records an event before a group of launches,
+// phase_end one after it (same stream) and keeps the pair for bf_get_timing.
+struct PhaseMark {
+  int phase = -1;
+  cudaEvent_t a = nullptr;
+};
+
+cudaEvent_t pool_event(bf_filter* f) {
+  if (f->ev_used == f->ev_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    f->ev_pool.push_back(e);
+  }
+  return f->ev_pool[f->ev_used++];
+}
+
+PhaseMark phase_begin(const bf_filter* fc, cudaStream_t s, int phase) {
+  bf_filter* f = const_cast<bf_filter*>(fc);
+  PhaseMark m;
+  if (!f->timing) return m;
+  m.a = pool_event(f);
+  if (m.a && cudaEventRecord(m.a, s) == cudaSuccess) m.phase = phase;
+  return m;
+}
+
+void phase_end(const bf_filter* fc, cudaStream_t s, const PhaseMark& m, uint32_t launches) {
+  bf_filter* f = const_cast<bf_filter*>(fc);
+  if (m.phase < 0) return;
+  cudaEvent_t b = pool_event(f);
+  if (b && cudaEventRecord(b, s) == cudaSuccess) f->segs.push_back({m.phase, m.a, b, launches});
+}
+
+// a new call: count its launches from zero (timing marks accumulate until read)
+void begin_call(const bf_filter* fc) { const_cast<bf_filter*>(fc)->last_launches = 0; }
 
 bf_status launch_sbf(const bf_filter* f, int op, const uint64_t* keys, uint64_t n, uint8_t* out,
                      cudaStream_t stream) {
@@ -303,8 +352,10 @@ bf_status launch_sbf(const bf_filter* f, int op, const uint64_t* keys, uint64_t 
   SbfArgs a{f->words, f->p.num_blocks, keys, n, out, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, l.flags,
             f->p.num_blocks < (1ull << 32) ? 0 : (f->p.num_blocks == (1ull << 32) ? 1 : 2)};
   void* args[] = {&a};
+  const PhaseMark pm = phase_begin(f, stream, op == BF_OP_ADD ? BF_PHASE_ADD_DIRECT : BF_PHASE_CONTAINS_DIRECT);
   cudaError_t err = cudaLaunchKernel(e->fn, dim3(grid), dim3(l.block_threads), args, 0, stream);
   if (err != cudaSuccess) return cuda_fail(err, op == BF_OP_ADD ? "launch add kernel" : "launch contains kernel");
+  phase_end(f, stream, pm, 1);
   const_cast<bf_filter*>(f)->last_launches += 1;
   return BF_OK;
 }
@@ -434,8 +485,10 @@ bf_status launch_partition_pass(bf_filter* f, const PartLaunch& L, const PartPla
   const uint64_t tiles = (cnt + part_tile(false) - 1) / part_tile(false);
   const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, L.max_grid));
   void* pargs[] = {&pa};
+  const PhaseMark pm = phase_begin(f, stream, BF_PHASE_PARTITION_ADD);
   if ((e = cudaLaunchKernel(L.pe->fn, dim3(grid), dim3(kPartThreads), pargs, L.smem, stream)) != cudaSuccess)
     return cuda_fail(e, "launch partition kernel");
+  phase_end(f, stream, pm, 1);
   f->last_launches += 1;
   return BF_OK;
 }
@@ -444,7 +497,9 @@ bf_status launch_partition_pass(bf_filter* f, const PartLaunch& L, const PartPla
 bf_status launch_record_windows(bf_filter* f, const PartLaunch& L, const PartPlan& pl, const uint64_t* records,
                                 const unsigned long long* counts, uint64_t cap, cudaStream_t stream) {
   const bf_layout& l = f->layout[BF_OP_ADD];
-  for (uint32_t plo = 0; plo < pl.nparts; plo += L.per_launch) {
+  const PhaseMark pm = phase_begin(f, stream, BF_PHASE_RECORD_INSERT);
+  uint32_t nl = 0;
+  for (uint32_t plo = 0; plo < pl.nparts; plo += L.per_launch, ++nl) {
     const uint32_t phi = std::min(pl.nparts, plo + L.per_launch);
     RecArgs ra{f->words, records, counts, plo, phi, cap, l.flags, f->p.num_blocks, f->status};
     uint32_t rgrid = 0;
@@ -455,6 +510,7 @@ bf_status launch_record_windows(bf_filter* f, const PartLaunch& L, const PartPla
     if (e != cudaSuccess) return cuda_fail(e, "launch record-insert kernel");
     f->last_launches += 1;
   }
+  phase_end(f, stream, pm, nl);
   return BF_OK;
 }
 
@@ -618,10 +674,14 @@ bf_status launch_contains_partitioned(const bf_filter* fc, const uint64_t* keys,
     const uint64_t tiles = (cnt + part_tile(true) - 1) / part_tile(true);
     const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, static_cast<uint64_t>(sms) * per_sm));
     void* pargs[] = {&pa};
+    PhaseMark pm = phase_begin(f, stream, BF_PHASE_PARTITION_LOOKUP);
     if ((e = cudaLaunchKernel(pe->fn, dim3(grid), dim3(kPartThreads), pargs, smem, stream)) != cudaSuccess)
       return cuda_fail(e, "launch partition kernel (lookup)");
+    phase_end(f, stream, pm, 1);
     f->last_launches += 1;
-    for (uint32_t plo = 0; plo < pl.nparts; plo += per_launch) {
+    pm = phase_begin(f, stream, BF_PHASE_RECORD_PROBE);
+    uint32_t nl = 0;
+    for (uint32_t plo = 0; plo < pl.nparts; plo += per_launch, ++nl) {
       const uint32_t phi = std::min(pl.nparts, plo + per_launch);
       ProbeArgs qa{f->words, records, idx, counts, plo, phi, cap, bitmap, l.flags, f->p.num_blocks, f->status};
       uint32_t qgrid = 0;
@@ -633,12 +693,15 @@ bf_status launch_contains_partitioned(const bf_filter* fc, const uint64_t* keys,
         return cuda_fail(e, "launch record-probe kernel");
       f->last_launches += 1;
     }
+    phase_end(f, stream, pm, nl);
     ExpandArgs xa{bitmap, cnt, out + lo};
     const uint64_t words = (cnt + 31) / 32;
     const uint32_t xgrid = static_cast<uint32_t>(std::min<uint64_t>((words + 255) / 256, static_cast<uint64_t>(sms) * 8));
     void* xargs[] = {&xa};
+    pm = phase_begin(f, stream, BF_PHASE_BITMAP_EXPAND);
     if ((e = cudaLaunchKernel(xe->fn, dim3(xgrid), dim3(256), xargs, 0, stream)) != cudaSuccess)
       return cuda_fail(e, "launch bitmap expansion");
+    phase_end(f, stream, pm, 1);
     f->last_launches += 1;
   }
   return BF_OK;
@@ -831,6 +894,7 @@ bf_status bf_destroy(bf_filter* f) {
   if (f->part_ws) cudaFree(f->part_ws);
   if (f->look_ws) cudaFree(f->look_ws);
   if (f->status) cudaFree(f->status);
+  for (cudaEvent_t e : f->ev_pool) cudaEventDestroy(e);
   if (f->owned && f->words) cudaFree(f->words);
   delete f;
   return BF_OK;
@@ -849,7 +913,7 @@ bf_status bf_add(bf_filter* f, const uint64_t* d_keys, uint64_t n, bf_stream_t s
   if (!d_keys) return fail(BF_EINVAL, "keys is NULL");
   if (reinterpret_cast<uintptr_t>(d_keys) % 8) return fail(BF_EINVAL, "keys must be 8-byte aligned");
   DeviceGuard g(f->device);
-  f->last_launches = 0;
+  begin_call(f);
   return run_add(f, d_keys, n, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -860,7 +924,7 @@ bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, ui
   if (!d_keys || !d_out) return fail(BF_EINVAL, "keys or out is NULL");
   if (reinterpret_cast<uintptr_t>(d_keys) % 8) return fail(BF_EINVAL, "keys must be 8-byte aligned");
   DeviceGuard g(f->device);
-  const_cast<bf_filter*>(f)->last_launches = 0;
+  begin_call(f);
   return run_contains(f, d_keys, n, d_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -869,7 +933,7 @@ bf_status bf_add_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, bf_strea
   if (n == 0) return BF_OK;
   if (!h_keys) return fail(BF_EINVAL, "keys is NULL");
   DeviceGuard g(f->device);
-  f->last_launches = 0;
+  begin_call(f);
   return host_pipeline(f, BF_OP_ADD, h_keys, n, nullptr, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -879,7 +943,7 @@ bf_status bf_contains_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, uin
   if (n == 0) return BF_OK;
   if (!h_keys || !h_out) return fail(BF_EINVAL, "keys or out is NULL");
   DeviceGuard g(f->device);
-  f->last_launches = 0;
+  begin_call(f);
   return host_pipeline(f, BF_OP_CONTAINS, h_keys, n, h_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -967,7 +1031,9 @@ bf_status bf_set_l2_persist(bf_filter* f, bf_stream_t stream, float hit_ratio) {
 
 bf_status bf_gups(int mode, void* d_table, uint64_t table_bytes, uint32_t unit_bytes, const uint64_t* d_keys,
                   uint64_t n, uint8_t* d_out, const bf_layout* layout, bf_stream_t stream) {
-  if (mode != BF_GUPS_LOAD && mode != BF_GUPS_RED_OR) return fail(BF_EINVAL, "bad mode");
+  if (mode != BF_GUPS_LOAD && mode != BF_GUPS_RED_OR && mode != BF_GUPS_RED_OR_SECTOR)
+    return fail(BF_EINVAL, "bad mode");
+  if (mode == BF_GUPS_RED_OR_SECTOR && unit_bytes < 32) return fail(BF_EINVAL, "full-sector mode needs unit_bytes >= 32");
   if (unit_bytes != 8 && unit_bytes != 32 && unit_bytes != 64 && unit_bytes != 128)
     return fail(BF_EINVAL, "unit_bytes must be 8, 32, 64 or 128");
   if (!d_table || table_bytes < unit_bytes) return fail(BF_EINVAL, "table too small");
@@ -1036,6 +1102,31 @@ bf_status bf_device_status(bf_filter* f, bf_stream_t stream, uint32_t* codes) {
     return cuda_fail(e, "cudaMemcpy(status)");
   if (v && (e = cudaMemset(f->status, 0, sizeof v)) != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
   *codes = v;
+  return BF_OK;
+}
+
+bf_status bf_set_timing(bf_filter* f, int enable) {
+  if (!f) return fail(BF_EINVAL, "filter is NULL");
+  f->timing = enable != 0;
+  f->segs.clear();
+  f->ev_used = 0;
+  return BF_OK;
+}
+
+bf_status bf_get_timing(bf_filter* f, bf_timing* out) {
+  if (!f || !out) return fail(BF_EINVAL, "NULL argument");
+  std::memset(out, 0, sizeof *out);
+  DeviceGuard g(f->device);
+  for (const auto& sg : f->segs) {
+    cudaError_t e = cudaEventSynchronize(sg.b);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, sg.a, sg.b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    out->ms[sg.phase] += ms;
+    out->launches[sg.phase] += sg.launches;
+  }
+  f->segs.clear();
+  f->ev_used = 0;
   return BF_OK;
 }
 

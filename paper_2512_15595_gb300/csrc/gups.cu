@@ -5,7 +5,10 @@
 // traffic without their arithmetic: the same 8-byte key stream, the same
 // multiply-shift unit selection (applied to the raw key instead of its hash),
 // the same wide loads / fire-and-forget atomics, and for loads the same
-// one-byte-per-key result stream.
+// one-byte-per-key result stream.  MODE 0: loads of the unit; MODE 1: one
+// 32-bit red.or per 32-byte sector of the unit; MODE 2: the record-insert
+// kernel's traffic, four lanes per key each ORing 64 bits, so every 32-byte
+// sector of the unit receives one full-width update (its 8 words).
 #include <cstdint>
 #include <vector>
 
@@ -14,8 +17,9 @@
 
 namespace bloomgb {
 
-template <int UNIT, int KPT, bool RED>
+template <int UNIT, int KPT, int MODE>
 __global__ void __launch_bounds__(kMaxBlockThreads) gups_kernel(const GupsArgs a) {
+  constexpr bool RED = MODE == 1;
   static_assert(UNIT == 8 || UNIT % 32 == 0, "unit");
   constexpr int kSectors = UNIT >= 32 ? UNIT / 32 : 1;
   const uint32_t lane = threadIdx.x & 31u;
@@ -34,7 +38,26 @@ __global__ void __launch_bounds__(kMaxBlockThreads) gups_kernel(const GupsArgs a
     uint64_t unit[KPT];
 #pragma unroll
     for (int u = 0; u < KPT; ++u) unit[u] = ((valid >> u) & 1u) ? block_of(key[u], a.nunits, a.unit_mode) : 0;
-    if constexpr (RED) {
+    if constexpr (MODE == 2) {
+      // lane r of each group of four lanes ORs 64-bit word r of every sector
+      // of the group members' units (the Theta = 4, Phi = 2 insert layout)
+      uint64_t* t = static_cast<uint64_t*>(a.table);
+      const uint32_t r = lane & 3u;
+#pragma unroll
+      for (int u = 0; u < KPT; ++u) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const uint64_t km = __shfl_sync(0xFFFFFFFFu, key[u], m, 4);
+          const uint64_t um = __shfl_sync(0xFFFFFFFFu, unit[u], m, 4);
+          const uint32_t vm = __shfl_sync(0xFFFFFFFFu, valid, m, 4);
+          if ((vm >> u) & 1u) {
+            const uint64_t bits = (1ull << (km >> 58)) | (1ull << ((km >> 52) & 63u));
+#pragma unroll
+            for (int c = 0; c < kSectors; ++c) red_or(t + um * (UNIT / 8) + c * 4 + r, bits, pol_tab);
+          }
+        }
+      }
+    } else if constexpr (RED) {
       uint32_t* t = static_cast<uint32_t*>(a.table);
 #pragma unroll
       for (int u = 0; u < KPT; ++u) {
@@ -86,8 +109,9 @@ template <int UNIT>
 void register_gups_unit(std::vector<GupsEntry>& v) {
   host_static_for<3>([&](auto lk) {
     constexpr int KPT = 1 << decltype(lk)::value;
-    v.push_back({0, UNIT, KPT, reinterpret_cast<const void*>(&gups_kernel<UNIT, KPT, false>)});
-    v.push_back({1, UNIT, KPT, reinterpret_cast<const void*>(&gups_kernel<UNIT, KPT, true>)});
+    v.push_back({0, UNIT, KPT, reinterpret_cast<const void*>(&gups_kernel<UNIT, KPT, 0>)});
+    v.push_back({1, UNIT, KPT, reinterpret_cast<const void*>(&gups_kernel<UNIT, KPT, 1>)});
+    if constexpr (UNIT >= 32) v.push_back({2, UNIT, KPT, reinterpret_cast<const void*>(&gups_kernel<UNIT, KPT, 2>)});
   });
 }
 

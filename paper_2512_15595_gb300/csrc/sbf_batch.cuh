@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_batch_kernel(const Batch
 #pragma unroll 1
     for (uint64_t tb = first; tb < first + kBatchChunk && tb < e.key_count; tb += kTile) {
       if constexpr (ADD) {
-        add_tile<C>(t, static_cast<W_of<C>*>(e.words), e.nblocks, mode, keys, e.key_count, a.acc0, vec_ok, tb);
+        add_tile<C>(t, static_cast<W_of<C>*>(e.words), e.nblocks, mode, keys, e.key_count, a.acc0, vec_ok, tb,
+                    (a.flags & kHintWarpAggregate) != 0);
       } else {
         contains_tile<C>(t, static_cast<const W_of<C>*>(e.words), e.nblocks, mode, keys, e.key_count,
                          a.out + e.key_offset, a.acc0, vec_ok, tb);

@@ -67,6 +67,10 @@ __device__ __forceinline__ uint32_t pattern_bit(uint32_t hlo, uint32_t salt) {
 __device__ __forceinline__ uint64_t pattern_bit(uint32_t hlo, uint64_t salt) {
   return (1ull << ((static_cast<uint64_t>(hlo) * salt) >> 58));
 }
+// the bit position alone (S = 64): the top 6 bits of (hlo * salt) mod 2^64
+__device__ __forceinline__ uint32_t pattern_pos(uint32_t hlo, uint64_t salt) {
+  return static_cast<uint32_t>((static_cast<uint64_t>(hlo) * salt) >> 58);
+}
 
 // salt i of salt set SET (0: the SplitMix64 tables; 1: the Parquet
 // split-block multipliers, 32-bit words only)

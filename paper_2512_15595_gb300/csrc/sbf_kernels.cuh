@@ -22,7 +22,7 @@
 
 namespace bloomgb {
 
-enum : uint32_t { kHintFilterEvictLast = 1u << 0, kHintKeysEvictNormal = 1u << 1 };
+enum : uint32_t { kHintFilterEvictLast = 1u << 0, kHintKeysEvictNormal = 1u << 1, kHintWarpAggregate = 1u << 3 };
 
 // SALTS_: the salt set (0: SplitMix64 tables; 1: the Parquet split-block
 // multipliers, valid for B = 256, S = 32, K = 8 only)
@@ -72,6 +72,19 @@ struct LaneSalts {
     for (int t = 0; t < C::kp; ++t) pat |= pattern_bit(hlo, v[q][p][t]);
     return pat;
   }
+  // 1 if word w has every pattern bit of (q, p) set.  For 64-bit words each
+  // bit is read out of w by a shift (no 64-bit one-hot pattern is built).
+  __device__ __forceinline__ uint32_t covers(uint32_t hlo, int q, int p, typename C::word_t w) const {
+    if constexpr (C::S == 64) {
+      uint32_t all = 1u;
+#pragma unroll
+      for (int t = 0; t < C::kp; ++t) all &= static_cast<uint32_t>(w >> pattern_pos(hlo, v[q][p][t]));
+      return all & 1u;
+    } else {
+      const typename C::word_t pat = pattern(hlo, q, p);
+      return (w & pat) == pat;
+    }
+  }
 };
 
 // OR one lane's PHI consecutive pattern words of step q into the filter at
@@ -95,6 +108,24 @@ __device__ __forceinline__ void red_lane_words(typename C::word_t* bp, const Lan
 #pragma unroll
     for (int p = 0; p < C::PHI; ++p) red_or(bp + p, salts.pattern(hlo, q, p), pol);
   }
+}
+
+// Warp aggregation of construction updates (kHintWarpAggregate): a key equal
+// to the key before it in the warp's tile (the previous key of the same lane,
+// or for a lane's first key the previous lane's last) sets exactly the same
+// bits, so it is dropped from the valid mask before any atomic; a run of
+// repeated keys then costs one update.  Called by all 32 lanes together.
+template <int KPT>
+__device__ __forceinline__ uint32_t drop_repeats(const uint64_t (&key)[KPT], uint32_t valid) {
+  const uint64_t prev = __shfl_up_sync(kFullMask, key[KPT - 1], 1);
+  const bool first_lane = (threadIdx.x & 31u) == 0;
+  uint32_t rep = 0;
+#pragma unroll
+  for (int u = 0; u < KPT; ++u) {
+    const uint64_t before = u ? key[u - 1] : prev;
+    if ((u || !first_lane) && key[u] == before) rep |= 1u << u;
+  }
+  return valid & ~rep;
 }
 
 // Load the lane's KPT keys; returns the validity mask.
@@ -179,16 +210,13 @@ __device__ __forceinline__ void contains_tile(const TileCtx<C>& t, const typenam
   for (int u = 0; u < KPT; ++u) {
 #pragma unroll
     for (int m = 0; m < THETA; ++m) {
-      W miss = 0;
+      uint32_t all = 1u;
 #pragma unroll
       for (int q = 0; q < STEPS; ++q) {
 #pragma unroll
-        for (int p = 0; p < PHI; ++p) {
-          const W pat = t.salts.pattern(hk[u][m], q, p);
-          miss |= pat & ~data[u][m][q][p];
-        }
+        for (int p = 0; p < PHI; ++p) all &= t.salts.covers(hk[u][m], q, p, data[u][m][q][p]);
       }
-      bool ok = (miss == 0);
+      bool ok = all != 0;
       if constexpr (THETA > 1) {
         const uint32_t seg = (__ballot_sync(kFullMask, ok) >> t.g0) & ((1u << THETA) - 1u);
         ok = (seg == (1u << THETA) - 1u);
@@ -213,12 +241,13 @@ __device__ __forceinline__ void contains_tile(const TileCtx<C>& t, const typenam
 template <class C>
 __device__ __forceinline__ void add_tile(const TileCtx<C>& t, typename C::word_t* __restrict__ filter,
                                          uint64_t nblocks, int block_mode, const uint64_t* keys, uint64_t n,
-                                         uint64_t acc0, bool vec_ok, uint64_t tile_base) {
+                                         uint64_t acc0, bool vec_ok, uint64_t tile_base, bool agg = false) {
   using W = typename C::word_t;
   constexpr int KPT = C::KPT, THETA = C::THETA, PHI = C::PHI, STEPS = C::steps;
   const uint64_t base = tile_base + static_cast<uint64_t>(t.lane) * KPT;
   uint64_t key[KPT];
-  const uint32_t valid = load_keys<KPT>(keys, n, base, vec_ok, t.pol_keys, key);
+  uint32_t valid = load_keys<KPT>(keys, n, base, vec_ok, t.pol_keys, key);
+  if (agg) valid = drop_repeats<KPT>(key, valid);
   uint32_t hlo[KPT];
   uint64_t blk[KPT];
 #pragma unroll
@@ -274,7 +303,8 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_add_kernel(const SbfArgs
   const uint64_t nwarps = static_cast<uint64_t>(gridDim.x) * warps_per_cta;
   const bool vec_ok = reinterpret_cast<uintptr_t>(a.keys) % (8u * C::KPT) == 0;
   for (uint64_t tile = blockIdx.x * warps_per_cta + (threadIdx.x >> 5); tile < ntiles; tile += nwarps)
-    add_tile<C>(t, filter, a.nblocks, a.block_mode, a.keys, a.n, a.acc0, vec_ok, tile * kTile);
+    add_tile<C>(t, filter, a.nblocks, a.block_mode, a.keys, a.n, a.acc0, vec_ok, tile * kTile,
+                (a.flags & kHintWarpAggregate) != 0);
 }
 
 }  // namespace bloomgb

@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_add_records_kernel(const
   const LaneSalts<C> salts(r);
   const uint64_t pol_rec = policy_evict_first();
   const uint64_t pol_filter = (a.flags & kHintFilterEvictLast) ? policy_evict_last() : policy_evict_normal();
+  const bool agg = (a.flags & kHintWarpAggregate) != 0;
   W* __restrict__ filter = static_cast<W*>(a.filter);
   constexpr uint64_t kTile = 32u * KPT;
   const uint64_t first_tile = static_cast<uint64_t>(a.part_lo) * a.cap / kTile;
@@ -296,7 +297,8 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_add_records_kernel(const
     const uint64_t base = slot0 + static_cast<uint64_t>(lane) * KPT;
     const uint64_t lim = count < a.cap ? count : a.cap;
     uint64_t rec[KPT];
-    const uint32_t valid = load_keys<KPT>(a.records + p * a.cap, lim, base, true, pol_rec, rec);
+    uint32_t valid = load_keys<KPT>(a.records + p * a.cap, lim, base, true, pol_rec, rec);
+    if (agg) valid = drop_repeats<KPT>(rec, valid);  // equal records: equal keys
 #pragma unroll
     for (int u = 0; u < KPT; ++u) {
 #pragma unroll
@@ -380,13 +382,13 @@ __global__ void __launch_bounds__(kMaxBlockThreads) sbf_probe_records_kernel(con
     for (int u = 0; u < KPT; ++u) {
 #pragma unroll
       for (int m = 0; m < THETA; ++m) {
-        W miss = 0;
+        uint32_t all = 1u;
 #pragma unroll
         for (int qq = 0; qq < STEPS; ++qq) {
 #pragma unroll
-          for (int pp = 0; pp < PHI; ++pp) miss |= salts.pattern(hk[u][m], qq, pp) & ~data[u][m][qq][pp];
+          for (int pp = 0; pp < PHI; ++pp) all &= salts.covers(hk[u][m], qq, pp, data[u][m][qq][pp]);
         }
-        bool ok = (miss == 0);
+        bool ok = all != 0;
         if constexpr (THETA > 1) {
           const uint32_t seg = (__ballot_sync(kFullMask, ok) >> g0) & ((1u << THETA) - 1u);
           ok = (seg == (1u << THETA) - 1u) && (r == static_cast<uint32_t>(m));

@@ -102,14 +102,17 @@ def test_fig2_layouts_are_valid_and_others_rejected(L):
 
 
 def test_layout_flags(L):
-    """The three hint bits are accepted for both operations (the L2 prefetch
-    hint is used by the batched kernels, ignored by the others); any other
-    bit is rejected before a launch."""
+    """The four hint bits are accepted for both operations (the L2 prefetch
+    hint is used by the batched kernels, the warp aggregation by the
+    construction kernels, each ignored by the others); any other bit is
+    rejected before a launch."""
+    every = (L.BF_HINT_FILTER_EVICT_LAST | L.BF_HINT_KEYS_EVICT_NORMAL | L.BF_HINT_PREFETCH_L2
+             | L.BF_HINT_WARP_AGGREGATE)
     for flags in (0, L.BF_HINT_FILTER_EVICT_LAST, L.BF_HINT_KEYS_EVICT_NORMAL, L.BF_HINT_PREFETCH_L2,
-                  L.BF_HINT_FILTER_EVICT_LAST | L.BF_HINT_KEYS_EVICT_NORMAL | L.BF_HINT_PREFETCH_L2):
+                  L.BF_HINT_WARP_AGGREGATE, every):
         for op in (L.BF_OP_ADD, L.BF_OP_CONTAINS):
             assert L.bf_layout_check(P(L), op, L.bf_layout(0, 0, 0, 0, 0, flags)) == L.BF_OK, flags
-    for bad in (1 << 3, 1 << 31):
+    for bad in (1 << 4, 1 << 31):
         assert L.bf_layout_check(P(L), L.BF_OP_ADD, L.bf_layout(0, 0, 0, 0, 0, bad)) == L.BF_EINVAL
 
 

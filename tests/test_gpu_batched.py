@@ -65,7 +65,8 @@ def queries_for(keys, filters, seed):
 
 @pytest.mark.parametrize("B,S,k", [(256, 32, 8), (512, 64, 16), (128, 32, 4)])
 def test_batch_matches_oracle_per_filter(torch, B, S, k):
-    from paper_2512_15595_gb300 import BF_HINT_PREFETCH_L2, BF_OP_ADD, BF_OP_CONTAINS, valid_layouts
+    from paper_2512_15595_gb300 import (BF_HINT_PREFETCH_L2, BF_HINT_WARP_AGGREGATE, BF_OP_ADD, BF_OP_CONTAINS,
+                                        valid_layouts)
     batch, filters, keys, views = make_batch(torch, B, S, k)
     q = queries_for(keys, filters, 55)
     refs = [oracle_for(filters, keys, B, S, k, i) for i in range(len(filters))]
@@ -79,7 +80,8 @@ def test_batch_matches_oracle_per_filter(torch, B, S, k):
         for kpt in (1, 2, 4):
             for v in views:
                 v.zero_()
-            flags = BF_HINT_PREFETCH_L2 if it % 2 else 0  # the L2 prefetch hint on every other layout
+            # the L2 prefetch hint on every other layout, the warp aggregation on every third
+            flags = (BF_HINT_PREFETCH_L2 if it % 2 else 0) | (BF_HINT_WARP_AGGREGATE if it % 3 == 1 else 0)
             it += 1
             batch.set_layout(BF_OP_ADD, cg=cg, phi=phi, kpt=kpt, flags=flags)
             batch.set_layout(BF_OP_CONTAINS, cg=cg, phi=phi, kpt=kpt, flags=flags)

@@ -367,6 +367,69 @@ def test_partition_many_tiles_per_cta(torch):
         f.close()
 
 
+@pytest.mark.parametrize("B,S,k", list(compiled_geometries()))
+def test_warp_aggregated_add_bit_exact(torch, B, S, k):
+    """BF_HINT_WARP_AGGREGATE: the direct and the record-insert construction
+    set the oracle's bits for every layout, with distinct keys, with runs of
+    repeated keys (many lanes of a warp on one block: the case the
+    aggregation merges) and on a 3-block filter (distinct keys sharing
+    blocks)."""
+    from paper_2512_15595_gb300 import BF_HINT_WARP_AGGREGATE, BF_OP_ADD, valid_layouts
+    distinct = synthkeys.insert_keys(20_011, seed=61)
+    runs = np.repeat(synthkeys.insert_keys(700, seed=62), 37)
+    for nb, keys in (((1 << 12) + 9, distinct), ((1 << 12) + 9, runs), (3, distinct[:3001])):
+        geom = oracle.Geometry(num_blocks=nb, block_bits=B, word_bits=S, k=k, seed=44)
+        ref = oracle.SBF(geom)
+        ref.add(keys)
+        dk = dev_keys(torch, keys)
+        for cg, phi in valid_layouts(B, S):
+            for kpt in (1, 4):
+                for part in ((0,), (1,)) if nb > 3 else ((0,),):
+                    f = gpu_filter(geom, torch)
+                    f.set_layout(BF_OP_ADD, cg=cg, phi=phi, kpt=kpt, flags=BF_HINT_WARP_AGGREGATE)
+                    if part[0]:
+                        f.set_partition(mode=1, slice_log2=16)
+                    f.add(dk)
+                    assert np.array_equal(words_np(f), ref.as_bytes()), (nb, cg, phi, kpt, part)
+                    assert f.device_status() == 0
+                    f.close()
+
+
+def test_phase_timing_counts_every_launch(torch):
+    """bf_set_timing / bf_get_timing: every launch of a partitioned
+    construction and lookup (and of the direct kernels) is counted in its
+    phase, durations are positive, the sums restart after each read, and the
+    results do not change."""
+    geom = oracle.Geometry(num_blocks=(1 << 14) + 77, block_bits=256, word_bits=32, k=8, seed=12)
+    ins = synthkeys.insert_keys(300_001, seed=97)
+    q, _ = synthkeys.mixed_queries(300_001, 50_000, 50_001, seed_insert=97)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    f = gpu_filter(geom, torch)
+    f.set_partition(mode=1, slice_log2=16, lookup_mode=1)
+    f.set_timing(True)
+    f.add(dev_keys(torch, ins))
+    n_add = f.last_launches()
+    out = f.contains(dev_keys(torch, q))
+    n_con = f.last_launches()
+    t = f.timing()
+    assert set(t) == {"partition_add", "record_insert", "partition_lookup", "record_probe", "bitmap_expand"}
+    assert t["partition_add"]["launches"] + t["record_insert"]["launches"] == n_add
+    assert sum(t[k]["launches"] for k in ("partition_lookup", "record_probe", "bitmap_expand")) == n_con
+    assert all(v["ms"] > 0 for v in t.values())
+    assert f.timing() == {}
+    f.set_partition(mode=0, lookup_mode=0)
+    f.add(dev_keys(torch, ins))
+    f.contains(dev_keys(torch, q), out=out)
+    t = f.timing()
+    assert t["add_direct"]["launches"] == 1 and t["contains_direct"]["launches"] == 1
+    assert np.array_equal(words_np(f), ref.as_bytes())
+    assert np.array_equal(out.cpu().numpy().astype(np.uint8), ref.contains(q))
+    assert f.device_status() == 0
+    f.set_timing(False)
+    f.close()
+
+
 def test_partitioned_add_skewed_keys(torch):
     # every key lands in one slice (duplicates): the slice buffer overflows and
     # the overflow records take the direct path
