@@ -425,8 +425,19 @@ def run_ours(args, w, wname):
     regime = autotune.regime_of(w["nbytes"], props.L2_cache_size)
 
     ins, qd, flags = gen_inputs(torch, w, device)
+    if args.key_runs > 1:
+        # an insert stream of runs of equal keys (same length; every run's key
+        # is an insert key, so the member queries stay members)
+        ins = ins[: -(-n_ins // args.key_runs)].repeat_interleave(args.key_runs)[:n_ins].contiguous()
+        torch.cuda.synchronize()
     f = Filter(b, w["block_bits"], w["word_bits"], w["k"], 0, device=device, salts=w.get("salts", 0))
     layouts = autotune.apply_tuned(f, regime)
+    if args.add_flags:
+        from paper_2512_15595_gb300 import BF_HINT_WARP_AGGREGATE, BF_OP_ADD
+        lay = f.layout(BF_OP_ADD)
+        lay["flags"] |= {"aggregate": BF_HINT_WARP_AGGREGATE}[args.add_flags]
+        f.set_layout(BF_OP_ADD, **lay)
+        layouts = {"add": f.layout(BF_OP_ADD), "contains": f.layout(1)}
     out = torch.empty(n_q, dtype=torch.uint8, device=device)
     stream = torch.cuda.current_stream()
 
@@ -489,7 +500,9 @@ def run_ours(args, w, wname):
     fresh = flags == 0
     n_fresh = int(fresh.sum().item())
     measured_fpr = float(out[fresh].float().sum().item()) / max(1, n_fresh)
-    missed = int((out[flags == 1] == 0).sum().item())
+    # member queries are insert-stream keys; with --key-runs the insert set is
+    # smaller, so the no-false-negative count only applies to the plain stream
+    missed = int((out[flags == 1] == 0).sum().item()) if args.key_runs == 1 else None
     realized_fpr = popcount_fpr(torch, f.words, w)
 
     # per-kernel device time of the timed steps (events around each group of
@@ -580,6 +593,7 @@ def run_ours(args, w, wname):
                        "word_bits": w["word_bits"], "k": w["k"], "n_insert": n_ins, "n_lookup": n_q,
                        "salts": "parquet split-block" if w.get("salts") else "splitmix64",
                        "regime": regime, "layouts": layouts, "partition": f.partition(),
+                       "key_runs": args.key_runs,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (no flush)" if n_ins * 8 > props.L2_cache_size
                              else "warm L2 (cache-resident regime)"},
@@ -610,25 +624,37 @@ def run_e2e(torch, f, ins, qd, args, world, device):
     stream = torch.cuda.current_stream()
     a_ins, a_q, a_out = h_ins.numpy(), h_q.numpy(), h_out.numpy()
 
-    def step():
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
         f.add_host(a_ins)
+        if ev:
+            ev[1].record(stream)
         f.contains_host(a_q, a_out)
+        if ev:
+            ev[2].record(stream)
 
     for _ in range(max(1, args.warmup)):
         step()
     torch.cuda.synchronize()
     barrier(world)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s.record(stream)
-    for _ in range(args.steps):
-        step()
+    for i in range(args.steps):
+        step(evs[i])
     e.record(stream)
     e.synchronize()
     ms = max_over_ranks(s.elapsed_time(e), world, device)
+    add_ms = statistics.median(x[0].elapsed_time(x[1]) for x in evs)
+    con_ms = statistics.median(x[1].elapsed_time(x[2]) for x in evs)
     n = ins.numel() + qd.numel()
     del h_ins, h_q, h_out
     return {"value": world * n * args.steps / (ms * 1e-3) / 1e9, "unit": "G keys/s",
             "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": qd.numel(), "ms_per_step": ms / args.steps,
+            "add_host_ms": add_ms, "contains_host_ms": con_ms,
+            "add_host_link_gbs": 8 * ins.numel() / (add_ms * 1e-3) / 1e9,
+            "contains_host_link_gbs": 9 * qd.numel() / (con_ms * 1e-3) / 1e9,
             "api": "bf_add_host + bf_contains_host (pinned host buffers)"}
 
 
@@ -1307,6 +1333,10 @@ def main():
     ap.add_argument("--no-gups", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-all-cores", action="store_true", help="skip the all-core oracle timing")
+    ap.add_argument("--add-flags", default="", choices=["", "aggregate"],
+                    help="construction hint: aggregate = BF_HINT_WARP_AGGREGATE")
+    ap.add_argument("--key-runs", type=int, default=1,
+                    help="insert stream as runs of this many equal keys (same length)")
     ap.add_argument("--l2-persist", type=float, default=0.0,
                     help="L2 persistence window over the filter with this hit ratio during the timed steps")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

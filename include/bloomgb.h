@@ -176,7 +176,10 @@ bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, ui
        slice-partitioned construction runs in (at least) eight passes over two
        alternating workspaces (twice the workspace of one such pass), the
        record inserts of one pass on an internal stream while the next pass's
-       partition reads the host keys;
+       partition reads the host keys, and bf_contains_host likewise runs a
+       slice-partitioned lookup in (at least) eight passes over two
+       alternating workspaces, the probes and result expansion of one pass on
+       the internal stream while the next pass's partition reads the queries;
      staged: otherwise, or when bf_set_staging selected BF_HOST_STAGED, keys
        are copied in chunks into device staging buffers on three internal
        streams, overlapping the copies with the kernels, and results are

@@ -624,6 +624,111 @@ const KernelEntry* find_expand() {
   return nullptr;
 }
 
+// Kernels, launch shapes and workspace layout of a slice-partitioned lookup.
+struct LookupLaunch {
+  const KernelEntry* pe = nullptr;  // slice partition (lookup)
+  const KernelEntry* qe = nullptr;  // record probe (the lookup layout)
+  const KernelEntry* xe = nullptr;  // bitmap expansion
+  size_t smem = 0;
+  uint32_t part_grid = 0;    // partition CTAs: SMs x min(resident, max_per_sm)
+  uint32_t per_launch = 1;   // slices per record-probe launch (one window)
+  uint32_t xgrid_cap = 0;    // expansion CTAs: at most SMs x 8
+  uint64_t ws_bytes = 0;     // one pass's workspace: counts | records | indexes | bitmap
+  uint64_t rec_off = 0, idx_off = 0, bitmap_off = 0;
+};
+
+bf_status prepare_lookup(bf_filter* f, const PartPlan& pl, uint64_t pass, int max_per_sm, LookupLaunch* L) {
+  const uint64_t cap_max = part_cap(f, pl, pass);
+  const uint64_t counts_bytes = 8ull * kMaxParts;
+  const uint64_t rec_bytes = static_cast<uint64_t>(pl.nparts) * cap_max * 8;
+  const uint64_t idx_bytes = static_cast<uint64_t>(pl.nparts) * cap_max * 4;
+  const uint64_t bitmap_bytes = ((pass + 31) / 32 * 4 + 255) / 256 * 256;
+  L->rec_off = counts_bytes;
+  L->idx_off = counts_bytes + rec_bytes;
+  L->bitmap_off = counts_bytes + rec_bytes + idx_bytes;
+  L->ws_bytes = L->bitmap_off + bitmap_bytes;
+  L->pe = find_op(5, f->p, 0, 0, 0);
+  const bf_layout& l = f->layout[BF_OP_CONTAINS];
+  L->qe = find_op(4, f->p, l.cg, l.phi, l.kpt);
+  L->xe = find_expand();
+  if (!L->pe || !L->qe || !L->xe) return fail(BF_EUNSUPPORTED, "no partitioned lookup kernels for this geometry");
+  bf_status s = ensure_status(f);
+  if (s != BF_OK) return s;
+  L->smem = partition_smem_bytes(static_cast<int>(pl.nparts), true);
+  cudaError_t e =
+      cudaFuncSetAttribute(L->pe->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L->smem));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(partition)");
+  int sms = 0, per_sm = 0;
+  if ((s = sm_count(f->device, &sms)) != BF_OK) return s;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L->pe->fn, kPartThreads, L->smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(partition)");
+  L->part_grid = static_cast<uint32_t>(sms * std::max(1, std::min(per_sm, max_per_sm)));
+  L->xgrid_cap = static_cast<uint32_t>(sms) * 8;
+  const uint32_t slice_bytes_log2 = pl.shift + static_cast<uint32_t>(__builtin_ctz(f->p.block_bits / 8));
+  L->per_launch = f->part.window_log2 > slice_bytes_log2
+                      ? 1u << std::min<uint32_t>(f->part.window_log2 - slice_bytes_log2, 20)
+                      : 1u;
+  return BF_OK;
+}
+
+// One lookup pass over queries keys[0, cnt) with the workspace at `ws`: the
+// partition on `part_stream`, then (ordered after it by `ev`) the record
+// probes and the bitmap expansion into out[0, cnt) on `probe_stream`.
+bf_status launch_lookup_pass(bf_filter* f, const LookupLaunch& L, const PartPlan& pl, const uint64_t* keys,
+                             uint64_t cnt, uint8_t* out, char* ws, cudaStream_t part_stream,
+                             cudaStream_t probe_stream, cudaEvent_t ev) {
+  unsigned long long* counts = reinterpret_cast<unsigned long long*>(ws);
+  uint64_t* records = reinterpret_cast<uint64_t*>(ws + L.rec_off);
+  uint32_t* idx = reinterpret_cast<uint32_t*>(ws + L.idx_off);
+  uint32_t* bitmap = reinterpret_cast<uint32_t*>(ws + L.bitmap_off);
+  const uint64_t cap = part_cap(f, pl, cnt);
+  const bf_layout& l = f->layout[BF_OP_CONTAINS];
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(counts, 0, 8ull * pl.nparts, part_stream)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemsetAsync");
+  if ((e = cudaMemsetAsync(bitmap, 0, (cnt + 31) / 32 * 4, part_stream)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemsetAsync");
+  PartArgs pa{keys, cnt, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, f->p.num_blocks,
+              f->p.num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, f->words, idx,
+              bitmap, f->status};
+  const uint64_t tiles = (cnt + part_tile(true) - 1) / part_tile(true);
+  const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, L.part_grid));
+  void* pargs[] = {&pa};
+  PhaseMark pm = phase_begin(f, part_stream, BF_PHASE_PARTITION_LOOKUP);
+  if ((e = cudaLaunchKernel(L.pe->fn, dim3(grid), dim3(kPartThreads), pargs, L.smem, part_stream)) != cudaSuccess)
+    return cuda_fail(e, "launch partition kernel (lookup)");
+  phase_end(f, part_stream, pm, 1);
+  f->last_launches += 1;
+  if (probe_stream != part_stream) {
+    if ((e = cudaEventRecord(ev, part_stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(probe_stream, ev, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+  }
+  pm = phase_begin(f, probe_stream, BF_PHASE_RECORD_PROBE);
+  uint32_t nl = 0;
+  for (uint32_t plo = 0; plo < pl.nparts; plo += L.per_launch, ++nl) {
+    const uint32_t phi = std::min(pl.nparts, plo + L.per_launch);
+    ProbeArgs qa{f->words, records, idx, counts, plo, phi, cap, bitmap, l.flags, f->p.num_blocks, f->status};
+    uint32_t qgrid = 0;
+    bf_status s = resolve_grid(L.qe->fn, f->device, l.block_threads, l.grid_ctas, (phi - plo) * cap, l.kpt, &qgrid);
+    if (s != BF_OK) return s;
+    void* qargs[] = {&qa};
+    if ((e = cudaLaunchKernel(L.qe->fn, dim3(qgrid), dim3(l.block_threads), qargs, 0, probe_stream)) != cudaSuccess)
+      return cuda_fail(e, "launch record-probe kernel");
+    f->last_launches += 1;
+  }
+  phase_end(f, probe_stream, pm, nl);
+  ExpandArgs xa{bitmap, cnt, out};
+  const uint64_t words = (cnt + 31) / 32;
+  const uint32_t xgrid = static_cast<uint32_t>(std::min<uint64_t>((words + 255) / 256, L.xgrid_cap));
+  void* xargs[] = {&xa};
+  pm = phase_begin(f, probe_stream, BF_PHASE_BITMAP_EXPAND);
+  if ((e = cudaLaunchKernel(L.xe->fn, dim3(xgrid), dim3(256), xargs, 0, probe_stream)) != cudaSuccess)
+    return cuda_fail(e, "launch bitmap expansion");
+  phase_end(f, probe_stream, pm, 1);
+  f->last_launches += 1;
+  return BF_OK;
+}
+
 // Slice-partitioned lookup: per pass of at most lookup_chunk_keys queries,
 // partition the queries by slice (with their indices), probe each L2-sized
 // window's records, setting a bit per positive query in a result bitmap
@@ -633,77 +738,60 @@ bf_status launch_contains_partitioned(const bf_filter* fc, const uint64_t* keys,
   bf_filter* f = const_cast<bf_filter*>(fc);
   const PartPlan pl = part_plan(f);
   const uint64_t pass = std::min<uint64_t>(n, f->part.lookup_chunk_keys);
-  const uint64_t cap_max = part_cap(f, pl, pass);
-  const uint64_t counts_bytes = 8ull * kMaxParts;
-  const uint64_t rec_bytes = static_cast<uint64_t>(pl.nparts) * cap_max * 8;
-  const uint64_t idx_bytes = static_cast<uint64_t>(pl.nparts) * cap_max * 4;
-  const uint64_t bitmap_bytes = ((pass + 31) / 32 * 4 + 255) / 256 * 256;
-  bf_status s = ensure_ws(&f->look_ws, &f->look_ws_bytes, counts_bytes + rec_bytes + idx_bytes + bitmap_bytes);
-  if (s != BF_OK) return launch_sbf(f, BF_OP_CONTAINS, keys, n, out, stream);  // no memory: direct kernel
-  const KernelEntry* pe = find_op(5, f->p, 0, 0, 0);
-  const bf_layout& l = f->layout[BF_OP_CONTAINS];
-  const KernelEntry* qe = find_op(4, f->p, l.cg, l.phi, l.kpt);
-  const KernelEntry* xe = find_expand();
-  if (!pe || !qe || !xe) return fail(BF_EUNSUPPORTED, "no partitioned lookup kernels for this geometry");
-  if ((s = ensure_status(f)) != BF_OK) return s;
-  char* ws = static_cast<char*>(f->look_ws);
-  unsigned long long* counts = reinterpret_cast<unsigned long long*>(ws);
-  uint64_t* records = reinterpret_cast<uint64_t*>(ws + counts_bytes);
-  uint32_t* idx = reinterpret_cast<uint32_t*>(ws + counts_bytes + rec_bytes);
-  uint32_t* bitmap = reinterpret_cast<uint32_t*>(ws + counts_bytes + rec_bytes + idx_bytes);
-  const size_t smem = partition_smem_bytes(static_cast<int>(pl.nparts), true);
-  cudaError_t e = cudaFuncSetAttribute(pe->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(partition)");
-  int sms = 0, per_sm = 0;
-  if ((s = sm_count(f->device, &sms)) != BF_OK) return s;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pe->fn, kPartThreads, smem);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(partition)");
-  per_sm = std::max(per_sm, 1);
-  const uint32_t slice_bytes_log2 = pl.shift + static_cast<uint32_t>(__builtin_ctz(f->p.block_bits / 8));
-  const uint32_t per_launch =
-      f->part.window_log2 > slice_bytes_log2 ? 1u << std::min<uint32_t>(f->part.window_log2 - slice_bytes_log2, 20) : 1u;
+  LookupLaunch L;
+  bf_status s = prepare_lookup(f, pl, pass, 1 << 30, &L);
+  if (s != BF_OK) return s;
+  if (ensure_ws(&f->look_ws, &f->look_ws_bytes, L.ws_bytes) != BF_OK)
+    return launch_sbf(f, BF_OP_CONTAINS, keys, n, out, stream);  // no memory: direct kernel
   for (uint64_t lo = 0; lo < n; lo += pass) {
     const uint64_t cnt = std::min(pass, n - lo);
-    const uint64_t cap = part_cap(f, pl, cnt);
-    if ((e = cudaMemsetAsync(counts, 0, 8ull * pl.nparts, stream)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    if ((e = cudaMemsetAsync(bitmap, 0, (cnt + 31) / 32 * 4, stream)) != cudaSuccess)
-      return cuda_fail(e, "cudaMemsetAsync");
-    PartArgs pa{keys + lo, cnt, f->p.seed + 0x27D4EB2F165667C5ull + 8ull, f->p.num_blocks,
-                f->p.num_blocks < (1ull << 32) ? 0 : 1, pl.shift, pl.nparts, cap, counts, records, f->words, idx,
-                bitmap, f->status};
-    const uint64_t tiles = (cnt + part_tile(true) - 1) / part_tile(true);
-    const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(tiles, static_cast<uint64_t>(sms) * per_sm));
-    void* pargs[] = {&pa};
-    PhaseMark pm = phase_begin(f, stream, BF_PHASE_PARTITION_LOOKUP);
-    if ((e = cudaLaunchKernel(pe->fn, dim3(grid), dim3(kPartThreads), pargs, smem, stream)) != cudaSuccess)
-      return cuda_fail(e, "launch partition kernel (lookup)");
-    phase_end(f, stream, pm, 1);
-    f->last_launches += 1;
-    pm = phase_begin(f, stream, BF_PHASE_RECORD_PROBE);
-    uint32_t nl = 0;
-    for (uint32_t plo = 0; plo < pl.nparts; plo += per_launch, ++nl) {
-      const uint32_t phi = std::min(pl.nparts, plo + per_launch);
-      ProbeArgs qa{f->words, records, idx, counts, plo, phi, cap, bitmap, l.flags, f->p.num_blocks, f->status};
-      uint32_t qgrid = 0;
-      if ((s = resolve_grid(qe->fn, f->device, l.block_threads, l.grid_ctas, (phi - plo) * cap, l.kpt, &qgrid)) !=
-          BF_OK)
-        return s;
-      void* qargs[] = {&qa};
-      if ((e = cudaLaunchKernel(qe->fn, dim3(qgrid), dim3(l.block_threads), qargs, 0, stream)) != cudaSuccess)
-        return cuda_fail(e, "launch record-probe kernel");
-      f->last_launches += 1;
-    }
-    phase_end(f, stream, pm, nl);
-    ExpandArgs xa{bitmap, cnt, out + lo};
-    const uint64_t words = (cnt + 31) / 32;
-    const uint32_t xgrid = static_cast<uint32_t>(std::min<uint64_t>((words + 255) / 256, static_cast<uint64_t>(sms) * 8));
-    void* xargs[] = {&xa};
-    pm = phase_begin(f, stream, BF_PHASE_BITMAP_EXPAND);
-    if ((e = cudaLaunchKernel(xe->fn, dim3(xgrid), dim3(256), xargs, 0, stream)) != cudaSuccess)
-      return cuda_fail(e, "launch bitmap expansion");
-    phase_end(f, stream, pm, 1);
-    f->last_launches += 1;
+    if ((s = launch_lookup_pass(f, L, pl, keys + lo, cnt, out + lo, static_cast<char*>(f->look_ws), stream, stream,
+                                nullptr)) != BF_OK)
+      return s;
   }
+  return BF_OK;
+}
+
+// Lookup of queries the kernels read in host memory (results written there):
+// the partition reads the host link, the probes do not.  At least
+// kHostPasses passes over two alternating workspaces; the probes and the
+// expansion of pass i run on the filter's second stream while the partition
+// of pass i + 1 (kHostPartCtas CTAs per SM) reads the next queries.
+bf_status launch_contains_partitioned_host(bf_filter* f, const uint64_t* keys, uint64_t n, uint8_t* out,
+                                           cudaStream_t stream) {
+  const PartPlan pl = part_plan(f);
+  const uint64_t pass = std::min<uint64_t>(f->part.lookup_chunk_keys, (n + kHostPasses - 1) / kHostPasses);
+  LookupLaunch L;
+  bf_status s = prepare_lookup(f, pl, pass, kHostPartCtas, &L);
+  if (s != BF_OK) return s;
+  if (ensure_ws(&f->look_ws, &f->look_ws_bytes, 2 * L.ws_bytes) != BF_OK)
+    return launch_contains_partitioned(f, keys, n, out, stream);
+  cudaError_t e;
+  if (!f->rec_stream && (e = cudaStreamCreateWithFlags(&f->rec_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamCreate");
+  for (int i = 0; i < 2; ++i) {
+    if (!f->ev_part[i] && (e = cudaEventCreateWithFlags(&f->ev_part[i], cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreate");
+    if (!f->ev_rec[i] && (e = cudaEventCreateWithFlags(&f->ev_rec[i], cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreate");
+  }
+  bool used[2] = {false, false};
+  uint64_t i = 0;
+  for (uint64_t lo = 0; lo < n; lo += pass, ++i) {
+    const int w = static_cast<int>(i & 1);
+    const uint64_t cnt = std::min(pass, n - lo);
+    if (used[w] && (e = cudaStreamWaitEvent(stream, f->ev_rec[w], 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
+    char* ws = static_cast<char*>(f->look_ws) + w * L.ws_bytes;
+    if ((s = launch_lookup_pass(f, L, pl, keys + lo, cnt, out + lo, ws, stream, f->rec_stream, f->ev_part[w])) !=
+        BF_OK)
+      return s;
+    if ((e = cudaEventRecord(f->ev_rec[w], f->rec_stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    used[w] = true;
+  }
+  for (int w = 0; w < 2; ++w)
+    if (used[w] && (e = cudaStreamWaitEvent(stream, f->ev_rec[w], 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
   return BF_OK;
 }
 
@@ -788,7 +876,8 @@ bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n
   if (device_can_access(f, h_keys) && (op == BF_OP_ADD || device_can_access(f, h_out))) {
     if (op == BF_OP_ADD)
       return use_partitioned(f, n) ? launch_partitioned_host(f, h_keys, n, stream) : run_add(f, h_keys, n, stream);
-    return run_contains(f, h_keys, n, h_out, stream);
+    return use_partitioned_lookup(f, n) ? launch_contains_partitioned_host(f, h_keys, n, h_out, stream)
+                                        : run_contains(f, h_keys, n, h_out, stream);
   }
   bf_status s = ensure_pipeline(f);
   if (s != BF_OK) return s;

@@ -430,6 +430,40 @@ def test_phase_timing_counts_every_launch(torch):
     f.close()
 
 
+def test_partitioned_lookup_from_host_queries(torch):
+    """Lookup of pinned host queries read in place, slice-partitioned: eight
+    passes over two workspaces, the probes and the expansion of one pass on
+    a second stream beside the next pass's partition; every answer is the
+    oracle's, launch counts as planned, and a device lookup afterwards
+    shares the workspace correctly."""
+    geom = oracle.Geometry(num_blocks=(1 << 14) + 77, block_bits=256, word_bits=32, k=8, seed=15)
+    ins = synthkeys.insert_keys(150_001, seed=93)
+    q, is_mem = synthkeys.mixed_queries(150_001, 60_000, 140_003, seed_insert=93)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    want = ref.contains(q)
+    h_q = torch.from_numpy(q.view(np.int64)).pin_memory().numpy()
+    h_out = torch.empty(q.size, dtype=torch.uint8).pin_memory().numpy()
+    for cfg in (dict(slice_log2=16), dict(slice_log2=16, lookup_chunk_keys=4096 * 3 + 1), dict(slice_log2=17,
+                                                                                             window_log2=17)):
+        f = gpu_filter(geom, torch)
+        f.set_partition(mode=0, lookup_mode=1, **cfg)
+        f.add(dev_keys(torch, ins))
+        h_out[:] = 7
+        f.contains_host(h_q, h_out)
+        torch.cuda.synchronize()
+        nparts = -(-geom.nbytes // (1 << cfg["slice_log2"]))
+        windows = -(-nparts // (1 << max(0, cfg.get("window_log2", 26) - cfg["slice_log2"])))
+        pass_keys = min(cfg.get("lookup_chunk_keys", 1 << 28), -(-q.size // 8))
+        assert f.last_launches() == -(-q.size // pass_keys) * (2 + windows), (cfg, f.last_launches())
+        assert np.array_equal(h_out, want), cfg
+        assert h_out[is_mem == 1].all()
+        out = f.contains(dev_keys(torch, q))
+        assert np.array_equal(out.cpu().numpy().astype(np.uint8), want), cfg
+        assert f.device_status() == 0
+        f.close()
+
+
 def test_partitioned_add_skewed_keys(torch):
     # every key lands in one slice (duplicates): the slice buffer overflows and
     # the overflow records take the direct path
