@@ -140,7 +140,9 @@ bf_status bf_params_check(const bf_params* params);
    1 <= cg*phi <= s, powers of two); zeros are resolved to defaults first. */
 bf_status bf_layout_check(const bf_params* params, int op, const bf_layout* layout);
 
-/* Create a filter on the current CUDA device.  If d_words is NULL the library
+/* Create a filter on the current CUDA device: the empty m-bit array of Sec.
+   II-A (m = b*B, all bits 0 for a library-allocated array), organised as b
+   blocks of s words.  If d_words is NULL the library
    allocates b*B/8 bytes (owned, freed by bf_destroy) and zeroes them with a
    blocking memset.  Otherwise it adopts the caller's buffer, which must hold
    b*B/8 bytes, be aligned to max(32, B/8) bytes and stay valid until
@@ -148,10 +150,13 @@ bf_status bf_layout_check(const bf_params* params, int op, const bf_layout* layo
 bf_status bf_create(const bf_params* params, void* d_words, bf_filter** out);
 
 /* Release the filter (and the bit array if the library allocated it).  The
-   caller must ensure no work on the filter is still in flight. */
+   bits themselves are the filter of Sec. II-A; an adopted array keeps them
+   after this call.  The caller must ensure no work on the filter is still
+   in flight. */
 bf_status bf_destroy(bf_filter* f);
 
-/* Zero the bit array, asynchronously on stream. */
+/* Zero the bit array, asynchronously on stream: the empty filter of Sec.
+   II-A (every lookup then reports absent). */
 bf_status bf_clear(bf_filter* f, bf_stream_t stream);
 
 /* Construction (Sec. II-A, Sec. IV): set the pattern of each of the n keys
@@ -197,7 +202,10 @@ bf_status bf_contains_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, uin
 typedef enum { BF_HOST_AUTO = 0, BF_HOST_STAGED = 1 } bf_host_mode;
 bf_status bf_set_staging(bf_filter* f, uint64_t chunk_keys, int mode);
 
-/* Raw bit array: device pointer and size in bytes. */
+/* Raw bit array: device pointer and size in bytes (b*B/8).  Layout as in
+   Sec. II-A (blocked) and Sec. II-A (sectorized): block j is words j*s ..
+   j*s+s-1, each S-bit word little-endian, bit p = 1 << p; the array is the
+   whole state of the filter (it can be saved and restored as bytes). */
 bf_status bf_words(const bf_filter* f, void** d_ptr, uint64_t* nbytes);
 
 /* Geometry of an existing filter. */
