@@ -691,7 +691,8 @@ def run_sweep(args, w, wname):
     out = torch.empty(n_con, dtype=torch.uint8, device=device)
     parts = [dict(mode=0)]
     if regime == "hbm":
-        parts += [dict(mode=1, slice_log2=sl, window_log2=wl) for sl, wl in ((23, 25), (24, 25), (24, 26), (25, 26))]
+        parts += [dict(mode=1, slice_log2=sl, window_log2=wl)
+                  for sl, wl in ((24, 25), (24, 26), (25, 25), (25, 26), (26, 26))]
     lparts = [dict(lookup_mode=0)] + ([dict(lookup_mode=1, lookup_chunk_keys=c) for c in (1 << 27, 1 << 28, 1 << 29)]
                                       if regime == "hbm" else [])
     res = autotune.sweep(torch, f, ins[:n_add], qd[:n_con], out, regime, partitions=parts, kpts=(1, 4), reps=3,
