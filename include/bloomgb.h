@@ -254,7 +254,10 @@ bf_status bf_set_l2_persist(bf_filter* f, bf_stream_t stream, float hit_ratio);
    pass) and the phases overlap: the record inserts of pass i run on an
    internal stream while the partition of pass i + 1 runs on the caller's.
    part_ctas: partition CTAs per SM (0 = as many as fit; with passes >= 2 a
-   smaller value leaves room for the record inserts beside the partition). */
+   smaller value leaves room for the record inserts beside the partition).
+   The host-buffer variants always overlap, with at least max(8, passes)
+   passes and part_ctas partition CTAs per SM (0 = one, enough for the
+   CPU-GPU link). */
 typedef enum { BF_PART_OFF = 0, BF_PART_ON = 1, BF_PART_AUTO = 2 } bf_part_mode;
 typedef struct {
     uint32_t mode;               /* construction; default BF_PART_AUTO */

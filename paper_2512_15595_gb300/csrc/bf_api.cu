@@ -600,14 +600,16 @@ bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cud
 // Construction from keys the kernels read in host memory: the slice
 // partition is bound by the host link, the record inserts (L2, no host
 // traffic) are not, so the overlapped schedule runs with at least
-// kHostPasses passes and kHostPartCtas partition CTAs per SM (enough for the
-// link).
+// max(kHostPasses, passes) passes and part_ctas (default kHostPartCtas)
+// partition CTAs per SM (enough for the link).
 constexpr uint64_t kHostPasses = 8;
 constexpr int kHostPartCtas = 1;
 
+int host_part_ctas(const bf_filter* f) { return f->part.part_ctas ? static_cast<int>(f->part.part_ctas) : kHostPartCtas; }
+
 bf_status launch_partitioned_host(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t stream) {
   return launch_partitioned_overlap(f, keys, n, stream, std::max<uint64_t>(kHostPasses, f->part.passes),
-                                    kHostPartCtas);
+                                    host_part_ctas(f));
 }
 
 bool use_partitioned_lookup(const bf_filter* f, uint64_t n) {
@@ -760,9 +762,10 @@ bf_status launch_contains_partitioned(const bf_filter* fc, const uint64_t* keys,
 bf_status launch_contains_partitioned_host(bf_filter* f, const uint64_t* keys, uint64_t n, uint8_t* out,
                                            cudaStream_t stream) {
   const PartPlan pl = part_plan(f);
-  const uint64_t pass = std::min<uint64_t>(f->part.lookup_chunk_keys, (n + kHostPasses - 1) / kHostPasses);
+  const uint64_t passes = std::max<uint64_t>(kHostPasses, f->part.passes);
+  const uint64_t pass = std::min<uint64_t>(f->part.lookup_chunk_keys, (n + passes - 1) / passes);
   LookupLaunch L;
-  bf_status s = prepare_lookup(f, pl, pass, kHostPartCtas, &L);
+  bf_status s = prepare_lookup(f, pl, pass, host_part_ctas(f), &L);
   if (s != BF_OK) return s;
   if (ensure_ws(&f->look_ws, &f->look_ws_bytes, 2 * L.ws_bytes) != BF_OK)
     return launch_contains_partitioned(f, keys, n, out, stream);

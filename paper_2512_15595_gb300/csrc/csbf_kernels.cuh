@@ -51,6 +51,19 @@ struct CsbfSalts {
     for (int t = 0; t < C::kz; ++t) p |= pattern_bit(hlo, pat[j][t]);
     return p;
   }
+  // 1 if word w has every pattern bit of the lane's j-th group set (64-bit
+  // words: each bit read out of w by a shift, no one-hot pattern built)
+  __device__ __forceinline__ uint32_t covers(uint32_t hlo, int j, typename C::word_t w) const {
+    if constexpr (C::S == 64) {
+      uint32_t all = 1u;
+#pragma unroll
+      for (int t = 0; t < C::kz; ++t) all &= static_cast<uint32_t>(w >> pattern_pos(hlo, pat[j][t]));
+      return all & 1u;
+    } else {
+      const typename C::word_t p = pattern(hlo, j);
+      return (w & p) == p;
+    }
+  }
   // word of the lane's j-th group (group q = r + THETA*j) within the block
   __device__ __forceinline__ uint32_t word(uint32_t hlo, int j, uint32_t r) const {
     const uint32_t q = r + C::THETA * j;
@@ -114,13 +127,10 @@ __global__ void __launch_bounds__(kMaxBlockThreads) csbf_contains_kernel(const S
     for (int u = 0; u < KPT; ++u) {
 #pragma unroll
       for (int m = 0; m < THETA; ++m) {
-        W miss = 0;
+        uint32_t all = 1u;
 #pragma unroll
-        for (int j = 0; j < GPL; ++j) {
-          const W pat = salts.pattern(hk[u][m], j);
-          miss |= pat & ~data[u][m][j];
-        }
-        bool ok = (miss == 0);
+        for (int j = 0; j < GPL; ++j) all &= salts.covers(hk[u][m], j, data[u][m][j]);
+        bool ok = all != 0;
         if constexpr (THETA > 1) {
           const uint32_t seg = (__ballot_sync(kFullMask, ok) >> g0) & ((1u << THETA) - 1u);
           ok = (seg == (1u << THETA) - 1u) && (r == static_cast<uint32_t>(m));
