@@ -241,7 +241,7 @@ def test_partition_struct_layout_matches_the_header(L, tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("gcc not available")
     fields = ("mode", "slice_log2", "chunk_keys", "cap_override", "window_log2", "lookup_mode",
-              "lookup_chunk_keys")
+              "lookup_chunk_keys", "passes", "part_ctas")
     src = tmp_path / "q.c"
     offs = ", ".join(f"offsetof(bf_partition, {f})" for f in fields)
     src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "bloomgb.h"\n'
@@ -252,3 +252,35 @@ def test_partition_struct_layout_matches_the_header(L, tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     S = L.bf_partition
     assert got == [ctypes.sizeof(S)] + [getattr(S, f).offset for f in fields]
+
+
+def test_timing_struct_layout_matches_the_header(L, tmp_path):
+    import ctypes
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src = tmp_path / "t.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "bloomgb.h"\n'
+                   'int main(void){printf("%zu %zu %d %d %d\\n", sizeof(bf_timing), offsetof(bf_timing, launches),'
+                   ' BF_PHASES, BF_PHASE_RECORD_INSERT, BF_PHASE_BITMAP_EXPAND); return 0;}\n')
+    exe = tmp_path / "t"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    T = L.bf_timing
+    assert got == [ctypes.sizeof(T), T.launches.offset, L.BF_PHASES,
+                   L.PHASE_NAMES.index("record_insert"), L.PHASE_NAMES.index("bitmap_expand")]
+
+
+def test_status_timing_and_partition_arguments_rejected_without_gpu(L):
+    """The index-check status, the phase timing and the overlapped-schedule
+    settings reject NULL handles and out-of-range values on the host."""
+    import ctypes
+    lib = L.lib()
+    v = ctypes.c_uint32(7)
+    assert lib.bf_device_status(None, None, ctypes.byref(v)) == L.BF_EINVAL
+    assert lib.bf_noalloc_status(None) == L.BF_EINVAL
+    assert lib.bf_set_timing(None, 1) == L.BF_EINVAL
+    t = L.bf_timing()
+    assert lib.bf_get_timing(None, ctypes.byref(t)) == L.BF_EINVAL
+    assert lib.bf_set_partition(None, ctypes.byref(L.bf_partition())) == L.BF_EINVAL
