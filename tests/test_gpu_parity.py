@@ -532,6 +532,10 @@ def test_partition_auto_and_off(torch):
         f.set_partition(mode=1, slice_log2=8)
     with pytest.raises(Exception):
         f.set_partition(mode=1, cap_override=100)
+    with pytest.raises(Exception):
+        f.set_partition(passes=65)
+    with pytest.raises(Exception):
+        f.set_partition(part_ctas=9)
     assert f.device_status() == 0
     f.close()
 
