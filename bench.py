@@ -391,7 +391,7 @@ PHASE_KERNELS = {
     "add_direct": "sbf_add_kernel", "contains_direct": "sbf_contains_kernel",
     "partition_add": "sbf_partition_kernel (construction)", "record_insert": "sbf_add_records_kernel",
     "partition_lookup": "sbf_partition_kernel (lookup)", "record_probe": "sbf_probe_records_kernel",
-    "bitmap_expand": "bitmap_expand_kernel",
+    "bitmap_expand": "bitmap_expand_kernel", "host_stage": "host_stage16_kernel (host keys to device staging)",
 }
 
 
@@ -413,6 +413,7 @@ def phase_bytes(phase, w, n_ins, n_q, part):
         "partition_lookup": n_q * (8 + 12),
         "record_probe": n_q * 12 + fb * look_passes,
         "bitmap_expand": n_q // 8 + n_q,
+        "host_stage": 8 * (n_ins + n_q),  # host keys over the link into device staging slots
     }[phase]
 
 

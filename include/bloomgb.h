@@ -172,34 +172,47 @@ bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, ui
 
 /* End-to-end variants over HOST buffers.  The work is ordered after prior
    work on `stream` and all of it is complete when `stream` is; h_keys / h_out
-   must stay valid until then.  Two ways, chosen per call:
-     direct: when the device can address the buffers (pinned memory from
-       cudaHostAlloc / cudaHostRegister, or any host memory on a GPU with
-       pageable memory access, as on Grace-coupled GB300), the kernels read the
-       keys and write the results in place over the CPU-GPU link; bf_add_host
-       then takes the same construction path as bf_add, except that a
-       slice-partitioned construction runs in (at least) eight passes over two
-       alternating workspaces (twice the workspace of one such pass), the
-       record inserts of one pass on an internal stream while the next pass's
-       partition reads the host keys, and bf_contains_host likewise runs a
-       slice-partitioned lookup in (at least) eight passes over two
-       alternating workspaces, the probes and result expansion of one pass on
-       the internal stream while the next pass's partition reads the queries;
-     staged: otherwise, or when bf_set_staging selected BF_HOST_STAGED, keys
-       are copied in chunks into device staging buffers on three internal
-       streams, overlapping the copies with the kernels, and results are
-       copied back.  The first staged call allocates the staging buffers
-       (3 slots of about 9 x chunk_keys bytes) and keeps them until
-       bf_destroy. */
+   must stay valid until then.  The device "can address" a buffer when it is
+   page-locked (cudaHostAlloc / cudaHostRegister) or the GPU has pageable
+   memory access (as on Grace-coupled GB300), and for the keys when h_keys is
+   also 8-byte aligned; bf_set_staging(BF_HOST_STAGED) makes every buffer
+   count as one it cannot address.  Three ways, chosen per call:
+     staged passes: when the call takes the slice-partitioned path (see
+       bf_set_partition), unless bf_set_staging selected BF_HOST_DIRECT and
+       the device can address the buffers: the call runs in (at least) eight
+       passes.  On an internal copy-in stream (highest priority) each pass's
+       keys are copied into one of two device staging slots, by a staging
+       kernel on one CTA slot per SM when the device can address them, else
+       by the copy engine, while `stream` partitions and inserts (or probes)
+       the previous pass from device memory; bf_contains_host returns each
+       pass's results by the copy engine on an internal copy-out stream, so
+       the host link stays busy in both directions.  The staging slots (2 x 8
+       bytes per key of a pass, plus 2 x 1 byte for lookups) are kept until
+       bf_set_staging or bf_destroy.  Without memory for them the call takes
+       one of the next two ways;
+     direct: otherwise, when the device can address the buffers, the kernels
+       read the keys and write the results in place over the CPU-GPU link; a
+       slice-partitioned call then runs in (at least) eight passes over two
+       alternating workspaces, the record inserts (or probes and result
+       expansion) of one pass on an internal stream while the next pass's
+       partition reads the host buffer;
+     chunked: otherwise keys are copied in chunks into device staging
+       buffers on three internal streams and the direct kernels run on each
+       chunk, overlapping the copies with the kernels, and results are copied
+       back.  The first such call allocates the staging buffers (3 slots of
+       about 9 x chunk_keys bytes) and keeps them until bf_destroy.
+   Host keys need no alignment. */
 bf_status bf_add_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, bf_stream_t stream);
 bf_status bf_contains_host(bf_filter* f, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
                            bf_stream_t stream);
 
-/* Host-variant settings: keys per staging chunk (default 1<<24) and mode
-   (BF_HOST_AUTO = direct when possible, BF_HOST_STAGED = always stage).
+/* Host-variant settings: keys per chunk of the chunked way (default 1<<24)
+   and mode (BF_HOST_AUTO = as above, BF_HOST_STAGED = never read host
+   memory from the kernels: copy-engine passes or chunks, BF_HOST_DIRECT =
+   read it in place whenever the device can address it).
    Frees the current staging buffers; must not be called while host-variant
    work on this filter is in flight. */
-typedef enum { BF_HOST_AUTO = 0, BF_HOST_STAGED = 1 } bf_host_mode;
+typedef enum { BF_HOST_AUTO = 0, BF_HOST_STAGED = 1, BF_HOST_DIRECT = 2 } bf_host_mode;
 bf_status bf_set_staging(bf_filter* f, uint64_t chunk_keys, int mode);
 
 /* Raw bit array: device pointer and size in bytes (b*B/8).  Layout as in
@@ -292,7 +305,7 @@ bf_status bf_device_status(bf_filter* f, bf_stream_t stream, uint32_t* codes);
    runs on.  bf_get_timing waits for those events and returns, per phase, the
    summed duration of the groups recorded since the previous bf_get_timing (or
    bf_set_timing) in milliseconds and their number of launches, then starts a
-   new sum.  Phases of the overlapped construction schedule run concurrently,
+   new sum.  Phases of the overlapped and staged schedules run concurrently,
    so their sums may exceed the calls' duration.  Timing costs two event
    records per group; bf_set_timing(f, 0) turns it off. */
 enum {
@@ -303,6 +316,9 @@ enum {
     BF_PHASE_PARTITION_LOOKUP = 4,  /* slice partition of lookup queries */
     BF_PHASE_RECORD_PROBE = 5,      /* record probes, one launch per window */
     BF_PHASE_BITMAP_EXPAND = 6,     /* result bitmap to result bytes */
+    BF_PHASE_HOST_STAGE = 7,        /* host keys into device staging slots on the copy-in stream of the
+                                       staged host-buffer passes: staging kernels, or copy-engine copies
+                                       (counted with 0 launches) */
     BF_PHASES = 8
 };
 typedef struct {

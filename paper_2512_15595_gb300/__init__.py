@@ -92,11 +92,19 @@ class Filter:
         return out
 
     def add_host(self, keys_np, stream=None) -> None:
-        """Construction from a host numpy uint64/int64 array (copied in chunks)."""
+        """Construction from a host numpy uint64/int64 array (bf_add_host)."""
         _lib.bf_add_host(self.handle, keys_np.ctypes.data, keys_np.size, stream)
 
     def contains_host(self, keys_np, out_np, stream=None) -> None:
+        """Lookup of host queries into a host uint8 array (bf_contains_host)."""
         _lib.bf_contains_host(self.handle, keys_np.ctypes.data, keys_np.size, out_np.ctypes.data, stream)
+
+    def set_staging(self, chunk_keys: int = 1 << 24, mode: str = "auto") -> None:
+        """Host-variant settings (bf_set_staging): chunk size of the chunked
+        way, and mode "auto", "staged" (the kernels never read host memory)
+        or "direct" (they read it in place whenever they can address it)."""
+        modes = {"auto": _lib.BF_HOST_AUTO, "staged": _lib.BF_HOST_STAGED, "direct": _lib.BF_HOST_DIRECT}
+        _lib.bf_set_staging(self.handle, chunk_keys, modes[mode])
 
     def clear(self, stream=None) -> None:
         _lib.bf_clear(self.handle, stream)

@@ -20,7 +20,7 @@ BF_HINT_KEYS_EVICT_NORMAL = 1 << 1
 BF_HINT_PREFETCH_L2 = 1 << 2
 BF_HINT_WARP_AGGREGATE = 1 << 3
 BF_GUPS_LOAD, BF_GUPS_RED_OR, BF_GUPS_RED_OR_SECTOR = 0, 1, 2
-BF_HOST_AUTO, BF_HOST_STAGED = 0, 1
+BF_HOST_AUTO, BF_HOST_STAGED, BF_HOST_DIRECT = 0, 1, 2
 
 # every symbol include/bloomgb.h declares
 EXPORTED = (
@@ -75,7 +75,7 @@ class bf_partition(ctypes.Structure):
 
 BF_PHASES = 8
 PHASE_NAMES = ("add_direct", "contains_direct", "partition_add", "record_insert", "partition_lookup",
-               "record_probe", "bitmap_expand")
+               "record_probe", "bitmap_expand", "host_stage")
 
 
 class bf_timing(ctypes.Structure):
@@ -83,7 +83,7 @@ class bf_timing(ctypes.Structure):
 
     def as_dict(self):
         return {name: {"ms": self.ms[i], "launches": self.launches[i]}
-                for i, name in enumerate(PHASE_NAMES) if self.launches[i]}
+                for i, name in enumerate(PHASE_NAMES) if self.launches[i] or self.ms[i] > 0}
 
 
 class bf_batch_filter(ctypes.Structure):

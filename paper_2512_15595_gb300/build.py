@@ -39,6 +39,7 @@ def _units():
     units = [("bf_api", os.path.join(CSRC, "bf_api.cu"), []),
              ("gups", os.path.join(CSRC, "gups.cu"), []),
              ("sbf_expand", os.path.join(CSRC, "sbf_expand.cu"), []),
+             ("host_stage", os.path.join(CSRC, "host_stage.cu"), []),
              ("bf_server", os.path.join(CSRC, "bf_server.cu"), []),
              ("lbf_kernels", os.path.join(CSRC, "lbf_kernels.cu"), []),
              ("lbf_tc", os.path.join(CSRC, "lbf_tc.cu"), []),

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "bloomgb.h"
+#include "host_stage.h"
 #include "registry.h"
 
 namespace bloomgb {
@@ -190,7 +191,17 @@ struct bf_filter {
   cudaEvent_t ev_part[2]{};
   cudaEvent_t ev_rec[2]{};
   cudaEvent_t ev_done[kPipelineDepth]{};
-  int host_access = 0;  // 0: kernels read device-accessible host buffers directly; 1: always stage
+  // slice-partitioned passes over host buffers staged through device memory:
+  // two staging slots (keys, then results), a copy-in stream (highest
+  // priority) and a copy-out stream
+  void* hstage = nullptr;
+  uint64_t hstage_bytes = 0;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_copied[2]{};    // slot's keys are on the device
+  cudaEvent_t ev_consumed[2]{};  // slot's keys have been partitioned
+  cudaEvent_t ev_computed[2]{};  // slot's results are ready
+  cudaEvent_t ev_drained[2]{};   // slot's results are on the host
+  int host_access = 0;  // bf_host_mode: BF_HOST_AUTO, BF_HOST_STAGED or BF_HOST_DIRECT
   bool l2_window = false;
   // L2-blocked construction
   bf_partition part{BF_PART_AUTO, 24, 1ull << 32, 0, 26, BF_PART_AUTO, 1ull << 28, 0, 0};
@@ -449,13 +460,25 @@ struct PartLaunch {
   uint32_t per_launch = 1;  // slices per record-insert launch (one window)
 };
 
-bf_status prepare_part_launch(bf_filter* f, const PartPlan& pl, int max_per_sm, PartLaunch* L) {
+// Shared-memory carveout of the kernels that share SMs with the slice
+// partition: kBesidePartitionCarveout in the overlapped and SM-staged
+// schedules (an SM that one of them brought up with a large L1, the default
+// without shared memory, would take no partition CTA until it went idle),
+// the default elsewhere (the record probes run faster with the whole L1).
+bf_status set_carveout(const void* fn, int carveout) {
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+  return e == cudaSuccess ? BF_OK : cuda_fail(e, "cudaFuncSetAttribute(carveout)");
+}
+
+bf_status prepare_part_launch(bf_filter* f, const PartPlan& pl, int max_per_sm, bool beside, PartLaunch* L) {
   bf_status st = ensure_status(f);
   if (st != BF_OK) return st;
   const bf_layout& l = f->layout[BF_OP_ADD];
   L->pe = find_op(3, f->p, 0, 0, 0);
   L->re = find_op(2, f->p, l.cg, l.phi, l.kpt);
   if (!L->pe || !L->re) return fail(BF_EUNSUPPORTED, "no partition kernels for this geometry");
+  if ((st = set_carveout(L->re->fn, beside ? kBesidePartitionCarveout : cudaSharedmemCarveoutDefault)) != BF_OK)
+    return st;
   L->smem = partition_smem_bytes(static_cast<int>(pl.nparts));
   cudaError_t e =
       cudaFuncSetAttribute(L->pe->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L->smem));
@@ -523,7 +546,8 @@ bf_status launch_partitioned_serial(bf_filter* f, const uint64_t* keys, uint64_t
   bf_status s = ensure_part_ws(f, counts_bytes + static_cast<uint64_t>(pl.nparts) * cap_max * 8);
   if (s != BF_OK) return launch_sbf(f, BF_OP_ADD, keys, n, nullptr, stream);  // no memory: direct kernel
   PartLaunch L;
-  if ((s = prepare_part_launch(f, pl, f->part.part_ctas ? static_cast<int>(f->part.part_ctas) : 1 << 30, &L)) !=
+  if ((s = prepare_part_launch(f, pl, f->part.part_ctas ? static_cast<int>(f->part.part_ctas) : 1 << 30, false,
+                                &L)) !=
       BF_OK)
     return s;
   unsigned long long* counts = static_cast<unsigned long long*>(f->part_ws);
@@ -563,7 +587,7 @@ bf_status launch_partitioned_overlap(bf_filter* f, const uint64_t* keys, uint64_
       return cuda_fail(e, "cudaEventCreate");
   }
   PartLaunch L;
-  bf_status s = prepare_part_launch(f, pl, part_ctas, &L);
+  bf_status s = prepare_part_launch(f, pl, part_ctas, true, &L);
   if (s != BF_OK) return s;
   bool used[2] = {false, false};
   uint64_t i = 0;
@@ -604,6 +628,16 @@ bf_status launch_partitioned(bf_filter* f, const uint64_t* keys, uint64_t n, cud
 // partition CTAs per SM (enough for the link).
 constexpr uint64_t kHostPasses = 8;
 constexpr int kHostPartCtas = 1;
+// Partition CTAs per SM beside the staging kernel's CTA (its 4096 registers
+// leave room for three partition CTAs of either kind).
+constexpr int kStagedPartCtas = 3;
+
+// Keys per pass of a pass-wise host-buffer call: n split into `passes`,
+// rounded up to 256 keys (keeps every pass 16-byte aligned when the buffer
+// is), at most `cap`.
+uint64_t host_pass_keys(uint64_t n, uint64_t passes, uint64_t cap) {
+  return std::min<uint64_t>(cap, ((n + passes - 1) / passes + 255) / 256 * 256);
+}
 
 int host_part_ctas(const bf_filter* f) { return f->part.part_ctas ? static_cast<int>(f->part.part_ctas) : kHostPartCtas; }
 
@@ -639,7 +673,8 @@ struct LookupLaunch {
   uint64_t rec_off = 0, idx_off = 0, bitmap_off = 0;
 };
 
-bf_status prepare_lookup(bf_filter* f, const PartPlan& pl, uint64_t pass, int max_per_sm, LookupLaunch* L) {
+bf_status prepare_lookup(bf_filter* f, const PartPlan& pl, uint64_t pass, int max_per_sm, bool beside,
+                         LookupLaunch* L) {
   const uint64_t cap_max = part_cap(f, pl, pass);
   const uint64_t counts_bytes = 8ull * kMaxParts;
   const uint64_t rec_bytes = static_cast<uint64_t>(pl.nparts) * cap_max * 8;
@@ -656,6 +691,8 @@ bf_status prepare_lookup(bf_filter* f, const PartPlan& pl, uint64_t pass, int ma
   if (!L->pe || !L->qe || !L->xe) return fail(BF_EUNSUPPORTED, "no partitioned lookup kernels for this geometry");
   bf_status s = ensure_status(f);
   if (s != BF_OK) return s;
+  const int carveout = beside ? kBesidePartitionCarveout : cudaSharedmemCarveoutDefault;
+  if ((s = set_carveout(L->qe->fn, carveout)) != BF_OK || (s = set_carveout(L->xe->fn, carveout)) != BF_OK) return s;
   L->smem = partition_smem_bytes(static_cast<int>(pl.nparts), true);
   cudaError_t e =
       cudaFuncSetAttribute(L->pe->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L->smem));
@@ -674,8 +711,10 @@ bf_status prepare_lookup(bf_filter* f, const PartPlan& pl, uint64_t pass, int ma
 }
 
 // One lookup pass over queries keys[0, cnt) with the workspace at `ws`: the
-// partition on `part_stream`, then (ordered after it by `ev`) the record
-// probes and the bitmap expansion into out[0, cnt) on `probe_stream`.
+// partition on `part_stream`, then the record probes and the bitmap
+// expansion into out[0, cnt) on `probe_stream`.  `ev` (required when the two
+// streams differ, else optional) is recorded on `part_stream` once the
+// partition has read the queries; `probe_stream` waits for it.
 bf_status launch_lookup_pass(bf_filter* f, const LookupLaunch& L, const PartPlan& pl, const uint64_t* keys,
                              uint64_t cnt, uint8_t* out, char* ws, cudaStream_t part_stream,
                              cudaStream_t probe_stream, cudaEvent_t ev) {
@@ -701,10 +740,9 @@ bf_status launch_lookup_pass(bf_filter* f, const LookupLaunch& L, const PartPlan
     return cuda_fail(e, "launch partition kernel (lookup)");
   phase_end(f, part_stream, pm, 1);
   f->last_launches += 1;
-  if (probe_stream != part_stream) {
-    if ((e = cudaEventRecord(ev, part_stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-    if ((e = cudaStreamWaitEvent(probe_stream, ev, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
-  }
+  if (ev && (e = cudaEventRecord(ev, part_stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  if (probe_stream != part_stream && (e = cudaStreamWaitEvent(probe_stream, ev, 0)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamWaitEvent");
   pm = phase_begin(f, probe_stream, BF_PHASE_RECORD_PROBE);
   uint32_t nl = 0;
   for (uint32_t plo = 0; plo < pl.nparts; plo += L.per_launch, ++nl) {
@@ -741,7 +779,7 @@ bf_status launch_contains_partitioned(const bf_filter* fc, const uint64_t* keys,
   const PartPlan pl = part_plan(f);
   const uint64_t pass = std::min<uint64_t>(n, f->part.lookup_chunk_keys);
   LookupLaunch L;
-  bf_status s = prepare_lookup(f, pl, pass, 1 << 30, &L);
+  bf_status s = prepare_lookup(f, pl, pass, 1 << 30, false, &L);
   if (s != BF_OK) return s;
   if (ensure_ws(&f->look_ws, &f->look_ws_bytes, L.ws_bytes) != BF_OK)
     return launch_sbf(f, BF_OP_CONTAINS, keys, n, out, stream);  // no memory: direct kernel
@@ -765,7 +803,7 @@ bf_status launch_contains_partitioned_host(bf_filter* f, const uint64_t* keys, u
   const uint64_t passes = std::max<uint64_t>(kHostPasses, f->part.passes);
   const uint64_t pass = std::min<uint64_t>(f->part.lookup_chunk_keys, (n + passes - 1) / passes);
   LookupLaunch L;
-  bf_status s = prepare_lookup(f, pl, pass, host_part_ctas(f), &L);
+  bf_status s = prepare_lookup(f, pl, pass, host_part_ctas(f), true, &L);
   if (s != BF_OK) return s;
   if (ensure_ws(&f->look_ws, &f->look_ws_bytes, 2 * L.ws_bytes) != BF_OK)
     return launch_contains_partitioned(f, keys, n, out, stream);
@@ -810,7 +848,7 @@ bf_status run_add(bf_filter* f, const uint64_t* keys, uint64_t n, cudaStream_t s
 
 // Can the kernels read (and for results, write) this host buffer directly?
 bool device_can_access(const bf_filter* f, const void* h) {
-  if (f->host_access != 0) return false;
+  if (f->host_access == BF_HOST_STAGED) return false;
   cudaPointerAttributes attr{};
   if (cudaPointerGetAttributes(&attr, h) != cudaSuccess) {
     cudaGetLastError();
@@ -867,21 +905,190 @@ void release_pipeline(bf_filter* f) {
   }
   if (f->ev_start) cudaEventDestroy(f->ev_start);
   f->ev_start = nullptr;
+  if (f->hstage) cudaFree(f->hstage);
+  f->hstage = nullptr;
+  f->hstage_bytes = 0;
+  for (cudaStream_t* st : {&f->h2d, &f->d2h}) {
+    if (*st) cudaStreamDestroy(*st);
+    *st = nullptr;
+  }
+  for (int i = 0; i < 2; ++i)
+    for (cudaEvent_t* ev : {&f->ev_copied[i], &f->ev_consumed[i], &f->ev_computed[i], &f->ev_drained[i]}) {
+      if (*ev) cudaEventDestroy(*ev);
+      *ev = nullptr;
+    }
 }
 
-// Chunked host->device pipeline: chunk c runs entirely on stream c % depth
-// (copy in, kernel, copy out), so its staging slot is reused in order; the
-// depth-many streams overlap one chunk's copies with another's kernel.
-bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
-                        cudaStream_t stream) {
-  // Grace-coupled GPUs read host memory coherently over NVLink-C2C: the
-  // kernels then stream the keys (and write the results) in place.
-  if (device_can_access(f, h_keys) && (op == BF_OP_ADD || device_can_access(f, h_out))) {
-    if (op == BF_OP_ADD)
-      return use_partitioned(f, n) ? launch_partitioned_host(f, h_keys, n, stream) : run_add(f, h_keys, n, stream);
-    return use_partitioned_lookup(f, n) ? launch_contains_partitioned_host(f, h_keys, n, h_out, stream)
-                                        : run_contains(f, h_keys, n, h_out, stream);
+bf_status ensure_stream(cudaStream_t* st) {
+  cudaError_t e;
+  if (!*st && (e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamCreate");
+  return BF_OK;
+}
+
+bf_status ensure_event(cudaEvent_t* ev) {
+  cudaError_t e;
+  if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventCreate");
+  return BF_OK;
+}
+
+bf_status ensure_copy_streams(bf_filter* f) {
+  bf_status s;
+  if (!f->h2d) {
+    // highest priority: the staging kernel's CTAs take the first free slots
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&f->h2d, cudaStreamNonBlocking, greatest);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithPriority");
   }
+  if ((s = ensure_stream(&f->d2h)) != BF_OK) return s;
+  if ((s = ensure_event(&f->ev_start)) != BF_OK) return s;
+  for (int i = 0; i < 2; ++i)
+    if ((s = ensure_event(&f->ev_copied[i])) != BF_OK || (s = ensure_event(&f->ev_consumed[i])) != BF_OK ||
+        (s = ensure_event(&f->ev_computed[i])) != BF_OK || (s = ensure_event(&f->ev_drained[i])) != BF_OK)
+      return s;
+  return BF_OK;
+}
+
+// Start the copy streams after the work already on `stream`.
+bf_status fork_copies(bf_filter* f, cudaStream_t stream) {
+  cudaError_t e;
+  if ((e = cudaEventRecord(f->ev_start, stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  if ((e = cudaStreamWaitEvent(f->h2d, f->ev_start, 0)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(f->d2h, f->ev_start, 0)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamWaitEvent");
+  return BF_OK;
+}
+
+// Copy n host keys into device memory on the copy-in stream: the staging
+// kernel (one CTA per SM) or the copy engine.
+bf_status stage_keys(bf_filter* f, const uint64_t* h, uint64_t* d, uint64_t n, int sms, bool sm_copy) {
+  uint32_t launches = 0;
+  const PhaseMark pm = phase_begin(f, f->h2d, BF_PHASE_HOST_STAGE);
+  cudaError_t e = sm_copy ? launch_host_stage(h, d, n, static_cast<uint32_t>(sms), f->h2d, &launches)
+                          : cudaMemcpyAsync(d, h, n * 8, cudaMemcpyHostToDevice, f->h2d);
+  if (e != cudaSuccess) return cuda_fail(e, sm_copy ? "launch staging kernel" : "cudaMemcpyAsync H2D");
+  phase_end(f, f->h2d, pm, launches);
+  f->last_launches += launches;
+  return BF_OK;
+}
+
+// Construction from host keys in passes staged through device memory: on
+// the copy-in stream (highest priority) each pass's keys are copied into one
+// of two device staging slots, by the staging kernel on one CTA slot per SM
+// when the kernels can address the keys (sm_copy), else by the copy engine,
+// while `stream` partitions (kStagedPartCtas CTAs per SM beside the staging
+// kernel) and inserts the previous pass from device memory; a pass's device
+// work takes a fraction of its copy, so the call costs about the copy of all
+// keys plus the device work of the last pass.  Pass i + 2 refills pass i's
+// slot once pass i's partition has read it.  Returns BF_ENOMEM, having
+// queued nothing, when the workspaces do not fit.
+bf_status launch_partitioned_staged(bf_filter* f, const uint64_t* h_keys, uint64_t n, cudaStream_t stream,
+                                    bool sm_copy) {
+  const PartPlan pl = part_plan(f);
+  const uint64_t pass = host_pass_keys(n, std::max<uint64_t>(kHostPasses, f->part.passes), f->part.chunk_keys);
+  const uint64_t counts_bytes = 8ull * static_cast<uint32_t>(kMaxParts);
+  const uint64_t kbytes = (pass * 8 + 255) / 256 * 256;
+  if (ensure_part_ws(f, counts_bytes + static_cast<uint64_t>(pl.nparts) * part_cap(f, pl, pass) * 8) != BF_OK ||
+      ensure_ws(&f->hstage, &f->hstage_bytes, 2 * kbytes) != BF_OK)
+    return BF_ENOMEM;
+  bf_status s = ensure_copy_streams(f);
+  if (s != BF_OK) return s;
+  PartLaunch L;
+  if ((s = prepare_part_launch(f, pl, sm_copy ? kStagedPartCtas : 1 << 30, sm_copy, &L)) != BF_OK) return s;
+  int sms = 0;
+  if ((s = sm_count(f->device, &sms)) != BF_OK) return s;
+  if ((s = fork_copies(f, stream)) != BF_OK) return s;
+  unsigned long long* counts = static_cast<unsigned long long*>(f->part_ws);
+  uint64_t* records = reinterpret_cast<uint64_t*>(static_cast<char*>(f->part_ws) + counts_bytes);
+  cudaError_t e;
+  uint64_t i = 0;
+  for (uint64_t lo = 0; lo < n; lo += pass, ++i) {
+    const int w = static_cast<int>(i & 1);
+    const uint64_t cnt = std::min(pass, n - lo);
+    uint64_t* d_keys = reinterpret_cast<uint64_t*>(static_cast<char*>(f->hstage) + w * kbytes);
+    if (i >= 2 && (e = cudaStreamWaitEvent(f->h2d, f->ev_consumed[w], 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
+    if ((s = stage_keys(f, h_keys + lo, d_keys, cnt, sms, sm_copy)) != BF_OK) return s;
+    if ((e = cudaEventRecord(f->ev_copied[w], f->h2d)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(stream, f->ev_copied[w], 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
+    const uint64_t cap = part_cap(f, pl, cnt);
+    if ((s = launch_partition_pass(f, L, pl, d_keys, cnt, cap, counts, records, stream)) != BF_OK) return s;
+    if ((e = cudaEventRecord(f->ev_consumed[w], stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((s = launch_record_windows(f, L, pl, records, counts, cap, stream)) != BF_OK) return s;
+  }
+  return BF_OK;
+}
+
+// Lookup of host queries in passes staged through device memory: pass i's
+// queries are copied into a staging slot on the copy-in stream (the staging
+// kernel when the kernels can address them, else the copy engine), the pass
+// runs on `stream` (partition, probes, expansion into the slot's result
+// bytes), and its results go back by the copy engine on the copy-out
+// stream, so both directions of the link stay busy while the device works.
+// Pass i + 2 refills slot i % 2 once pass i's partition has read its
+// queries, and overwrites its results once they have reached the host.
+// Returns BF_ENOMEM, having queued nothing, when the workspaces do not fit.
+bf_status launch_contains_partitioned_staged(bf_filter* f, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
+                                             cudaStream_t stream, bool sm_copy) {
+  const PartPlan pl = part_plan(f);
+  const uint64_t pass =
+      host_pass_keys(n, std::max<uint64_t>(kHostPasses, f->part.passes), f->part.lookup_chunk_keys);
+  LookupLaunch L;
+  bf_status s = prepare_lookup(f, pl, pass, sm_copy ? kStagedPartCtas : 1 << 30, sm_copy, &L);
+  if (s != BF_OK) return s;
+  const uint64_t kbytes = (pass * 8 + 255) / 256 * 256;
+  const uint64_t slot = kbytes + (pass + 255) / 256 * 256;
+  if (ensure_ws(&f->look_ws, &f->look_ws_bytes, L.ws_bytes) != BF_OK ||
+      ensure_ws(&f->hstage, &f->hstage_bytes, 2 * slot) != BF_OK)
+    return BF_ENOMEM;
+  if ((s = ensure_copy_streams(f)) != BF_OK) return s;
+  int sms = 0;
+  if ((s = sm_count(f->device, &sms)) != BF_OK) return s;
+  if ((s = fork_copies(f, stream)) != BF_OK) return s;
+  cudaError_t e;
+  uint64_t i = 0;
+  int last = 0;
+  for (uint64_t lo = 0; lo < n; lo += pass, ++i) {
+    const int w = static_cast<int>(i & 1);
+    const uint64_t cnt = std::min(pass, n - lo);
+    char* base = static_cast<char*>(f->hstage) + w * slot;
+    uint64_t* d_keys = reinterpret_cast<uint64_t*>(base);
+    uint8_t* d_res = reinterpret_cast<uint8_t*>(base + kbytes);
+    if (i >= 2 && (e = cudaStreamWaitEvent(f->h2d, f->ev_consumed[w], 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
+    if ((s = stage_keys(f, h_keys + lo, d_keys, cnt, sms, sm_copy)) != BF_OK) return s;
+    if ((e = cudaEventRecord(f->ev_copied[w], f->h2d)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(stream, f->ev_copied[w], 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
+    if (i >= 2 && (e = cudaStreamWaitEvent(stream, f->ev_drained[w], 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
+    if ((s = launch_lookup_pass(f, L, pl, d_keys, cnt, d_res, static_cast<char*>(f->look_ws), stream, stream,
+                                f->ev_consumed[w])) != BF_OK)
+      return s;
+    if ((e = cudaEventRecord(f->ev_computed[w], stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(f->d2h, f->ev_computed[w], 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamWaitEvent");
+    if ((e = cudaMemcpyAsync(h_out + lo, d_res, cnt, cudaMemcpyDeviceToHost, f->d2h)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync D2H");
+    if ((e = cudaEventRecord(f->ev_drained[w], f->d2h)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    last = w;
+  }
+  // the copy-out stream is FIFO: its last event covers every result copy
+  if ((e = cudaStreamWaitEvent(stream, f->ev_drained[last], 0)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamWaitEvent");
+  return BF_OK;
+}
+
+// Chunked host->device pipeline of the direct kernels: chunk c runs
+// entirely on stream c % depth (copy in, kernel, copy out), so its staging
+// slot is reused in order; the depth-many streams overlap one chunk's copies
+// with another's kernel.  The chunks never take the slice-partitioned path,
+// whose workspace is one per filter.
+bf_status host_chunked_direct(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
+                              cudaStream_t stream) {
   bf_status s = ensure_pipeline(f);
   if (s != BF_OK) return s;
   cudaError_t e = cudaEventRecord(f->ev_start, stream);
@@ -899,8 +1106,7 @@ bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n
     uint8_t* d_out = reinterpret_cast<uint8_t*>(slot_base + keys_region(f->chunk_keys));
     if ((e = cudaMemcpyAsync(d_keys, h_keys + lo, cnt * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync H2D");
-    if ((s = op == BF_OP_ADD ? run_add(f, d_keys, cnt, st) : run_contains(f, d_keys, cnt, d_out, st)) != BF_OK)
-      return s;
+    if ((s = launch_sbf(f, op, d_keys, cnt, op == BF_OP_ADD ? nullptr : d_out, st)) != BF_OK) return s;
     if (op == BF_OP_CONTAINS &&
         (e = cudaMemcpyAsync(h_out + lo, d_out, cnt, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync D2H");
@@ -910,6 +1116,32 @@ bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n
     if ((e = cudaStreamWaitEvent(stream, f->ev_done[i], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
   }
   return BF_OK;
+}
+
+// Host-buffer entry.  Slice-partitioned work runs in passes staged through
+// device memory (the staging kernel reads buffers the kernels can address,
+// the copy engine the others), unless BF_HOST_DIRECT asks for in-place
+// reads; otherwise Grace-coupled GPUs read host memory coherently over
+// NVLink-C2C and the direct kernels stream the keys (and write the results)
+// in place; else the chunked pipeline of the direct kernels.
+bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
+                        cudaStream_t stream) {
+  const bool add = op == BF_OP_ADD;
+  // kernels load keys as aligned 8-byte words; the copy engine takes any address
+  const bool aligned = reinterpret_cast<uintptr_t>(h_keys) % 8 == 0;
+  const bool in_place = aligned && device_can_access(f, h_keys) && (add || device_can_access(f, h_out));
+  const bool part = add ? use_partitioned(f, n) : use_partitioned_lookup(f, n);
+  if (part && (f->host_access != BF_HOST_DIRECT || !in_place)) {
+    const bf_status s = add ? launch_partitioned_staged(f, h_keys, n, stream, in_place)
+                            : launch_contains_partitioned_staged(f, h_keys, n, h_out, stream, in_place);
+    if (s != BF_ENOMEM) return s;  // else nothing was queued: a path with less memory
+  }
+  if (in_place) {
+    if (add) return part ? launch_partitioned_host(f, h_keys, n, stream) : run_add(f, h_keys, n, stream);
+    return part ? launch_contains_partitioned_host(f, h_keys, n, h_out, stream)
+                : run_contains(f, h_keys, n, h_out, stream);
+  }
+  return host_chunked_direct(f, op, h_keys, n, h_out, stream);
 }
 
 }  // namespace
@@ -1043,7 +1275,8 @@ bf_status bf_set_staging(bf_filter* f, uint64_t chunk_keys, int mode) {
   if (!f) return fail(BF_EINVAL, "filter is NULL");
   if (chunk_keys < 1024 || chunk_keys > (1ull << 32))
     return fail(BF_EINVAL, "chunk_keys must be in [1024, 2^32]");
-  if (mode != BF_HOST_AUTO && mode != BF_HOST_STAGED) return fail(BF_EINVAL, "mode must be BF_HOST_AUTO or BF_HOST_STAGED");
+  if (mode != BF_HOST_AUTO && mode != BF_HOST_STAGED && mode != BF_HOST_DIRECT)
+    return fail(BF_EINVAL, "mode must be BF_HOST_AUTO, BF_HOST_STAGED or BF_HOST_DIRECT");
   DeviceGuard g(f->device);
   release_pipeline(f);
   f->chunk_keys = chunk_keys;

@@ -22,6 +22,7 @@ def test_phase_bytes_of_the_4gib_workload():
     assert pb("record_probe") == 12 * n_q + 2 * (4 << 30)            # two passes of 2^29 queries
     assert pb("bitmap_expand") == n_q // 8 + n_q
     assert pb("add_direct") == 72 * n_ins and pb("contains_direct") == 41 * n_q
+    assert pb("host_stage") == 8 * (n_ins + n_q)
     # more construction passes re-read the windows once per pass
     assert bench.phase_bytes("record_insert", w, n_ins, n_q, dict(part, chunk_keys=1 << 31)) == \
         8 * n_ins + 2 * 2 * (4 << 30)

@@ -262,11 +262,47 @@ def test_partitioned_add_bit_exact(torch, B, S, k):
                 f.close()
 
 
-def test_partitioned_add_from_host_keys(torch):
-    """Construction from pinned host keys read in place: passes over two
-    alternating workspaces with the record inserts on a second stream; bits as
-    the oracle's, launch counts as planned, and the workspace shared correctly
-    with a following device-key construction and a host-key lookup."""
+def host_buffers(torch, buf, *arrays):
+    """Host copies of `arrays`: page-locked, or plain (pageable) numpy."""
+    if buf.startswith("pinned"):
+        return [torch.from_numpy(a.view(np.int64) if a.dtype == np.uint64 else a).pin_memory().numpy()
+                for a in arrays]
+    return [a.copy() for a in arrays]
+
+
+def host_plan(buf, n, cap, h_keys):
+    """(keys per pass, launches per pass beyond the filter kernels) of a
+    pass-wise host-buffer call: staged passes round n / 8 up to 256 keys;
+    with keys the kernels can address (every buffer but the forced-staging
+    one) the staging kernel runs once per pass, plus a one-thread launch for
+    an odd last key of a 16-byte aligned pass; the copy engine counts none;
+    in-place passes (BF_HOST_DIRECT) split n / 8 unrounded."""
+    if buf == "pinned_direct":
+        pk = min(cap, -(-n // 8))
+        return pk, [0] * -(-n // pk)
+    pk = min(cap, -(-(-(-n // 8)) // 256) * 256)
+    extra = []
+    for lo in range(0, n, pk):
+        cnt = min(pk, n - lo)
+        if buf == "pageable_staged":
+            extra.append(0)
+        elif (h_keys.ctypes.data + 8 * lo) % 16 == 0:
+            extra.append(int(cnt >= 2) + (cnt & 1))
+        else:
+            extra.append(1)
+    return pk, extra
+
+
+@pytest.mark.parametrize("buf", ["pinned", "pinned_direct", "pageable", "pageable_staged"])
+def test_partitioned_add_from_host_keys(torch, buf):
+    """Construction from host keys in passes: staged into two device slots
+    (by the staging kernel from page-locked or pageable keys, by the copy
+    engine when staging is forced) while the device partitions and inserts
+    the previous pass; or, with BF_HOST_DIRECT, read in place over two
+    alternating workspaces with the record inserts on a second stream.  Bits
+    as the oracle's, launch counts as planned, and the workspace shared
+    correctly with a following device-key construction and a host-key
+    lookup."""
     geom = oracle.Geometry(num_blocks=(1 << 14) + 77, block_bits=256, word_bits=32, k=8, seed=5)
     ins = synthkeys.insert_keys(150_001, seed=87)
     more = synthkeys.insert_keys(40_000, seed=88)
@@ -275,21 +311,21 @@ def test_partitioned_add_from_host_keys(torch):
     ref.add(ins)
     want_first = ref.as_bytes().copy()
     ref.add(more)
-    h_ins = torch.from_numpy(ins.view(np.int64)).pin_memory().numpy()
-    h_q = torch.from_numpy(q.view(np.int64)).pin_memory().numpy()
-    h_out = torch.empty(q.size, dtype=torch.uint8).pin_memory().numpy()
+    h_ins, h_q, h_out = host_buffers(torch, buf, ins, q, np.zeros(q.size, dtype=np.uint8))
     cases = [dict(slice_log2=16), dict(slice_log2=16, chunk_keys=4096 * 5 + 1), dict(slice_log2=16, cap_override=128),
              dict(slice_log2=17, window_log2=17)]
     for cfg in cases:
         f = gpu_filter(geom, torch)
         f.set_partition(mode=1, **cfg)
+        if buf in ("pageable_staged", "pinned_direct"):
+            f.set_staging(mode="staged" if buf == "pageable_staged" else "direct")
         f.add_host(h_ins)
         torch.cuda.synchronize()
         nparts = -(-geom.nbytes // (1 << cfg["slice_log2"]))
         per_launch = 1 << max(0, cfg.get("window_log2", 26) - cfg["slice_log2"])
-        pass_keys = min(cfg.get("chunk_keys", 1 << 32), -(-ins.size // 8))
-        passes = -(-ins.size // pass_keys)
-        assert f.last_launches() == passes * (1 + -(-nparts // per_launch)), (cfg, f.last_launches())
+        _, extra = host_plan(buf, ins.size, cfg.get("chunk_keys", 1 << 32), h_ins)
+        assert f.last_launches() == len(extra) * (1 + -(-nparts // per_launch)) + sum(extra), (cfg,
+                                                                                                f.last_launches())
         assert np.array_equal(words_np(f), want_first), cfg
         f.add(dev_keys(torch, more))
         f.contains_host(h_q, h_out)
@@ -430,38 +466,72 @@ def test_phase_timing_counts_every_launch(torch):
     f.close()
 
 
-def test_partitioned_lookup_from_host_queries(torch):
-    """Lookup of pinned host queries read in place, slice-partitioned: eight
-    passes over two workspaces, the probes and the expansion of one pass on
-    a second stream beside the next pass's partition; every answer is the
-    oracle's, launch counts as planned, and a device lookup afterwards
-    shares the workspace correctly."""
+@pytest.mark.parametrize("buf", ["pinned", "pinned_direct", "pageable", "pageable_staged"])
+def test_partitioned_lookup_from_host_queries(torch, buf):
+    """Slice-partitioned lookup of host queries in passes: through two
+    device staging slots (queries in by the staging kernel, or by the copy
+    engine when staging is forced; results out by the copy engine); or, with
+    BF_HOST_DIRECT, read and written in place, the probes and the expansion
+    of one pass on a second stream beside the next pass's partition.  Every
+    answer is the oracle's, launch counts as planned, and a device lookup
+    afterwards shares the workspace correctly."""
     geom = oracle.Geometry(num_blocks=(1 << 14) + 77, block_bits=256, word_bits=32, k=8, seed=15)
     ins = synthkeys.insert_keys(150_001, seed=93)
     q, is_mem = synthkeys.mixed_queries(150_001, 60_000, 140_003, seed_insert=93)
     ref = oracle.SBF(geom)
     ref.add(ins)
     want = ref.contains(q)
-    h_q = torch.from_numpy(q.view(np.int64)).pin_memory().numpy()
-    h_out = torch.empty(q.size, dtype=torch.uint8).pin_memory().numpy()
+    h_q, h_out = host_buffers(torch, buf, q, np.zeros(q.size, dtype=np.uint8))
     for cfg in (dict(slice_log2=16), dict(slice_log2=16, lookup_chunk_keys=4096 * 3 + 1), dict(slice_log2=17,
                                                                                              window_log2=17)):
         f = gpu_filter(geom, torch)
         f.set_partition(mode=0, lookup_mode=1, **cfg)
+        if buf in ("pageable_staged", "pinned_direct"):
+            f.set_staging(mode="staged" if buf == "pageable_staged" else "direct")
         f.add(dev_keys(torch, ins))
         h_out[:] = 7
         f.contains_host(h_q, h_out)
         torch.cuda.synchronize()
         nparts = -(-geom.nbytes // (1 << cfg["slice_log2"]))
         windows = -(-nparts // (1 << max(0, cfg.get("window_log2", 26) - cfg["slice_log2"])))
-        pass_keys = min(cfg.get("lookup_chunk_keys", 1 << 28), -(-q.size // 8))
-        assert f.last_launches() == -(-q.size // pass_keys) * (2 + windows), (cfg, f.last_launches())
+        _, extra = host_plan(buf, q.size, cfg.get("lookup_chunk_keys", 1 << 28), h_q)
+        assert f.last_launches() == len(extra) * (2 + windows) + sum(extra), (cfg, f.last_launches())
         assert np.array_equal(h_out, want), cfg
         assert h_out[is_mem == 1].all()
         out = f.contains(dev_keys(torch, q))
         assert np.array_equal(out.cpu().numpy().astype(np.uint8), want), cfg
         assert f.device_status() == 0
         f.close()
+
+
+@pytest.mark.parametrize("partitioned", [False, True])
+def test_host_keys_at_an_odd_address(torch, partitioned):
+    """Host keys 4 bytes off 8-byte alignment (no alignment is required of
+    host buffers): the copy engine takes them, directly or in staged passes;
+    bits and answers as the oracle's."""
+    geom = oracle.Geometry(num_blocks=(1 << 14) + 77, block_bits=256, word_bits=32, k=8, seed=21)
+    ins = synthkeys.insert_keys(100_003, seed=95)
+    q, is_mem = synthkeys.mixed_queries(100_003, 30_000, 70_001, seed_insert=95)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    raw = torch.empty(8 * (ins.size + q.size) + 16, dtype=torch.uint8).pin_memory().numpy()
+    base = (-raw.ctypes.data) % 8 + 4
+    h_ins = np.frombuffer(raw, dtype=np.uint64, count=ins.size, offset=base)
+    h_q = np.frombuffer(raw, dtype=np.uint64, count=q.size, offset=base + 8 * ins.size)
+    assert h_ins.ctypes.data % 8 == 4 and h_q.ctypes.data % 8 == 4
+    h_ins[:] = ins
+    h_q[:] = q
+    h_out = np.zeros(q.size + 1, dtype=np.uint8)[1:]
+    f = gpu_filter(geom, torch)
+    if partitioned:
+        f.set_partition(mode=1, slice_log2=16, lookup_mode=1)
+    f.add_host(h_ins)
+    f.contains_host(h_q, h_out)
+    torch.cuda.synchronize()
+    assert np.array_equal(words_np(f), ref.as_bytes())
+    assert np.array_equal(h_out, ref.contains(q))
+    assert f.device_status() == 0
+    f.close()
 
 
 def test_partitioned_add_skewed_keys(torch):
@@ -536,6 +606,8 @@ def test_partition_auto_and_off(torch):
         f.set_partition(passes=65)
     with pytest.raises(Exception):
         f.set_partition(part_ctas=9)
+    assert _lib.lib().bf_set_staging(f.handle, 1 << 24, 3) == _lib.BF_EINVAL
+    assert _lib.lib().bf_set_staging(f.handle, 1000, _lib.BF_HOST_DIRECT) == _lib.BF_EINVAL
     assert f.device_status() == 0
     f.close()
 
