@@ -627,6 +627,29 @@ def run_ours(args, w, wname):
         dist.destroy_process_group()
 
 
+def link_rates(torch, regions, stream, nbytes=2 << 30, reps=3):
+    """Host-link rates: the best of `reps` copy-engine copies of `nbytes`
+    from and back to each pinned region in `regions` (tensors of 8-byte
+    elements) through one device buffer -- the link itself, not a slow patch
+    of host memory.  The step's ceiling is its host-to-device bytes at the
+    host-to-device rate."""
+    out = {"h2d_gbs": 0.0, "d2h_gbs": 0.0}
+    for r in regions:
+        n = min(r.numel(), nbytes // 8)
+        d = torch.empty(n, dtype=r.dtype, device=stream.device)
+        for name, fn in (("h2d_gbs", lambda: d.copy_(r[:n], non_blocking=True)),
+                         ("d2h_gbs", lambda: r[:n].copy_(d, non_blocking=True))):
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                out[name] = max(out[name], 8 * n / (a.elapsed_time(b) * 1e-3) / 1e9)
+        del d  # the region's first n elements went there and back unchanged
+    return out
+
+
 def run_e2e(torch, f, ins, qd, args, world, device):
     """Same step through the host-buffer entry points: keys start in pinned
     host memory, results end there; the copies are inside the timed region."""
@@ -638,6 +661,8 @@ def run_e2e(torch, f, ins, qd, args, world, device):
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     a_ins, a_q, a_out = h_ins.numpy(), h_q.numpy(), h_out.numpy()
+    link = link_rates(torch, [h_q, h_ins[h_ins.numel() // 2:]], stream)
+    f.set_staging(mode=args.host_mode)
 
     def step(ev=None):
         if ev:
@@ -664,13 +689,23 @@ def run_e2e(torch, f, ins, qd, args, world, device):
     add_ms = statistics.median(x[0].elapsed_time(x[1]) for x in evs)
     con_ms = statistics.median(x[1].elapsed_time(x[2]) for x in evs)
     n = ins.numel() + qd.numel()
+    # per-phase device time of one more (untimed) step: where the schedule spends it
+    f.set_timing(True)
+    step()
+    phases = {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in f.timing().items()}
+    f.set_timing(False)
+    f.set_staging(mode="auto")
     del h_ins, h_q, h_out
     return {"value": world * n * args.steps / (ms * 1e-3) / 1e9, "unit": "G keys/s",
             "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": qd.numel(), "ms_per_step": ms / args.steps,
             "add_host_ms": add_ms, "contains_host_ms": con_ms,
             "add_host_link_gbs": 8 * ins.numel() / (add_ms * 1e-3) / 1e9,
             "contains_host_link_gbs": 9 * qd.numel() / (con_ms * 1e-3) / 1e9,
-            "api": "bf_add_host + bf_contains_host (pinned host buffers)"}
+            "api": "bf_add_host + bf_contains_host (pinned host buffers)", "host_mode": args.host_mode,
+            # every key and query crosses host-to-device once (8 bytes); results go the other way
+            "link": dict(link, ceiling_gkeys_s=link["h2d_gbs"] / 8,
+                         frac_of_ceiling=n * args.steps / (ms * 1e-3) / 1e9 / (link["h2d_gbs"] / 8)),
+            "phases_one_step": phases}
 
 
 def run_sweep(args, w, wname):
@@ -1355,6 +1390,10 @@ def main():
                     help="insert stream as runs of this many equal keys (same length)")
     ap.add_argument("--l2-persist", type=float, default=0.0,
                     help="L2 persistence window over the filter with this hit ratio during the timed steps")
+    ap.add_argument("--host-mode", default="auto", choices=["auto", "direct", "staged"],
+                    help="host-buffer schedule of the e2e leg (bf_set_staging): auto = passes staged "
+                         "through device memory, direct = kernels read host memory in place, "
+                         "staged = copy-engine staging")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.warmup < 3:
