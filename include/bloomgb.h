@@ -387,7 +387,8 @@ bf_status bf_batch_info(const bf_batch* b, uint32_t* nfilters, uint64_t* total_k
    device-resident filters of one geometry (sectorized), lookup requests
    (filter, host keys, host results) arriving over time.  A worker thread
    admits pending requests in arrival order while a device key arena of
-   arena_keys slots (and the per-launch request limit) has room, copies their
+   arena_keys slots, the per-launch request limit and the launch's share of
+   the arena (a third; a larger request goes alone) have room, copies their
    keys in, runs one batched lookup launch over all of them (across filters),
    copies each request's results back, and frees the arena in completion
    order; up to three launches are in flight.  Answers are those of

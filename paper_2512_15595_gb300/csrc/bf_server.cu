@@ -6,8 +6,9 @@
 //
 // Worker loop (one thread per server):
 //   admit    pending requests in arrival order while the arena (a ring of
-//            keys, freed in completion order) and the launch's request slots
-//            have room;
+//            keys, freed in completion order), the launch's request slots
+//            and its share of the arena (a kMaxInflight-th; a larger request
+//            goes alone) have room;
 //   launch   copy the admitted requests' keys into the arena, write one
 //            batch descriptor per request, one kernel over all of them, copy
 //            every request's results back to its host buffer, record an event;
@@ -196,12 +197,18 @@ void worker_loop(bf_server* s) {
       {
         std::unique_lock<std::mutex> g(s->mu);
         L.arena_used = 0;
+        // at most a kMaxInflight-th of the arena per launch (a larger request
+        // goes alone), so that one launch's copies overlap another's kernel
+        const uint64_t launch_cap = std::max<uint64_t>(1, s->ring.cap / kMaxInflight);
+        uint64_t keys = 0;
         while (!s->pending.empty() && L.reqs.size() < s->max_reqs) {
           Request* r = s->pending.front();
+          if (!L.reqs.empty() && keys + r->n > launch_cap) break;
           uint64_t off = 0, consumed = 0;
           if (!s->ring.take(r->n, &off, &consumed)) break;
           r->arena_off = off;
           L.arena_used += consumed;
+          keys += r->n;
           L.reqs.push_back(r);
           s->pending.pop_front();
         }
