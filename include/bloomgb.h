@@ -391,9 +391,13 @@ bf_status bf_batch_info(const bf_batch* b, uint32_t* nfilters, uint64_t* total_k
    the arena (a third; a larger request goes alone) have room, copies their
    keys in, runs one batched lookup launch over all of them (across filters),
    copies each request's results back, and frees the arena in completion
-   order; up to three launches are in flight.  Answers are those of
-   bf_contains on the request's filter.  Host buffers must stay valid until
-   the request completes; pinned memory makes the copies asynchronous.
+   order; up to three launches are in flight.  When the kernels can address
+   every request's buffers of a launch (pinned memory, or any host memory on
+   a GPU with pageable memory access, and 8-byte aligned keys), staging
+   kernels on high-priority streams gather the keys and scatter the results;
+   otherwise the copy engine copies each request's keys and results.
+   Answers are those of bf_contains on the request's filter.  Host buffers
+   must stay valid until the request completes.
    bf_server_create allocates the arena (9 bytes per slot) and a stream and
    starts the worker; bf_server_destroy completes in-flight work and stops it. */
 typedef struct bf_server bf_server;

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "bloomgb.h"
+#include "host_stage.h"
 #include "key_ring.h"
 #include "registry.h"
 
@@ -54,6 +55,7 @@ struct Request {
   uint64_t arena_off = 0;  // first key slot in the arena
   double t_submit = 0, t_done = 0;
   bool done = false;
+  bool addressable = false;  // the kernels can read h_keys and write h_out in place
 };
 
 struct Launch {
@@ -63,8 +65,12 @@ struct Launch {
   cudaEvent_t looked = nullptr;   // kernel finished
   BatchFilter* h_desc = nullptr;  // pinned
   uint64_t* h_begin = nullptr;    // pinned
+  const uint64_t** h_src = nullptr;  // pinned: each request's host keys
+  uint8_t** h_dst = nullptr;         // pinned: each request's host results
   BatchFilter* d_desc = nullptr;
   uint64_t* d_begin = nullptr;
+  const uint64_t** d_src = nullptr;
+  uint8_t** d_dst = nullptr;
   uint64_t arena_end = 0;         // ring position after this launch's keys
   uint64_t arena_used = 0;        // ring slots this launch consumed
   bool busy = false;
@@ -90,7 +96,10 @@ struct bf_server {
   cudaStream_t d2h = nullptr;     // copies out
   const KernelEntry* kernel = nullptr;
   uint32_t threads = 256;
-  uint32_t max_grid = 0;
+  uint32_t max_grid = 0;         // batched lookup CTAs when the copy engines stage
+  uint32_t max_grid_beside = 0;  // ... when staging kernels share the SMs (one CTA slot per SM left)
+  uint32_t stage_ctas = 0;       // staging kernel CTAs (one per SM)
+  int pageable_access = 0;       // the device reads pageable host memory
   uint32_t max_reqs = 0;
   // key / result arena: a ring of `cap` key slots
   uint64_t* d_keys = nullptr;
@@ -135,38 +144,73 @@ void complete_front(bf_server* s) {
   s->cv_done.notify_all();
 }
 
+// Can the kernels read (keys) or write (results) this host buffer in place?
+bool kernels_can_address(const bf_server* s, const void* p) {
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) return true;
+  if (attr.type == cudaMemoryTypeHost) return attr.devicePointer == p;
+  return s->pageable_access == 1;
+}
+
+// One launch: the requests' keys into the arena, one batched lookup, the
+// results back.  When the kernels can address every request's buffers the
+// staging kernels move them (gather on the copy-in stream, scatter on the
+// copy-out stream; the batched lookup leaves them a CTA slot per SM), else
+// the copy engine does, one copy per request and direction.
 bool launch_batch(bf_server* s, int slot) {
   Launch& L = s->launches[slot];
   cudaError_t e = cudaSuccess;
   uint64_t chunks = 0;
+  bool sm = true;
+  for (const Request* r : L.reqs) sm = sm && r->addressable;
   for (size_t i = 0; i < L.reqs.size(); ++i) {
     Request* r = L.reqs[i];
     const BatchFilter& f = s->filters[r->filter];
     L.h_desc[i] = BatchFilter{f.words, f.nblocks, r->arena_off, r->n};
     L.h_begin[i] = chunks;
+    L.h_src[i] = r->h_keys;
+    L.h_dst[i] = r->h_out;
     chunks += (r->n + kBatchChunk - 1) / kBatchChunk;
-    if (e == cudaSuccess && r->n)
+    if (!sm && e == cudaSuccess && r->n)
       e = cudaMemcpyAsync(s->d_keys + r->arena_off, r->h_keys, r->n * 8, cudaMemcpyHostToDevice, s->h2d);
   }
   L.h_begin[L.reqs.size()] = chunks;
   const size_t nr = L.reqs.size();
   if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_desc, L.h_desc, sizeof(BatchFilter) * nr, cudaMemcpyHostToDevice, s->h2d);
   if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_begin, L.h_begin, sizeof(uint64_t) * (nr + 1), cudaMemcpyHostToDevice, s->h2d);
+  if (sm) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_src, L.h_src, sizeof(void*) * nr, cudaMemcpyHostToDevice, s->h2d);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_dst, L.h_dst, sizeof(void*) * nr, cudaMemcpyHostToDevice, s->h2d);
+    if (e == cudaSuccess)
+      e = launch_batch_gather(L.d_desc, L.d_begin, static_cast<uint32_t>(nr), chunks, L.d_src, s->d_keys, s->stage_ctas,
+                              s->h2d);
+  }
   if (e == cudaSuccess) e = cudaEventRecord(L.copied, s->h2d);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, L.copied, 0);
   if (e == cudaSuccess && chunks) {
     BatchArgs a{L.d_desc, L.d_begin, static_cast<uint32_t>(nr), chunks, s->d_keys, s->d_out,
                 s->p.seed + 0x27D4EB2F165667C5ull + 8ull, 0u};
     const uint64_t ctas = (chunks + s->threads / 32 - 1) / (s->threads / 32);
-    const uint32_t grid = static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(ctas, s->max_grid)));
+    const uint32_t cap = sm ? s->max_grid_beside : s->max_grid;
+    const uint32_t grid = static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(ctas, cap)));
     void* args[] = {&a};
     e = cudaLaunchKernel(s->kernel->fn, dim3(grid), dim3(s->threads), args, 0, s->stream);
   }
   if (e == cudaSuccess) e = cudaEventRecord(L.looked, s->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->d2h, L.looked, 0);
-  for (size_t i = 0; i < nr && e == cudaSuccess; ++i) {
-    Request* r = L.reqs[i];
-    if (r->n) e = cudaMemcpyAsync(r->h_out, s->d_out + r->arena_off, r->n, cudaMemcpyDeviceToHost, s->d2h);
+  if (sm) {
+    if (e == cudaSuccess)
+      e = launch_batch_scatter(L.d_desc, L.d_begin, static_cast<uint32_t>(nr), chunks, L.d_dst, s->d_out,
+                               s->stage_ctas, s->d2h);
+  } else {
+    for (size_t i = 0; i < nr && e == cudaSuccess; ++i) {
+      Request* r = L.reqs[i];
+      if (r->n) e = cudaMemcpyAsync(r->h_out, s->d_out + r->arena_off, r->n, cudaMemcpyDeviceToHost, s->d2h);
+    }
   }
   if (e == cudaSuccess) e = cudaEventRecord(L.done, s->d2h);
   if (e != cudaSuccess) {
@@ -271,9 +315,15 @@ bf_status bf_server_create(const bf_params* params, const bf_batch_filter* filte
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
   const int per_sm = e == cudaSuccess ? kernel_resident_ctas(k->fn, s->threads, s->device) : 0;
   s->max_grid = static_cast<uint32_t>(std::max(1, sms * std::max(per_sm, 1)));
+  s->max_grid_beside = static_cast<uint32_t>(std::max(1, sms * std::max(per_sm - 1, 1)));
+  s->stage_ctas = static_cast<uint32_t>(std::max(1, sms));
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->pageable_access, cudaDevAttrPageableMemoryAccess, s->device);
+  int least = 0, greatest = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
+  // staging streams at the highest priority: the staging kernels' CTAs take free slots first
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->h2d, cudaStreamNonBlocking, greatest);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->d2h, cudaStreamNonBlocking, greatest);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_keys, arena_keys * 8);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_out, arena_keys);
   for (int i = 0; i < kMaxInflight && e == cudaSuccess; ++i) {
@@ -283,8 +333,12 @@ bf_status bf_server_create(const bf_params* params, const bf_batch_filter* filte
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.looked, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaHostAlloc(&L.h_desc, sizeof(BatchFilter) * s->max_reqs, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&L.h_begin, sizeof(uint64_t) * (s->max_reqs + 1), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&L.h_src, sizeof(void*) * s->max_reqs, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&L.h_dst, sizeof(void*) * s->max_reqs, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&L.d_desc, sizeof(BatchFilter) * s->max_reqs);
     if (e == cudaSuccess) e = cudaMalloc(&L.d_begin, sizeof(uint64_t) * (s->max_reqs + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_src, sizeof(void*) * s->max_reqs);
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_dst, sizeof(void*) * s->max_reqs);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -310,8 +364,12 @@ bf_status bf_server_destroy(bf_server* s) {
     if (L.looked) cudaEventDestroy(L.looked);
     if (L.h_desc) cudaFreeHost(L.h_desc);
     if (L.h_begin) cudaFreeHost(L.h_begin);
+    if (L.h_src) cudaFreeHost(L.h_src);
+    if (L.h_dst) cudaFreeHost(L.h_dst);
     if (L.d_desc) cudaFree(L.d_desc);
     if (L.d_begin) cudaFree(L.d_begin);
+    if (L.d_src) cudaFree(L.d_src);
+    if (L.d_dst) cudaFree(L.d_dst);
   }
   if (s->d_keys) cudaFree(s->d_keys);
   if (s->d_out) cudaFree(s->d_out);
@@ -332,6 +390,8 @@ bf_status bf_server_submit(bf_server* s, uint32_t filter, const uint64_t* h_keys
   r->n = n;
   r->h_out = h_out;
   r->t_submit = now_s();
+  r->addressable = n == 0 || (reinterpret_cast<uintptr_t>(h_keys) % 8 == 0 && kernels_can_address(s, h_keys) &&
+                              kernels_can_address(s, h_out));
   {
     std::lock_guard<std::mutex> g(s->mu);
     r->ticket = s->next_ticket++;

@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "host_stage.h"
+#include "registry.h"
 
 namespace bloomgb {
 
@@ -46,6 +47,82 @@ __global__ void __launch_bounds__(kHostStageThreads, 16)
   copy_units<uint64_t, uint64_t>(src, dst, n);
 }
 
+// One chunk of a batch request: its host and arena element pointers and
+// the number of its elements (1 to kBatchChunk).
+template <typename T>
+struct ChunkRef {
+  T* host;
+  T* arena;
+  uint32_t cnt;
+};
+
+// The request owning chunk c, advanced from r (chunks are walked upwards;
+// requests without elements own no chunk and are skipped).
+__device__ __forceinline__ uint32_t owner(const uint64_t* __restrict__ begin, uint32_t r, uint64_t c) {
+  while (begin[r + 1] <= c) ++r;
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ ChunkRef<T> chunk_ref(const BatchFilter* __restrict__ desc, const uint64_t* __restrict__ begin,
+                                                 const void* const* __restrict__ host, T* arena, uint32_t r, uint64_t c) {
+  const uint64_t i0 = (c - begin[r]) * kBatchChunk;
+  const uint64_t left = desc[r].key_count - i0;
+  // host buffers of a gather are only read
+  return {static_cast<T*>(const_cast<void*>(host[r])) + i0, arena + desc[r].key_offset + i0,
+          static_cast<uint32_t>(left < kBatchChunk ? left : kBatchChunk)};
+}
+
+// GATHER: host keys -> arena; else arena results -> host.  Warp w walks
+// chunks [w * per, (w + 1) * per), two at a time: all loads of both chunks,
+// then the stores (lane l takes elements l, l + 32, l + 64, l + 96).
+template <bool GATHER, typename T>
+__global__ void __launch_bounds__(kHostStageThreads, 8)
+    batch_stage_kernel(const BatchFilter* __restrict__ desc, const uint64_t* __restrict__ begin, uint32_t nreq,
+                       uint64_t chunks, const void* const* __restrict__ host, T* __restrict__ arena) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
+  const uint64_t w = static_cast<uint64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+  const uint64_t per = (chunks + warps - 1) / warps;
+  uint64_t c = w * per;
+  const uint64_t c_end = c + per < chunks ? c + per : chunks;
+  if (c >= c_end) return;
+  // the last request whose first chunk is at or before c (begin[0] = 0 <= c < begin[nreq])
+  uint32_t lo = 0, hi = nreq;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (begin[mid] <= c) lo = mid;
+    else hi = mid;
+  }
+  uint32_t r = lo;
+  constexpr uint32_t kStep = kBatchChunk / 4;  // 32: one element per lane per quarter chunk
+  for (; c < c_end; c += 2) {
+    r = owner(begin, r, c);
+    const ChunkRef<T> a = chunk_ref<T>(desc, begin, host, arena, r, c);
+    const bool two = c + 1 < c_end;
+    uint32_t r2 = r;
+    ChunkRef<T> b{nullptr, nullptr, 0};
+    if (two) {
+      r2 = owner(begin, r, c + 1);
+      b = chunk_ref<T>(desc, begin, host, arena, r2, c + 1);
+    }
+    T va[4], vb[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t i = lane + j * kStep;
+      if (i < a.cnt) va[j] = __ldcs(GATHER ? a.host + i : a.arena + i);
+      if (i < b.cnt) vb[j] = __ldcs(GATHER ? b.host + i : b.arena + i);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t i = lane + j * kStep;
+      if (i < a.cnt) __stcs(GATHER ? a.arena + i : a.host + i, va[j]);
+      if (i < b.cnt) __stcs(GATHER ? b.arena + i : b.host + i, vb[j]);
+    }
+    r = r2;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_host_stage(const uint64_t* src, uint64_t* dst, uint64_t n, uint32_t ctas, cudaStream_t stream,
@@ -78,6 +155,25 @@ cudaError_t launch_host_stage(const uint64_t* src, uint64_t* dst, uint64_t n, ui
     host_stage8_kernel<<<ctas, kHostStageThreads, 0, stream>>>(src, dst, n);
     *launches = 1;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_gather(const BatchFilter* desc, const uint64_t* begin, uint32_t nreq, uint64_t chunks,
+                                const uint64_t* const* host, uint64_t* arena_keys, uint32_t ctas,
+                                cudaStream_t stream) {
+  if (chunks == 0) return cudaSuccess;
+  if (ctas == 0 || nreq == 0) return cudaErrorInvalidValue;
+  batch_stage_kernel<true, uint64_t><<<ctas, kHostStageThreads, 0, stream>>>(
+      desc, begin, nreq, chunks, reinterpret_cast<const void* const*>(host), arena_keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_scatter(const BatchFilter* desc, const uint64_t* begin, uint32_t nreq, uint64_t chunks,
+                                 uint8_t* const* host, const uint8_t* arena_out, uint32_t ctas, cudaStream_t stream) {
+  if (chunks == 0) return cudaSuccess;
+  if (ctas == 0 || nreq == 0) return cudaErrorInvalidValue;
+  batch_stage_kernel<false, uint8_t><<<ctas, kHostStageThreads, 0, stream>>>(
+      desc, begin, nreq, chunks, reinterpret_cast<const void* const*>(host), const_cast<uint8_t*>(arena_out));
   return cudaGetLastError();
 }
 

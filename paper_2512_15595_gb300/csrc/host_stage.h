@@ -34,4 +34,22 @@ constexpr int kBesidePartitionCarveout = 50;
 cudaError_t launch_host_stage(const uint64_t* src, uint64_t* dst, uint64_t n, uint32_t ctas, cudaStream_t stream,
                               uint32_t* launches);
 
+// Staging of a batch of requests between their host buffers and a device
+// arena by the SMs, in the chunk decomposition of the batched kernels:
+// request r (of nreq) owns chunks [begin[r], begin[r + 1]) of kBatchChunk
+// elements, and its element i lives at arena element desc[r].key_offset + i
+// and at host element i of host[r]; desc[r].key_count elements in all.
+// gather: the 8-byte keys from host[r] (8-byte aligned) into arena_keys;
+// scatter: the 1-byte results from arena_out into host[r].  desc, begin and
+// host are device arrays; the host buffers must be addressable by the
+// kernels.  One warp walks a contiguous run of chunks (one search for its
+// first request), each lane four elements of a chunk, two chunks of loads
+// in flight; `ctas` CTAs of kHostStageThreads threads.
+struct BatchFilter;
+cudaError_t launch_batch_gather(const BatchFilter* desc, const uint64_t* begin, uint32_t nreq, uint64_t chunks,
+                                const uint64_t* const* host, uint64_t* arena_keys, uint32_t ctas,
+                                cudaStream_t stream);
+cudaError_t launch_batch_scatter(const BatchFilter* desc, const uint64_t* begin, uint32_t nreq, uint64_t chunks,
+                                 uint8_t* const* host, const uint8_t* arena_out, uint32_t ctas, cudaStream_t stream);
+
 }  // namespace bloomgb

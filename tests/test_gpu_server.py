@@ -19,7 +19,28 @@ def env():
     return torch, Filter, _lib
 
 
+def request_buffers(torch, q, kind):
+    """Host key / result buffers of one request: 0 pinned, 1 pageable (the
+    kernels address both in place: staging kernels), 2 pinned keys at an
+    address 4 bytes off 8-byte alignment (the copy engine stages the whole
+    launch).  Returns (key pointer, result array, objects to keep alive)."""
+    n = q.size
+    if kind == 1:
+        keys, out = q.copy(), np.zeros(max(n, 1), dtype=np.uint8)
+        return keys.ctypes.data, out, (keys,)
+    out_t = torch.zeros(max(n, 1), dtype=torch.uint8).pin_memory()
+    if kind == 2:
+        raw = torch.empty(8 * n + 16, dtype=torch.uint8).pin_memory()
+        base = (-raw.data_ptr()) % 8 + 4
+        np.frombuffer(raw.numpy(), dtype=np.uint64, count=n, offset=base)[:] = q
+        return raw.data_ptr() + base, out_t.numpy(), (raw, out_t)
+    keys_t = torch.from_numpy(q.view(np.int64)).pin_memory()
+    return keys_t.data_ptr(), out_t.numpy(), (keys_t, out_t)
+
+
 def test_server_answers_match_oracle(env):
+    """Requests of pinned, pageable and misaligned host buffers (staging
+    kernels or copy-engine copies per launch), empty requests, ring wraps."""
     torch, Filter, L = env
     B, S, k = 256, 32, 8
     sizes = [1000, 333, 4097, 64, 2500]
@@ -45,15 +66,15 @@ def test_server_answers_match_oracle(env):
             if n:
                 own = synthkeys.splitmix64(200 + fi, 0, sizes[fi] * 20)
                 q[::3] = own[rng.integers(0, own.size, size=q[::3].size)]
-            hq = torch.from_numpy(q.view(np.int64)).pin_memory()
-            ho = torch.zeros(max(n, 1), dtype=torch.uint8).pin_memory()
-            t = L.bf_server_submit(srv, fi, hq.data_ptr() if n else 0, n, ho.data_ptr() if n else 0)
-            reqs.append((t, fi, q, hq, ho, n))
-        for t, fi, q, hq, ho, n in reqs:
+            kind = 2 if r % 23 == 5 else r % 2  # a misaligned request now and then
+            kp, ho, keep = request_buffers(torch, q, kind)
+            t = L.bf_server_submit(srv, fi, kp if n else 0, n, ho.ctypes.data if n else 0)
+            reqs.append((t, fi, q, keep, ho, n))
+        for t, fi, q, keep, ho, n in reqs:
             lat = L.bf_server_wait(srv, t, 60.0)
             assert lat >= 0
             if n:
-                assert np.array_equal(ho.numpy()[:n], refs[fi].contains(q)), (t, fi, n)
+                assert np.array_equal(ho[:n], refs[fi].contains(q)), (t, fi, n)
         st = L.bf_server_get_stats(srv)
         assert st["requests"] == 300 and st["keys"] == sum(r[5] for r in reqs)
         assert st["launches"] >= 300 // 7
