@@ -632,11 +632,14 @@ constexpr int kHostPartCtas = 1;
 // leave room for three partition CTAs of either kind).
 constexpr int kStagedPartCtas = 3;
 
-// Keys per pass of a pass-wise host-buffer call: n split into `passes`,
+// Keys per pass of a staged host-buffer call: n split into passes - 3/4
+// equal shares, so the last pass is about a quarter of the others (only the
+// last pass's device work is not hidden behind the staging of the next one),
 // rounded up to 256 keys (keeps every pass 16-byte aligned when the buffer
 // is), at most `cap`.
 uint64_t host_pass_keys(uint64_t n, uint64_t passes, uint64_t cap) {
-  return std::min<uint64_t>(cap, ((n + passes - 1) / passes + 255) / 256 * 256);
+  const uint64_t share = (4 * n + 4 * passes - 4) / (4 * passes - 3);  // ceil(4n / (4 passes - 3))
+  return std::min<uint64_t>(cap, (share + 255) / 256 * 256);
 }
 
 int host_part_ctas(const bf_filter* f) { return f->part.part_ctas ? static_cast<int>(f->part.part_ctas) : kHostPartCtas; }

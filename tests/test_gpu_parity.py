@@ -272,7 +272,8 @@ def host_buffers(torch, buf, *arrays):
 
 def host_plan(buf, n, cap, h_keys):
     """(keys per pass, launches per pass beyond the filter kernels) of a
-    pass-wise host-buffer call: staged passes round n / 8 up to 256 keys;
+    pass-wise host-buffer call: staged passes split n into 7.25 shares (a
+    short last pass), rounded up to 256 keys;
     with keys the kernels can address (every buffer but the forced-staging
     one) the staging kernel runs once per pass, plus a one-thread launch for
     an odd last key of a 16-byte aligned pass; the copy engine counts none;
@@ -280,7 +281,7 @@ def host_plan(buf, n, cap, h_keys):
     if buf == "pinned_direct":
         pk = min(cap, -(-n // 8))
         return pk, [0] * -(-n // pk)
-    pk = min(cap, -(-(-(-n // 8)) // 256) * 256)
+    pk = min(cap, -(-(-(-4 * n // 29)) // 256) * 256)
     extra = []
     for lo in range(0, n, pk):
         cnt = min(pk, n - lo)
