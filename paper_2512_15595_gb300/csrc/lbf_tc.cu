@@ -7,12 +7,16 @@
 // an exactly representable integer multiple of a power of two:
 //   * A1 = the key bits (0/1), B1 = W1q * 2^-sh1 (int8 times a power of two:
 //     exact in bf16); |sum x W1q| <= 64 * 127.
-//   * the epilogue adds a per-unit fp32 constant c1 = (b1' + 128 * 2^sh1)
-//     2^-sh1 (b1' = b1q clamped to the range where it still changes the
-//     result), so y1 = 128 + a1 / 2^sh1 exactly, converts to bf16 rounding
+//   * a per-unit constant c1 = (b1' + 128 * 2^sh1) 2^-sh1 (b1' = b1q
+//     clamped to the range where it still changes the result) is the first
+//     product of the layer: one more MMA of K = 16 over a constant A (1.0 in
+//     k = 0..2) and B = the three bf16 parts of c1 (an integer below 2^24
+//     times 2^-sh1 is the sum of three 8-bit parts, each exact), so
+//     y1 = 128 + a1 / 2^sh1 exactly; the epilogue converts to bf16 rounding
 //     toward zero (the bf16 spacing on [128, 256) is 1, so this is the floor)
 //     and clamps to [128, 255]: A2 = 128 + h1, exact in bf16.
-//   * B2 = W2q * 2^-sh2; the offset 128 * colsum(W2q) is folded into c2, and
+//   * B2 = W2q * 2^-sh2; the offset 128 * colsum(W2q) is folded into c2
+//     (added by the layer's bias MMA the same way), and
 //     likewise 128 + h2 (exact in bf16 and fp32) is dotted with W3q on the
 //     CUDA cores in fp32 (integer partial sums below 2^24), score = acc3 +
 //     (b3q - 128 sum W3q).
@@ -53,7 +57,13 @@ namespace {
 // shared-memory map (offsets from a 1024-byte aligned base)
 constexpr uint32_t kB1 = 0;                     // 128 rows (unit j) x 64 bf16 (input i)
 constexpr uint32_t kB2 = kB1 + 128 * 128;       // 2 k-blocks x 64 rows x 64 bf16
-constexpr uint32_t kImage = kB2 + 2 * 64 * 128;  // bytes copied from the device image
+// bias k-block: A = 1.0 in k = 0..2 of every row, B = the three bf16 parts of
+// each unit's requantization constant (zero elsewhere), so one more MMA of
+// K = 16 per layer adds the constant to the accumulator
+constexpr uint32_t kAx = kB2 + 2 * 64 * 128;    // 128 rows x 64 bf16 (k < 3 used)
+constexpr uint32_t kB1x = kAx + 128 * 128;      // 128 rows (unit j)
+constexpr uint32_t kB2x = kB1x + 128 * 128;     // 64 rows (unit j)
+constexpr uint32_t kImage = kB2x + 64 * 128;    // bytes copied from the device image
 constexpr uint32_t kSlots = (kImage + 1023) / 1024 * 1024;  // 4 slots of 16 KiB (A1)
 constexpr uint32_t kSlotBytes = 16384;
 constexpr int kWG = 4;
@@ -61,7 +71,8 @@ constexpr uint32_t kBar = kSlots + kWG * kSlotBytes;  // 4 mbarriers per warpgro
 // + alignment slack; at least 120 KiB so that no second CTA (which would
 // wait for this one's tensor memory) is ever placed on the same SM
 constexpr uint32_t kSmemBytes = kBar + 256 + 1024 > 120 * 1024 ? kBar + 256 + 1024 : 120 * 1024;
-static_assert(kSlots % 1024 == 0 && kB2 % 1024 == 0, "swizzled operands must be 1024-byte aligned");
+static_assert(kSlots % 1024 == 0 && kB2 % 1024 == 0 && kAx % 1024 == 0 && kB1x % 1024 == 0 && kB2x % 1024 == 0,
+              "swizzled operands must be 1024-byte aligned");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 constexpr int kEpiThreads = 128 * kWG;
 constexpr int kThreads = kEpiThreads + 32;  // + the MMA warp
@@ -88,8 +99,6 @@ struct TcArgs {
   uint64_t* out_keys;
   unsigned int* err;
   long long s3;
-  float c1[128];  // per-unit constants of the two requantizations
-  float c2[64];
   float w3[64];   // W3q as fp32 (layer 3 runs on the CUDA cores)
   // mode 5: the backup filter (256-bit blocks, S = 32, K = 8, sectorized)
   const uint32_t* bk_words;
@@ -239,18 +248,12 @@ __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
 __device__ __forceinline__ float lo_of(uint64_t v) { return __uint_as_float(static_cast<uint32_t>(v)); }
 __device__ __forceinline__ float hi_of(uint64_t v) { return __uint_as_float(static_cast<uint32_t>(v >> 32)); }
 
-// 32 loaded accumulator columns of layer L (first unit u0) -> 16 columns of
-// packed bf16 (128 + h) at `to`
-template <int L>
-__device__ __forceinline__ void requant_store(const TcArgs& P, const uint32_t (&a)[32], int u0, uint32_t to) {
-  const float* c = L == 1 ? P.c1 : P.c2;
+// 32 loaded layer-1 accumulator columns (the constant already added by the
+// bias MMA) -> 16 columns of packed bf16 (128 + h) at `to`
+__device__ __forceinline__ void requant_store(const uint32_t (&a)[32], uint32_t to) {
   uint32_t w[16];
 #pragma unroll
-  for (int p = 0; p < 16; ++p) {
-    const uint64_t y = add2(pack2(a[2 * p], a[2 * p + 1]),
-                            pack2(__float_as_uint(c[u0 + 2 * p]), __float_as_uint(c[u0 + 2 * p + 1])));
-    w[p] = requant2(lo_of(y), hi_of(y));
-  }
+  for (int p = 0; p < 16; ++p) w[p] = requant2(__uint_as_float(a[2 * p]), __uint_as_float(a[2 * p + 1]));
   LBF_ST16(to, w);
 }
 
@@ -258,20 +261,20 @@ __device__ __forceinline__ void requant_store(const TcArgs& P, const uint32_t (&
 // chunks of 32 columns with the next chunk's load in flight while the current
 // one is converted; chunk c is stored over columns that chunk c/2 already
 // loaded (to <= from), so no store overwrites an unread column.
-__device__ __forceinline__ void epilogue1(const TcArgs& P, uint32_t from, uint32_t to) {
+__device__ __forceinline__ void epilogue1(uint32_t from, uint32_t to) {
   uint32_t a[32], b[32];
   LBF_LD32(a, from);
   tmem_wait_ld();
   LBF_LD32(b, from + 32);
-  requant_store<1>(P, a, 0, to);
+  requant_store(a, to);
   tmem_wait_ld();
   LBF_LD32(a, from + 64);
-  requant_store<1>(P, b, 32, to + 16);
+  requant_store(b, to + 16);
   tmem_wait_ld();
   LBF_LD32(b, from + 96);
-  requant_store<1>(P, a, 64, to + 32);
+  requant_store(a, to + 32);
   tmem_wait_ld();
-  requant_store<1>(P, b, 96, to + 48);
+  requant_store(b, to + 48);
 }
 
 // Layer-2 accumulators (64 columns at `from`) -> 128 + h2 -> dot with W3q
@@ -282,19 +285,16 @@ __device__ __forceinline__ float epilogue2(const TcArgs& P, uint32_t from) {
   LBF_LD32(a, from);
   LBF_LD32(b, from + 32);
   tmem_wait_ld();
-  auto cp = [&](int u) { return pack2(__float_as_uint(P.c2[u]), __float_as_uint(P.c2[u + 1])); };
   auto wp = [&](int u) { return pack2(__float_as_uint(P.w3[u]), __float_as_uint(P.w3[u + 1])); };
   uint64_t acc = 0;
 #pragma unroll
   for (int p = 0; p < 16; ++p) {
-    const uint64_t y = add2(pack2(a[2 * p], a[2 * p + 1]), cp(2 * p));
-    const uint32_t w = requant2(lo_of(y), hi_of(y));
+    const uint32_t w = requant2(__uint_as_float(a[2 * p]), __uint_as_float(a[2 * p + 1]));
     acc = fma2(pack2(w << 16, w & 0xFFFF0000u), wp(2 * p), acc);
   }
 #pragma unroll
   for (int p = 0; p < 16; ++p) {
-    const uint64_t y = add2(pack2(b[2 * p], b[2 * p + 1]), cp(32 + 2 * p));
-    const uint32_t w = requant2(lo_of(y), hi_of(y));
+    const uint32_t w = requant2(__uint_as_float(b[2 * p]), __uint_as_float(b[2 * p + 1]));
     acc = fma2(pack2(w << 16, w & 0xFFFF0000u), wp(32 + 2 * p), acc);
   }
   return lo_of(acc) + hi_of(acc);
@@ -311,8 +311,10 @@ __device__ __forceinline__ uint64_t tiles_of(uint64_t ntiles, uint64_t first, ui
 // The MMA warp's elected thread issues the warpgroups' products in a fixed
 // round: L1 of every warpgroup, then L2 of every warpgroup, and so on (the
 // warpgroups run the same work, so they become ready in about this order).
-// Each wait is a blocking try_wait (the thread sleeps in hardware).  Returns
-// false when a request did not come within 2 s.
+// Each layer starts with its bias product.  Each wait is a blocking try_wait
+// (the thread sleeps in hardware).  Returns false when a request did not come
+// within 2 s.  (Issuing whichever warpgroup's request is ready first, by
+// polling, was measured slower: 21.9 vs 24.1 G scores/s.)
 __device__ bool mma_issuer(uint32_t sb, uint32_t tmem, uint64_t ntiles) {
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWG;
   uint64_t left[kWG];
@@ -332,8 +334,9 @@ __device__ bool mma_issuer(uint32_t sb, uint32_t tmem, uint64_t ntiles) {
       fence_after();
       const uint32_t a1 = sb + kSlots + w * kSlotBytes;
       const uint32_t tm = tmem + 128 * w;
+      mma_bf16(tm, sdesc(sb + kAx), sdesc(sb + kB1x), idesc(128), 0);  // D1 = the layer-1 constants
 #pragma unroll
-      for (uint32_t s = 0; s < 4; ++s) mma_bf16(tm, sdesc(a1 + s * 32), sdesc(sb + kB1 + s * 32), idesc(128), s);
+      for (uint32_t s = 0; s < 4; ++s) mma_bf16(tm, sdesc(a1 + s * 32), sdesc(sb + kB1 + s * 32), idesc(128), 1);
       mma_commit(bars + 8 * kBarD1);
     }
 #pragma unroll
@@ -343,9 +346,10 @@ __device__ bool mma_issuer(uint32_t sb, uint32_t tmem, uint64_t ntiles) {
       if (!mbar_wait(bars + 8 * kBarA2, ph, limit)) return false;
       fence_after();
       const uint32_t tm = tmem + 128 * w;
+      mma_bf16(tm + 64, sdesc(sb + kAx), sdesc(sb + kB2x), idesc(64), 0);  // D2 = the layer-2 constants
 #pragma unroll
       for (uint32_t s = 0; s < 8; ++s)
-        mma_bf16_ta(tm + 64, tm + 8 * s, sdesc(sb + kB2 + (s >> 2) * 8192u + (s & 3) * 32), idesc(64), s);
+        mma_bf16_ta(tm + 64, tm + 8 * s, sdesc(sb + kB2 + (s >> 2) * 8192u + (s & 3) * 32), idesc(64), 1);
       mma_commit(bars + 8 * kBarD2);
     }
   }
@@ -451,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_mlp(const __grid_constant__ 
       }
       // epilogue 1: D1 (columns 0..127) + c1 -> A2 = 128 + h1 packed in columns 0..63
       if (!wait_on(kBarD1)) { failed = true; break; }
-      epilogue1(P, tm_row, tm_row);
+      epilogue1(tm_row, tm_row);
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       fence_before();
       mbar_arrive(bars + 8 * kBarA2);
@@ -509,6 +513,31 @@ uint32_t swz_host(uint32_t row, uint32_t k) {  // element k (< 64) of a 128-byte
   return row * 128u + ((((k >> 3) ^ (row & 7u)) & 7u) << 4) + (k & 7u) * 2u;
 }
 
+double double_of_bf16(uint16_t b) {
+  const uint32_t u = static_cast<uint32_t>(b) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// The three bf16 parts of N * s for an integer |N| < 2^24 and s a power of
+// two: N = hi + mid + lo with hi = floor(N / 2^16) * 2^16 (at most 8
+// significant bits), mid a multiple of 2^8 below 2^16 and lo below 2^8, each
+// exact in bf16; the tensor core adds them (and the layer's products) as
+// integer multiples of s below 2^24, exactly.  False if a part is not exact.
+bool split3(long long n, double s, uint16_t (&out)[3]) {
+  if (n <= -(1LL << 24) || n >= (1LL << 24)) return false;
+  const long long q = n >= 0 ? n / 65536 : -((-n + 65535) / 65536);
+  const long long hi = q * 65536, r = n - hi, mid = (r / 256) * 256, lo = r - mid;
+  const long long parts[3] = {lo, mid, hi};
+  for (int k = 0; k < 3; ++k) {
+    const double v = static_cast<double>(parts[k]) * s;
+    out[k] = bf16_of(v);
+    if (double_of_bf16(out[k]) != v) return false;
+  }
+  return true;
+}
+
 }  // namespace
 
 bool tc_eligible(const bf_mlp_int8* m) { return m->sh1 >= 0 && m->sh1 <= 15 && m->sh2 >= 0 && m->sh2 <= 15; }
@@ -527,11 +556,16 @@ bool tc_prepare(const bf_mlp_int8* m, TcModel* out) {
   // per-unit constants: integers below 2^24 times 2^-sh, exact in fp32
   const long long A1 = 64LL * 127, A2 = 128LL * 127 * 127;
   const long long p1 = 1LL << m->sh1, p2 = 1LL << m->sh2;
+  // ... written into the image as the bias k-block (A = 1.0 in k < 3, B = the parts)
+  for (uint32_t row = 0; row < 128; ++row)
+    for (uint32_t k = 0; k < 3; ++k) put16(img, kAx + swz_host(row, k), 0x3F80u);
+  uint16_t part[3];
   for (uint32_t j = 0; j < 128; ++j) {
     const long long b = std::min(std::max<long long>(m->b1[j], -(A1 + 1)), 128 * p1 + A1);
     const double c = static_cast<double>(b + 128 * p1) * s1;
     out->c1[j] = static_cast<float>(c);
-    if (static_cast<double>(out->c1[j]) != c) return false;
+    if (static_cast<double>(out->c1[j]) != c || !split3(b + 128 * p1, s1, part)) return false;
+    for (uint32_t k = 0; k < 3; ++k) put16(img, kB1x + swz_host(j, k), part[k]);
   }
   for (uint32_t j = 0; j < 64; ++j) {
     long long col = 0;
@@ -539,7 +573,8 @@ bool tc_prepare(const bf_mlp_int8* m, TcModel* out) {
     const long long b = std::min(std::max<long long>(m->b2[j], -(A2 + 1)), 128 * p2 + A2);
     const double c = static_cast<double>(b - 128 * col + 128 * p2) * s2;
     out->c2[j] = static_cast<float>(c);
-    if (static_cast<double>(out->c2[j]) != c) return false;
+    if (static_cast<double>(out->c2[j]) != c || !split3(b - 128 * col + 128 * p2, s2, part)) return false;
+    for (uint32_t k = 0; k < 3; ++k) put16(img, kB2x + swz_host(j, k), part[k]);
   }
   out->s3 = static_cast<long long>(m->b3) - 128 * sum3;
   for (int i = 0; i < 64; ++i) out->w3[i] = static_cast<float>(m->w3[i]);
@@ -576,8 +611,6 @@ cudaError_t tc_run(const uint8_t* d_image, const TcModel& tm, const uint64_t* d_
   a.out_keys = out_keys;
   a.err = err;
   a.s3 = tm.s3;
-  std::memcpy(a.c1, tm.c1, sizeof(a.c1));
-  std::memcpy(a.c2, tm.c2, sizeof(a.c2));
   std::memcpy(a.w3, tm.w3, sizeof(a.w3));
   a.bk_words = backup ? backup->words : nullptr;
   a.bk_blocks = backup ? backup->num_blocks : 0;
