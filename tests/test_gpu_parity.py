@@ -467,6 +467,43 @@ def test_phase_timing_counts_every_launch(torch):
     f.close()
 
 
+@pytest.mark.parametrize("buf", ["pinned", "pageable_staged"])
+def test_phase_timing_of_staged_host_passes(torch, buf):
+    """The host_stage phase of staged host-buffer calls: with the staging
+    kernel it counts exactly its launches (as planned per pass), with the
+    copy engine (staging forced) none; either way it has a positive time,
+    and every filter-kernel launch is counted in its own phase."""
+    geom = oracle.Geometry(num_blocks=(1 << 14) + 77, block_bits=256, word_bits=32, k=8, seed=13)
+    ins = synthkeys.insert_keys(150_001, seed=99)
+    q, _ = synthkeys.mixed_queries(150_001, 30_000, 60_001, seed_insert=99)
+    ref = oracle.SBF(geom)
+    ref.add(ins)
+    h_ins, h_q, h_out = host_buffers(torch, buf, ins, q, np.zeros(q.size, dtype=np.uint8))
+    f = gpu_filter(geom, torch)
+    f.set_partition(mode=1, slice_log2=16, lookup_mode=1)
+    if buf == "pageable_staged":
+        f.set_staging(mode="staged")
+    f.set_timing(True)
+    f.add_host(h_ins)
+    n_add = f.last_launches()
+    t = f.timing()
+    _, extra = host_plan(buf, ins.size, 1 << 32, h_ins)
+    assert t["host_stage"]["launches"] == sum(extra) and t["host_stage"]["ms"] > 0
+    assert t["partition_add"]["launches"] + t["record_insert"]["launches"] + sum(extra) == n_add
+    f.contains_host(h_q, h_out)
+    n_con = f.last_launches()
+    t = f.timing()
+    _, extra = host_plan(buf, q.size, 1 << 28, h_q)
+    assert t["host_stage"]["launches"] == sum(extra) and t["host_stage"]["ms"] > 0
+    assert sum(t[k]["launches"] for k in ("partition_lookup", "record_probe", "bitmap_expand")) + sum(extra) == n_con
+    torch.cuda.synchronize()
+    assert np.array_equal(words_np(f), ref.as_bytes())
+    assert np.array_equal(h_out, ref.contains(q))
+    assert f.device_status() == 0
+    f.set_timing(False)
+    f.close()
+
+
 @pytest.mark.parametrize("buf", ["pinned", "pinned_direct", "pageable", "pageable_staged"])
 def test_partitioned_lookup_from_host_queries(torch, buf):
     """Slice-partitioned lookup of host queries in passes: through two
