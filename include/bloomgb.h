@@ -40,7 +40,10 @@
  *       salt32[i] = (salt64[i] >> 32) | 1.
  *   - Thread safety: distinct filters may be used from distinct host threads.
  *     Calls on one filter from several host threads must be serialized by the
- *     caller.
+ *     caller.  A filter's slice-partitioned and host-buffer calls use
+ *     workspaces and internal streams of that filter, so calls on one filter
+ *     enqueued on different streams must be ordered by the caller (one
+ *     stream, or events between them).
  */
 #ifndef BLOOMGB_H
 #define BLOOMGB_H
