@@ -98,7 +98,8 @@ struct bf_server {
   uint32_t threads = 256;
   uint32_t max_grid = 0;         // batched lookup CTAs when the copy engines stage
   uint32_t max_grid_beside = 0;  // ... when staging kernels share the SMs (one CTA slot per SM left)
-  uint32_t stage_ctas = 0;       // staging kernel CTAs (one per SM)
+  uint32_t gather_ctas = 0;      // key gather CTAs (two per SM: about 2.5 MB of host loads in flight)
+  uint32_t scatter_ctas = 0;     // result scatter CTAs (one per SM)
   int pageable_access = 0;       // the device reads pageable host memory
   uint32_t max_reqs = 0;
   // key / result arena: a ring of `cap` key slots
@@ -186,7 +187,7 @@ bool launch_batch(bf_server* s, int slot) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_src, L.h_src, sizeof(void*) * nr, cudaMemcpyHostToDevice, s->h2d);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_dst, L.h_dst, sizeof(void*) * nr, cudaMemcpyHostToDevice, s->h2d);
     if (e == cudaSuccess)
-      e = launch_batch_gather(L.d_desc, L.d_begin, static_cast<uint32_t>(nr), chunks, L.d_src, s->d_keys, s->stage_ctas,
+      e = launch_batch_gather(L.d_desc, L.d_begin, static_cast<uint32_t>(nr), chunks, L.d_src, s->d_keys, s->gather_ctas,
                               s->h2d);
   }
   if (e == cudaSuccess) e = cudaEventRecord(L.copied, s->h2d);
@@ -205,7 +206,7 @@ bool launch_batch(bf_server* s, int slot) {
   if (sm) {
     if (e == cudaSuccess)
       e = launch_batch_scatter(L.d_desc, L.d_begin, static_cast<uint32_t>(nr), chunks, L.d_dst, s->d_out,
-                               s->stage_ctas, s->d2h);
+                               s->scatter_ctas, s->d2h);
   } else {
     for (size_t i = 0; i < nr && e == cudaSuccess; ++i) {
       Request* r = L.reqs[i];
@@ -316,7 +317,9 @@ bf_status bf_server_create(const bf_params* params, const bf_batch_filter* filte
   const int per_sm = e == cudaSuccess ? kernel_resident_ctas(k->fn, s->threads, s->device) : 0;
   s->max_grid = static_cast<uint32_t>(std::max(1, sms * std::max(per_sm, 1)));
   s->max_grid_beside = static_cast<uint32_t>(std::max(1, sms * std::max(per_sm - 1, 1)));
-  s->stage_ctas = static_cast<uint32_t>(std::max(1, sms));
+  // two gather CTAs per SM measured faster than one and four (20.9 / 19.7 / 20.3 G keys/s capacity)
+  s->gather_ctas = static_cast<uint32_t>(std::max(1, 2 * sms));
+  s->scatter_ctas = static_cast<uint32_t>(std::max(1, sms));
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->pageable_access, cudaDevAttrPageableMemoryAccess, s->device);
   int least = 0, greatest = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
