@@ -391,10 +391,10 @@ bf_status bf_batch_info(const bf_batch* b, uint32_t* nfilters, uint64_t* total_k
    (filter, host keys, host results) arriving over time.  A worker thread
    admits pending requests in arrival order while a device key arena of
    arena_keys slots, the per-launch request limit and the launch's share of
-   the arena (a third; a larger request goes alone) have room, copies their
+   the arena (a quarter; a larger request goes alone) have room, copies their
    keys in, runs one batched lookup launch over all of them (across filters),
    copies each request's results back, and frees the arena in completion
-   order; up to three launches are in flight.  When the kernels can address
+   order; up to four launches are in flight.  When the kernels can address
    every request's buffers of a launch (pinned memory, or any host memory on
    a GPU with pageable memory access, and 8-byte aligned keys), staging
    kernels on high-priority streams gather the keys and scatter the results;

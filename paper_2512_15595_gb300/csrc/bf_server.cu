@@ -41,7 +41,7 @@ using namespace bloomgb;
 
 namespace {
 
-constexpr int kMaxInflight = 3;
+constexpr int kMaxInflight = 4;
 using Clock = std::chrono::steady_clock;
 
 double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
