@@ -187,11 +187,12 @@ bf_status bf_contains(const bf_filter* f, const uint64_t* d_keys, uint64_t n, ui
        keys are copied into one of two device staging slots, by a staging
        kernel on one CTA slot per SM when the device can address them, else
        by the copy engine, while `stream` partitions and inserts (or probes)
-       the previous pass from device memory; bf_contains_host returns each
-       pass's results by the copy engine on an internal copy-out stream, so
-       the host link stays busy in both directions.  The staging slots (2 x 8
-       bytes per key of a pass, plus 2 x 1 byte for lookups) are kept until
-       bf_set_staging or bf_destroy.  Without memory for them the call takes
+       the previous pass from device memory; for bf_contains_host the copy
+       engine returns each pass's results on an internal copy-out stream, so
+       the host link stays busy in both directions (into a pageable h_out
+       the device can address, the kernels write the results in place).
+       The staging slots (2 x 8 bytes per key of a pass, plus 2 x 1 byte for
+       lookups) are kept until bf_set_staging or bf_destroy.  Without memory for them the call takes
        one of the next two ways;
      direct: otherwise, when the device can address the buffers, the kernels
        read the keys and write the results in place over the CPU-GPU link; a

@@ -922,6 +922,17 @@ void release_pipeline(bf_filter* f) {
     }
 }
 
+// Is this host buffer page-locked (cudaHostAlloc / cudaHostRegister)?  The
+// copy engine then copies to it asynchronously.
+bool is_page_locked(const void* h) {
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, h) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeHost;
+}
+
 bf_status ensure_stream(cudaStream_t* st) {
   cudaError_t e;
   if (!*st && (e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking)) != cudaSuccess)
@@ -1027,15 +1038,19 @@ bf_status launch_partitioned_staged(bf_filter* f, const uint64_t* h_keys, uint64
 
 // Lookup of host queries in passes staged through device memory: pass i's
 // queries are copied into a staging slot on the copy-in stream (the staging
-// kernel when the kernels can address them, else the copy engine), the pass
-// runs on `stream` (partition, probes, expansion into the slot's result
-// bytes), and its results go back by the copy engine on the copy-out
-// stream, so both directions of the link stay busy while the device works.
-// Pass i + 2 refills slot i % 2 once pass i's partition has read its
-// queries, and overwrites its results once they have reached the host.
+// kernel when the kernels can address the buffers, else the copy engine),
+// and the pass runs on `stream` (partition, probes, expansion into the
+// slot's result bytes); the copy engine takes the results back on the
+// copy-out stream, so both directions of the link stay busy while the device
+// works.  For a pageable h_out the kernels can address (results_in_place),
+// whose copy would wait for the results before returning, the expansion
+// writes into h_out itself (slower: about 80 GB/s of byte stores over the
+// link, on `stream`).  Pass i + 2 refills slot i % 2 once pass i's partition
+// has read its queries, and overwrites its results once they have reached
+// the host.
 // Returns BF_ENOMEM, having queued nothing, when the workspaces do not fit.
 bf_status launch_contains_partitioned_staged(bf_filter* f, const uint64_t* h_keys, uint64_t n, uint8_t* h_out,
-                                             cudaStream_t stream, bool sm_copy) {
+                                             cudaStream_t stream, bool sm_copy, bool results_in_place) {
   const PartPlan pl = part_plan(f);
   const uint64_t pass =
       host_pass_keys(n, std::max<uint64_t>(kHostPasses, f->part.passes), f->part.lookup_chunk_keys);
@@ -1043,7 +1058,7 @@ bf_status launch_contains_partitioned_staged(bf_filter* f, const uint64_t* h_key
   bf_status s = prepare_lookup(f, pl, pass, sm_copy ? kStagedPartCtas : 1 << 30, sm_copy, &L);
   if (s != BF_OK) return s;
   const uint64_t kbytes = (pass * 8 + 255) / 256 * 256;
-  const uint64_t slot = kbytes + (pass + 255) / 256 * 256;
+  const uint64_t slot = kbytes + (results_in_place ? 0 : (pass + 255) / 256 * 256);
   if (ensure_ws(&f->look_ws, &f->look_ws_bytes, L.ws_bytes) != BF_OK ||
       ensure_ws(&f->hstage, &f->hstage_bytes, 2 * slot) != BF_OK)
     return BF_ENOMEM;
@@ -1059,18 +1074,19 @@ bf_status launch_contains_partitioned_staged(bf_filter* f, const uint64_t* h_key
     const uint64_t cnt = std::min(pass, n - lo);
     char* base = static_cast<char*>(f->hstage) + w * slot;
     uint64_t* d_keys = reinterpret_cast<uint64_t*>(base);
-    uint8_t* d_res = reinterpret_cast<uint8_t*>(base + kbytes);
+    uint8_t* d_res = results_in_place ? h_out + lo : reinterpret_cast<uint8_t*>(base + kbytes);
     if (i >= 2 && (e = cudaStreamWaitEvent(f->h2d, f->ev_consumed[w], 0)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamWaitEvent");
     if ((s = stage_keys(f, h_keys + lo, d_keys, cnt, sms, sm_copy)) != BF_OK) return s;
     if ((e = cudaEventRecord(f->ev_copied[w], f->h2d)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     if ((e = cudaStreamWaitEvent(stream, f->ev_copied[w], 0)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamWaitEvent");
-    if (i >= 2 && (e = cudaStreamWaitEvent(stream, f->ev_drained[w], 0)) != cudaSuccess)
+    if (!results_in_place && i >= 2 && (e = cudaStreamWaitEvent(stream, f->ev_drained[w], 0)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamWaitEvent");
     if ((s = launch_lookup_pass(f, L, pl, d_keys, cnt, d_res, static_cast<char*>(f->look_ws), stream, stream,
                                 f->ev_consumed[w])) != BF_OK)
       return s;
+    if (results_in_place) continue;
     if ((e = cudaEventRecord(f->ev_computed[w], stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     if ((e = cudaStreamWaitEvent(f->d2h, f->ev_computed[w], 0)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamWaitEvent");
@@ -1080,7 +1096,7 @@ bf_status launch_contains_partitioned_staged(bf_filter* f, const uint64_t* h_key
     last = w;
   }
   // the copy-out stream is FIFO: its last event covers every result copy
-  if ((e = cudaStreamWaitEvent(stream, f->ev_drained[last], 0)) != cudaSuccess)
+  if (!results_in_place && (e = cudaStreamWaitEvent(stream, f->ev_drained[last], 0)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamWaitEvent");
   return BF_OK;
 }
@@ -1136,7 +1152,8 @@ bf_status host_pipeline(bf_filter* f, int op, const uint64_t* h_keys, uint64_t n
   const bool part = add ? use_partitioned(f, n) : use_partitioned_lookup(f, n);
   if (part && (f->host_access != BF_HOST_DIRECT || !in_place)) {
     const bf_status s = add ? launch_partitioned_staged(f, h_keys, n, stream, in_place)
-                            : launch_contains_partitioned_staged(f, h_keys, n, h_out, stream, in_place);
+                            : launch_contains_partitioned_staged(f, h_keys, n, h_out, stream, in_place,
+                                                                 in_place && !is_page_locked(h_out));
     if (s != BF_ENOMEM) return s;  // else nothing was queued: a path with less memory
   }
   if (in_place) {
