@@ -1084,7 +1084,11 @@ def run_serving(args):
             results.append({"offered_gkeys_s": load_gkeys, "requests_per_s": rate,
                             "sustained_gkeys_s": st["keys"] / st["span_s"] / 1e9 if st["span_s"] else 0.0,
                             "p50_ms": st["p50_s"] * 1e3, "p99_ms": st["p99_s"] * 1e3, "max_ms": st["max_s"] * 1e3,
-                            "requests": st["requests"], "launches": st["launches"]})
+                            "requests": st["requests"], "launches": st["launches"],
+                            # device time of each stage over the served span: how busy each stream was
+                            "busy": {k: st[k + "_s"] / st["span_s"] if st["span_s"] else 0.0
+                                     for k in ("stage_in", "lookup", "stage_out")},
+                            "stage_in_gbs": 8 * st["keys"] / st["stage_in_s"] / 1e9 if st["stage_in_s"] else 0.0})
             print(json.dumps(results[-1]), file=sys.stderr, flush=True)
     finally:
         _lib.bf_server_destroy(srv)

@@ -412,6 +412,9 @@ typedef struct {
     double p50_s, p99_s, mean_s, max_s;  /* request latency: submit -> results on the host */
     double span_s;         /* first submit -> last completion */
     double offered_s;      /* bf_server_run_poisson: the arrival window */
+    /* device time summed over the completed launches (CUDA events on each
+       stream): keys into the arena, batched lookup kernels, results out */
+    double stage_in_s, lookup_s, stage_out_s;
 } bf_server_stats;
 bf_status bf_server_create(const bf_params* params, const bf_batch_filter* filters /* d_words, num_blocks */,
                            uint32_t nfilters, uint64_t arena_keys, uint32_t max_requests_per_launch,

@@ -94,7 +94,8 @@ class bf_batch_filter(ctypes.Structure):
 class bf_server_stats_t(ctypes.Structure):
     _fields_ = [("requests", ctypes.c_uint64), ("keys", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double), ("mean_s", ctypes.c_double),
-                ("max_s", ctypes.c_double), ("span_s", ctypes.c_double), ("offered_s", ctypes.c_double)]
+                ("max_s", ctypes.c_double), ("span_s", ctypes.c_double), ("offered_s", ctypes.c_double),
+                ("stage_in_s", ctypes.c_double), ("lookup_s", ctypes.c_double), ("stage_out_s", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -63,6 +63,9 @@ struct Launch {
   cudaEvent_t done = nullptr;     // results are on the host
   cudaEvent_t copied = nullptr;   // keys are on the device
   cudaEvent_t looked = nullptr;   // kernel finished
+  // timing: start of each stage on its stream (the stage ends at copied,
+  // looked and done)
+  cudaEvent_t in0 = nullptr, look0 = nullptr, out0 = nullptr;
   BatchFilter* h_desc = nullptr;  // pinned
   uint64_t* h_begin = nullptr;    // pinned
   const uint64_t** h_src = nullptr;  // pinned: each request's host keys
@@ -116,6 +119,7 @@ struct bf_server {
   uint64_t next_ticket = 1;
   std::vector<double> latencies;  // completed requests since the last stats reset
   uint64_t keys_done = 0, reqs_done = 0, launches_done = 0;
+  double stage_in_s = 0, lookup_s = 0, stage_out_s = 0;  // device time of completed launches
   double first_submit = 0, last_done = 0;
   std::thread worker;
   std::atomic<bool> stop{false};
@@ -138,6 +142,11 @@ void complete_front(bf_server* s) {
   }
   s->last_done = t;
   s->launches_done += 1;
+  float ms = 0;
+  if (cudaEventElapsedTime(&ms, L.in0, L.copied) == cudaSuccess) s->stage_in_s += ms * 1e-3;
+  if (cudaEventElapsedTime(&ms, L.look0, L.looked) == cudaSuccess) s->lookup_s += ms * 1e-3;
+  if (cudaEventElapsedTime(&ms, L.out0, L.done) == cudaSuccess) s->stage_out_s += ms * 1e-3;
+  cudaGetLastError();
   s->ring.release(L.arena_used, L.arena_end);
   L.reqs.clear();
   L.busy = false;
@@ -168,6 +177,7 @@ bool launch_batch(bf_server* s, int slot) {
   uint64_t chunks = 0;
   bool sm = true;
   for (const Request* r : L.reqs) sm = sm && r->addressable;
+  e = cudaEventRecord(L.in0, s->h2d);
   for (size_t i = 0; i < L.reqs.size(); ++i) {
     Request* r = L.reqs[i];
     const BatchFilter& f = s->filters[r->filter];
@@ -192,6 +202,7 @@ bool launch_batch(bf_server* s, int slot) {
   }
   if (e == cudaSuccess) e = cudaEventRecord(L.copied, s->h2d);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, L.copied, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(L.look0, s->stream);
   if (e == cudaSuccess && chunks) {
     BatchArgs a{L.d_desc, L.d_begin, static_cast<uint32_t>(nr), chunks, s->d_keys, s->d_out,
                 s->p.seed + 0x27D4EB2F165667C5ull + 8ull, 0u};
@@ -203,6 +214,7 @@ bool launch_batch(bf_server* s, int slot) {
   }
   if (e == cudaSuccess) e = cudaEventRecord(L.looked, s->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->d2h, L.looked, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(L.out0, s->d2h);
   if (sm) {
     if (e == cudaSuccess)
       e = launch_batch_scatter(L.d_desc, L.d_begin, static_cast<uint32_t>(nr), chunks, L.d_dst, s->d_out,
@@ -317,7 +329,7 @@ bf_status bf_server_create(const bf_params* params, const bf_batch_filter* filte
   const int per_sm = e == cudaSuccess ? kernel_resident_ctas(k->fn, s->threads, s->device) : 0;
   s->max_grid = static_cast<uint32_t>(std::max(1, sms * std::max(per_sm, 1)));
   s->max_grid_beside = static_cast<uint32_t>(std::max(1, sms * std::max(per_sm - 1, 1)));
-  // two gather CTAs per SM measured faster than one and four (20.9 / 19.7 / 20.3 G keys/s capacity)
+  // two gather CTAs per SM: faster than one and four, as fast as three
   s->gather_ctas = static_cast<uint32_t>(std::max(1, 2 * sms));
   s->scatter_ctas = static_cast<uint32_t>(std::max(1, sms));
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->pageable_access, cudaDevAttrPageableMemoryAccess, s->device);
@@ -331,9 +343,12 @@ bf_status bf_server_create(const bf_params* params, const bf_batch_filter* filte
   if (e == cudaSuccess) e = cudaMalloc(&s->d_out, arena_keys);
   for (int i = 0; i < kMaxInflight && e == cudaSuccess; ++i) {
     Launch& L = s->launches[i];
-    e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.copied, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.looked, cudaEventDisableTiming);
+    e = cudaEventCreate(&L.done);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.copied);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.looked);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.in0);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.look0);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.out0);
     if (e == cudaSuccess) e = cudaHostAlloc(&L.h_desc, sizeof(BatchFilter) * s->max_reqs, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&L.h_begin, sizeof(uint64_t) * (s->max_reqs + 1), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&L.h_src, sizeof(void*) * s->max_reqs, cudaHostAllocDefault);
@@ -365,6 +380,8 @@ bf_status bf_server_destroy(bf_server* s) {
     if (L.done) cudaEventDestroy(L.done);
     if (L.copied) cudaEventDestroy(L.copied);
     if (L.looked) cudaEventDestroy(L.looked);
+    for (cudaEvent_t ev : {L.in0, L.look0, L.out0})
+      if (ev) cudaEventDestroy(ev);
     if (L.h_desc) cudaFreeHost(L.h_desc);
     if (L.h_begin) cudaFreeHost(L.h_begin);
     if (L.h_src) cudaFreeHost(L.h_src);
@@ -442,10 +459,14 @@ bf_status bf_server_get_stats(bf_server* s, int reset, bf_server_stats* out) {
     out->mean_s = sum / v.size();
   }
   out->span_s = s->last_done > s->first_submit ? s->last_done - s->first_submit : 0;
+  out->stage_in_s = s->stage_in_s;
+  out->lookup_s = s->lookup_s;
+  out->stage_out_s = s->stage_out_s;
   if (reset) {
     s->latencies.clear();
     s->keys_done = s->reqs_done = s->launches_done = 0;
     s->first_submit = s->last_done = 0;
+    s->stage_in_s = s->lookup_s = s->stage_out_s = 0;
   }
   return s->error == cudaSuccess ? BF_OK : BF_ECUDA;
 }

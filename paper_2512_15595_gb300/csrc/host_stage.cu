@@ -73,13 +73,52 @@ __device__ __forceinline__ ChunkRef<T> chunk_ref(const BatchFilter* __restrict__
           static_cast<uint32_t>(left < kBatchChunk ? left : kBatchChunk)};
 }
 
-// GATHER: host keys -> arena; else arena results -> host.  Warp w walks
-// chunks [w * per, (w + 1) * per), two at a time: all loads of both chunks,
-// then the stores (lane l takes elements l, l + 32, l + 64, l + 96).
-template <bool GATHER, typename T>
+// Keys of one chunk as 16-byte host loads: the chunk's keys from `h`
+// (8-byte aligned) split into an optional head key (when h is 8 mod 16), 64
+// or fewer 16-byte pairs, and an optional tail key; lane l loads pairs l and
+// l + 32, lane 0 the head, lane 1 the tail.  Stores into the arena are
+// 8-byte (any arena offset).
+struct KeyChunk {
+  ulonglong2 v[2];
+  uint64_t head, tail;
+};
+
+__device__ __forceinline__ void load_chunk(const uint64_t* __restrict__ h, uint32_t cnt, uint32_t lane, KeyChunk& k) {
+  const uint32_t mis = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(h) >> 3) & 1u;
+  const uint32_t body = cnt - mis, npairs = body >> 1;
+  const ulonglong2* hp = reinterpret_cast<const ulonglong2*>(h + mis);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const uint32_t p = lane + 32u * j;
+    if (p < npairs) k.v[j] = __ldcs(hp + p);
+  }
+  if (mis && lane == 0) k.head = __ldcs(h);
+  if ((body & 1u) && lane == 1) k.tail = __ldcs(h + mis + 2 * npairs);
+}
+
+__device__ __forceinline__ void store_chunk(const uint64_t* h, uint64_t* __restrict__ a, uint32_t cnt, uint32_t lane,
+                                            const KeyChunk& k) {
+  const uint32_t mis = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(h) >> 3) & 1u;
+  const uint32_t body = cnt - mis, npairs = body >> 1;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const uint32_t p = lane + 32u * j;
+    if (p < npairs) {
+      __stcs(a + mis + 2 * p, k.v[j].x);
+      __stcs(a + mis + 2 * p + 1, k.v[j].y);
+    }
+  }
+  if (mis && lane == 0) __stcs(a, k.head);
+  if ((body & 1u) && lane == 1) __stcs(a + mis + 2 * npairs, k.tail);
+}
+
+// Gather of a batch's keys from host memory into the arena: warp w walks
+// chunks [w * per, (w + 1) * per), two at a time (one search for its first
+// request, then the owner advanced), all loads of both chunks before the
+// stores; 16-byte host loads (half the requests of 8-byte ones over the link).
 __global__ void __launch_bounds__(kHostStageThreads, 8)
-    batch_stage_kernel(const BatchFilter* __restrict__ desc, const uint64_t* __restrict__ begin, uint32_t nreq,
-                       uint64_t chunks, const void* const* __restrict__ host, T* __restrict__ arena) {
+    batch_gather_kernel(const BatchFilter* __restrict__ desc, const uint64_t* __restrict__ begin, uint32_t nreq,
+                        uint64_t chunks, const void* const* __restrict__ host, uint64_t* __restrict__ arena) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
   const uint64_t w = static_cast<uint64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
@@ -87,7 +126,6 @@ __global__ void __launch_bounds__(kHostStageThreads, 8)
   uint64_t c = w * per;
   const uint64_t c_end = c + per < chunks ? c + per : chunks;
   if (c >= c_end) return;
-  // the last request whose first chunk is at or before c (begin[0] = 0 <= c < begin[nreq])
   uint32_t lo = 0, hi = nreq;
   while (hi - lo > 1) {
     const uint32_t mid = (lo + hi) / 2;
@@ -95,31 +133,67 @@ __global__ void __launch_bounds__(kHostStageThreads, 8)
     else hi = mid;
   }
   uint32_t r = lo;
-  constexpr uint32_t kStep = kBatchChunk / 4;  // 32: one element per lane per quarter chunk
   for (; c < c_end; c += 2) {
     r = owner(begin, r, c);
-    const ChunkRef<T> a = chunk_ref<T>(desc, begin, host, arena, r, c);
+    const ChunkRef<uint64_t> a = chunk_ref<uint64_t>(desc, begin, host, arena, r, c);
     const bool two = c + 1 < c_end;
     uint32_t r2 = r;
-    ChunkRef<T> b{nullptr, nullptr, 0};
+    ChunkRef<uint64_t> b{nullptr, nullptr, 0};
     if (two) {
       r2 = owner(begin, r, c + 1);
-      b = chunk_ref<T>(desc, begin, host, arena, r2, c + 1);
+      b = chunk_ref<uint64_t>(desc, begin, host, arena, r2, c + 1);
     }
-    T va[4], vb[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t i = lane + j * kStep;
-      if (i < a.cnt) va[j] = __ldcs(GATHER ? a.host + i : a.arena + i);
-      if (i < b.cnt) vb[j] = __ldcs(GATHER ? b.host + i : b.arena + i);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t i = lane + j * kStep;
-      if (i < a.cnt) __stcs(GATHER ? a.arena + i : a.host + i, va[j]);
-      if (i < b.cnt) __stcs(GATHER ? b.arena + i : b.host + i, vb[j]);
-    }
+    KeyChunk ka, kb;
+    load_chunk(a.host, a.cnt, lane, ka);
+    if (two) load_chunk(b.host, b.cnt, lane, kb);
+    store_chunk(a.host, a.arena, a.cnt, lane, ka);
+    if (two) store_chunk(b.host, b.arena, b.cnt, lane, kb);
     r = r2;
+  }
+}
+
+// Results of one chunk to host memory with 4-byte stores: the cnt result
+// bytes at `a` (device) go to `h` (host, any alignment) as head bytes up to
+// h's 4-byte boundary, 32 or fewer 4-byte words (lane l: word l, its bytes
+// loaded one by one from the device) and tail bytes (lane l: byte l).
+__device__ __forceinline__ void scatter_chunk(const uint8_t* __restrict__ a, uint8_t* __restrict__ h, uint32_t cnt,
+                                              uint32_t lane) {
+  const uint32_t lead = (4u - static_cast<uint32_t>(reinterpret_cast<uintptr_t>(h) & 3u)) & 3u;
+  const uint32_t head = lead < cnt ? lead : cnt;
+  const uint32_t nw = (cnt - head) >> 2, tail0 = head + 4 * nw;
+  if (lane < nw) {
+    const uint8_t* s = a + head + 4 * lane;
+    const uint32_t v = static_cast<uint32_t>(s[0]) | (static_cast<uint32_t>(s[1]) << 8) |
+                       (static_cast<uint32_t>(s[2]) << 16) | (static_cast<uint32_t>(s[3]) << 24);
+    __stcs(reinterpret_cast<uint32_t*>(h + head) + lane, v);
+  }
+  if (lane < head) h[lane] = a[lane];
+  if (lane < cnt - tail0) h[tail0 + lane] = a[tail0 + lane];
+}
+
+// Scatter of a batch's results from the arena into host memory: warp w walks
+// chunks [w * per, (w + 1) * per), with 4-byte host stores.
+__global__ void __launch_bounds__(kHostStageThreads, 8)
+    batch_scatter_kernel(const BatchFilter* __restrict__ desc, const uint64_t* __restrict__ begin, uint32_t nreq,
+                         uint64_t chunks, const void* const* __restrict__ host, uint8_t* __restrict__ arena) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
+  const uint64_t w = static_cast<uint64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+  const uint64_t per = (chunks + warps - 1) / warps;
+  uint64_t c = w * per;
+  const uint64_t c_end = c + per < chunks ? c + per : chunks;
+  if (c >= c_end) return;
+  uint32_t lo = 0, hi = nreq;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (begin[mid] <= c) lo = mid;
+    else hi = mid;
+  }
+  uint32_t r = lo;
+  for (; c < c_end; ++c) {
+    r = owner(begin, r, c);
+    const ChunkRef<uint8_t> k = chunk_ref<uint8_t>(desc, begin, host, arena, r, c);
+    scatter_chunk(k.arena, k.host, k.cnt, lane);
   }
 }
 
@@ -163,8 +237,8 @@ cudaError_t launch_batch_gather(const BatchFilter* desc, const uint64_t* begin, 
                                 cudaStream_t stream) {
   if (chunks == 0) return cudaSuccess;
   if (ctas == 0 || nreq == 0) return cudaErrorInvalidValue;
-  batch_stage_kernel<true, uint64_t><<<ctas, kHostStageThreads, 0, stream>>>(
-      desc, begin, nreq, chunks, reinterpret_cast<const void* const*>(host), arena_keys);
+  batch_gather_kernel<<<ctas, kHostStageThreads, 0, stream>>>(desc, begin, nreq, chunks,
+                                                               reinterpret_cast<const void* const*>(host), arena_keys);
   return cudaGetLastError();
 }
 
@@ -172,8 +246,9 @@ cudaError_t launch_batch_scatter(const BatchFilter* desc, const uint64_t* begin,
                                  uint8_t* const* host, const uint8_t* arena_out, uint32_t ctas, cudaStream_t stream) {
   if (chunks == 0) return cudaSuccess;
   if (ctas == 0 || nreq == 0) return cudaErrorInvalidValue;
-  batch_stage_kernel<false, uint8_t><<<ctas, kHostStageThreads, 0, stream>>>(
-      desc, begin, nreq, chunks, reinterpret_cast<const void* const*>(host), const_cast<uint8_t*>(arena_out));
+  batch_scatter_kernel<<<ctas, kHostStageThreads, 0, stream>>>(desc, begin, nreq, chunks,
+                                                                reinterpret_cast<const void* const*>(host),
+                                                                const_cast<uint8_t*>(arena_out));
   return cudaGetLastError();
 }
 

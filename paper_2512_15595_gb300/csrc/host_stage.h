@@ -43,8 +43,10 @@ cudaError_t launch_host_stage(const uint64_t* src, uint64_t* dst, uint64_t n, ui
 // scatter: the 1-byte results from arena_out into host[r].  desc, begin and
 // host are device arrays; the host buffers must be addressable by the
 // kernels.  One warp walks a contiguous run of chunks (one search for its
-// first request), each lane four elements of a chunk, two chunks of loads
-// in flight; `ctas` CTAs of kHostStageThreads threads.
+// first request); the gather loads two chunks at a time as 16-byte host
+// loads (a single key at either end where the host address is 8 mod 16),
+// the scatter stores 4-byte words (single bytes up to the host address's
+// 4-byte boundary and at the end); `ctas` CTAs of kHostStageThreads threads.
 struct BatchFilter;
 cudaError_t launch_batch_gather(const BatchFilter* desc, const uint64_t* begin, uint32_t nreq, uint64_t chunks,
                                 const uint64_t* const* host, uint64_t* arena_keys, uint32_t ctas,

@@ -79,6 +79,7 @@ def test_server_answers_match_oracle(env):
         assert st["requests"] == 300 and st["keys"] == sum(r[5] for r in reqs)
         assert st["launches"] >= 300 // 7
         assert st["p50_s"] <= st["p99_s"] <= st["max_s"]
+        assert st["stage_in_s"] > 0 and st["lookup_s"] > 0 and st["stage_out_s"] > 0
     finally:
         L.bf_server_destroy(srv)
         for f in filters:
