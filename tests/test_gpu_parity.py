@@ -542,6 +542,32 @@ def test_partitioned_lookup_from_host_queries(torch, buf):
         f.close()
 
 
+@pytest.mark.parametrize("buf", ["pinned", "pageable", "pageable_staged"])
+def test_staged_host_passes_tiny_and_ragged(torch, buf):
+    """Staged host passes at their edges: 1, 7, 255, 257 and 4099 keys on a
+    slice-partitioned filter (a single short pass, the one-thread launch for
+    an odd last key, several ragged passes), built up call by call; bits
+    and answers as the oracle's after every call."""
+    geom = oracle.Geometry(num_blocks=(1 << 14) + 77, block_bits=256, word_bits=32, k=8, seed=31)
+    f = gpu_filter(geom, torch)
+    f.set_partition(mode=1, slice_log2=16, lookup_mode=1)
+    if buf == "pageable_staged":
+        f.set_staging(mode="staged")
+    ref = oracle.SBF(geom)
+    for i, n in enumerate((1, 7, 255, 257, 4099)):
+        ins = synthkeys.insert_keys(n, seed=200 + i)
+        q, _ = synthkeys.mixed_queries(n, max(1, n // 3), n, seed_insert=200 + i)
+        ref.add(ins)
+        h_ins, h_q, h_out = host_buffers(torch, buf, ins, q, np.zeros(q.size, dtype=np.uint8))
+        f.add_host(h_ins)
+        f.contains_host(h_q, h_out)
+        torch.cuda.synchronize()
+        assert np.array_equal(words_np(f), ref.as_bytes()), n
+        assert np.array_equal(h_out, ref.contains(q)), n
+    assert f.device_status() == 0
+    f.close()
+
+
 @pytest.mark.parametrize("partitioned", [False, True])
 def test_host_keys_at_an_odd_address(torch, partitioned):
     """Host keys 4 bytes off 8-byte alignment (no alignment is required of
