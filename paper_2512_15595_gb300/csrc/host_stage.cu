@@ -73,6 +73,28 @@ __device__ __forceinline__ ChunkRef<T> chunk_ref(const BatchFilter* __restrict__
           static_cast<uint32_t>(left < kBatchChunk ? left : kBatchChunk)};
 }
 
+// The run of chunks [c, c_end) of this warp (warp w of all: chunks
+// [w * per, (w + 1) * per)) and the request owning its first chunk, found
+// by binary search (begin[0] = 0 <= c < begin[nreq]).  False if the run is
+// empty.
+__device__ __forceinline__ bool warp_run(const uint64_t* __restrict__ begin, uint32_t nreq, uint64_t chunks,
+                                         uint64_t& c, uint64_t& c_end, uint32_t& r) {
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
+  const uint64_t w = static_cast<uint64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+  const uint64_t per = (chunks + warps - 1) / warps;
+  c = w * per;
+  c_end = c + per < chunks ? c + per : chunks;
+  if (c >= c_end) return false;
+  uint32_t lo = 0, hi = nreq;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (begin[mid] <= c) lo = mid;
+    else hi = mid;
+  }
+  r = lo;
+  return true;
+}
+
 // Keys of one chunk as 16-byte host loads: the chunk's keys from `h`
 // (8-byte aligned) split into an optional head key (when h is 8 mod 16), 64
 // or fewer 16-byte pairs, and an optional tail key; lane l loads pairs l and
@@ -120,19 +142,9 @@ __global__ void __launch_bounds__(kHostStageThreads, 8)
     batch_gather_kernel(const BatchFilter* __restrict__ desc, const uint64_t* __restrict__ begin, uint32_t nreq,
                         uint64_t chunks, const void* const* __restrict__ host, uint64_t* __restrict__ arena) {
   const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
-  const uint64_t w = static_cast<uint64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
-  const uint64_t per = (chunks + warps - 1) / warps;
-  uint64_t c = w * per;
-  const uint64_t c_end = c + per < chunks ? c + per : chunks;
-  if (c >= c_end) return;
-  uint32_t lo = 0, hi = nreq;
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) / 2;
-    if (begin[mid] <= c) lo = mid;
-    else hi = mid;
-  }
-  uint32_t r = lo;
+  uint64_t c, c_end;
+  uint32_t r;
+  if (!warp_run(begin, nreq, chunks, c, c_end, r)) return;
   for (; c < c_end; c += 2) {
     r = owner(begin, r, c);
     const ChunkRef<uint64_t> a = chunk_ref<uint64_t>(desc, begin, host, arena, r, c);
@@ -177,19 +189,9 @@ __global__ void __launch_bounds__(kHostStageThreads, 8)
     batch_scatter_kernel(const BatchFilter* __restrict__ desc, const uint64_t* __restrict__ begin, uint32_t nreq,
                          uint64_t chunks, const void* const* __restrict__ host, uint8_t* __restrict__ arena) {
   const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
-  const uint64_t w = static_cast<uint64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
-  const uint64_t per = (chunks + warps - 1) / warps;
-  uint64_t c = w * per;
-  const uint64_t c_end = c + per < chunks ? c + per : chunks;
-  if (c >= c_end) return;
-  uint32_t lo = 0, hi = nreq;
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) / 2;
-    if (begin[mid] <= c) lo = mid;
-    else hi = mid;
-  }
-  uint32_t r = lo;
+  uint64_t c, c_end;
+  uint32_t r;
+  if (!warp_run(begin, nreq, chunks, c, c_end, r)) return;
   for (; c < c_end; ++c) {
     r = owner(begin, r, c);
     const ChunkRef<uint8_t> k = chunk_ref<uint8_t>(desc, begin, host, arena, r, c);
