@@ -325,9 +325,11 @@ def test_learned_lookup_matches_oracle(torch, data, small_learned, quantile, eng
     assert got[:mem.size].all()  # no false negatives
 
 
-def test_learned_lookup_from_host_buffers(torch, data, small_learned):
-    """bf_mlp_contains_host over two ragged chunks equals the device path, and
-    a sample of positions equals the oracle."""
+@pytest.mark.parametrize("out_kind", ["pinned", "pageable"])
+def test_learned_lookup_from_host_buffers(torch, data, small_learned, out_kind):
+    """bf_mlp_contains_host over two ragged chunks, with page-locked and
+    pageable result buffers, equals the device path, and a sample of
+    positions equals the oracle."""
     from paper_2512_15595_gb300.learned import LearnedFilter
     mem, non, _, _ = data
     m, ref = small_learned
@@ -337,7 +339,7 @@ def test_learned_lookup_from_host_buffers(torch, data, small_learned):
     q = torch.empty(n, dtype=torch.int64, pin_memory=True)
     q.copy_(synthkeys.splitmix64_torch(44, 0, n, "cuda"))
     q[:mem.size] = torch.from_numpy(mem.view(np.int64))
-    out = torch.zeros(n, dtype=torch.bool, pin_memory=True)
+    out = torch.zeros(n, dtype=torch.bool, pin_memory=out_kind == "pinned")
     lf.contains_host(q, out)
     torch.cuda.synchronize()
     dq = q.cuda()
